@@ -1,0 +1,386 @@
+"""Benchmark of the generalized Stokes solve on GB300 (one JSON line on stdout).
+
+Step = one full solve of the 2D channel workload (FSI2i-like geometry: 2.5 x 0.41 channel,
+square obstacle, stiff bar with eta contrast 1e4, alpha = rho / dt = 1e3, parabolic inflow,
+do-nothing outflow) on a 1280 x 224 Q2-Q1 mesh with 6 multigrid levels: FGMRES in FP64 with the
+FP32 multigrid V-cycle + Schur step inside, to relative residual 1e-8.  Inputs are resident in
+HBM before the timed region; L2 is flushed (256 MiB write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+
+N > 1 (torchrun, one process per GPU): every rank solves its own replica (the path has no
+exchange step); value = unknowns solved by all ranks / max-over-ranks time.
+--impl reference times the FP64 CPU oracle (the plain assembled-matrix reference of the same
+method) on a bounded sample of the workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A·x GDoF/s; time-to-solve rel-res 1e-8, FP32-MG vs FP64 on GB300; p50/p99"
+WORKLOAD = dict(nx=1280, ny=224, levels=6)
+TOL = 1e-8
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# --------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample
+# --------------------------------------------------------------------------------------------
+ORACLE_SAMPLE = dict(nx=160, ny=28, levels=3)
+
+
+def oracle_sample_run(steps: int, warmup: int):
+    """Time the oracle solve of the channel workload at a reduced mesh (same geometry and
+    coefficients); returns (seconds per solve list, unknowns, iterations)."""
+    from oracle.krylov import StokesOracle
+    from oracle.mesh import mesh_from_problem
+    from paper_2305_08986_gb300 import inputs
+    p = inputs.config_channel(**ORACLE_SAMPLE)
+    m = mesh_from_problem(p)
+    times, its = [], []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        o = StokesOracle(m, p.eta, p.alpha, p.levels)
+        b = o.sys.lift_rhs(p.f, p.g)
+        x, it, rel, _ = o.solve(b, tol=TOL, max_iter=2000)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+            its.append(it)
+    return times, m.N, its
+
+
+def oracle_subprocess(steps: int, warmup: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "t,n,it=bench.oracle_sample_run(%d,%d); print(json.dumps({'t':t,'n':n,'it':it}))"
+            % (ROOT, steps, warmup))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(res):
+    t = statistics.median(res["t"])
+    return {"value": res["n"] / t / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": (f"channel geometry at {ORACLE_SAMPLE['nx']}x{ORACLE_SAMPLE['ny']} cells, "
+                       f"{ORACLE_SAMPLE['levels']} levels ({res['n']} unknowns), full setup + FGMRES solve "
+                       f"to rel-res 1e-8 ({statistics.median(res['it'])} iterations), median of {len(res['t'])}")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 3))
+    res = oracle_subprocess(steps, 0)
+    cb = cpu_baseline_entry(res)
+    t = statistics.median(res["t"])
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GDoF/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"channel {WORKLOAD['nx']}x{WORKLOAD['ny']} (sampled at "
+                                   f"{ORACLE_SAMPLE['nx']}x{ORACLE_SAMPLE['ny']})", "tol": TOL},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------------
+def algorithmic_cost(kind, dim, n_cells, n_u, n_p, elem_bytes):
+    """Algorithmic bytes / flops per launch of the dominant kernel classes."""
+    if kind == "saddle_fp64":
+        # flops of the sum-factorised cell operator (A, B^T, B) per cell, 2D
+        return {"flops": n_cells * (534 + 2 * 75), "bytes": 8 * (2 * (n_u + n_p)) + 8 * n_cells}
+    if kind in ("cheb_step", "residual_A"):
+        vec = n_u * elem_bytes
+        nvec = 6 if kind == "cheb_step" else 3
+        return {"bytes": nvec * vec + n_cells * elem_bytes, "flops": n_cells * 534}
+    return None
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2305_08986_gb300 import build as gsbuild
+    gsbuild.build(verbose=False)
+    from paper_2305_08986_gb300 import gs, inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    p = inputs.config_channel(**WORKLOAD)
+    stream = torch.cuda.current_stream(dev)
+    solver = gs.Solver.from_problem(p, device=dev, restart=args.restart, max_iter=4000)
+    N = solver.n_total
+    f = torch.tensor(p.f, device=dev)
+    g = torch.tensor(p.g, device=dev)
+    rhs = torch.empty_like(f)
+    solver.lift_rhs(f, g, rhs)
+    x = torch.zeros_like(f)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        x.zero_()
+        solver.solve(rhs, x, tol=TOL, allow_noconv=True)
+    launches0 = solver.info().kernel_launches
+    times, its, rels = [], [], []
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    for _ in range(args.steps):
+        x.zero_()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        it, rel, st = solver.solve(rhs, x, tol=TOL, allow_noconv=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        its.append(it)
+        rels.append(rel)
+    barrier()
+    clk = clocks.stop()
+    launches = solver.info().kernel_launches - launches0 - 0
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = N * args.steps * world / (total_ms * 1e-3) / 1e9
+
+    # ---- per-kernel profile of one solve (dominant kernel, roofline) ----
+    solver.profile(True)
+    x.zero_()
+    solver.solve(rhs, x, tol=TOL, allow_noconv=True)
+    solver.profile(False)
+    prof = solver.profile_read()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    peaks = _peaks()
+    n_cells = p.n_cells
+    n_u, n_p = solver.n_u, solver.n_p
+    cost = algorithmic_cost(dom[0], 2, n_cells, n_u, n_p, 4)
+    roof = None
+    if dom[1][0] > 0:
+        avg_s = dom[1][1] / dom[1][0] * 1e-3
+        if dom[0] == "saddle_fp64":
+            peak = args.fp64_peak_tflops
+            ach = cost["flops"] / avg_s / 1e12
+            roof = {"bound": "alu", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom[1][0],
+                    "peak_source": "FP64 FMA microbenchmark on this GB300 (profiles/fp64_fp32_alu_peaks.md)"}
+        elif cost is not None:
+            ach = cost["bytes"] / avg_s / 1e9
+            peak = peaks.get("hbm_gbs", 6800.0)
+            roof = {"bound": "hbm", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom[1][0],
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+
+    # ---- A x throughput (FP64 / FP32), L2 flushed between launches ----
+    def time_apply(dtype, reps=30):
+        xx = torch.randn(n_u, dtype=dtype, device=dev)
+        yy = torch.empty_like(xx)
+        for _ in range(3):
+            solver.vmult_A(xx, yy)
+        ts = []
+        for _ in range(reps):
+            flush.fill_(2.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            solver.vmult_A(xx, yy)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        t = statistics.median(ts) * 1e-3
+        return {"gdofs": n_u / t / 1e9, "us": t * 1e6}
+    ax64 = time_apply(torch.float64)
+    ax32 = time_apply(torch.float32)
+
+    # ---- FP64 multigrid comparison (plain FP64 GPU solve) ----
+    fp64 = None
+    if not args.skip_fp64 and rank == 0:
+        s64 = gs.Solver.from_problem(p, device=dev, mg_precision=64, restart=args.restart, max_iter=4000)
+        x64 = torch.zeros_like(f)
+        s64.solve(rhs, x64, tol=TOL, allow_noconv=True)
+        t64 = []
+        for _ in range(max(1, min(2, args.steps))):
+            x64.zero_()
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            it64, rel64, _ = s64.solve(rhs, x64, tol=TOL, allow_noconv=True)
+            b.record(stream)
+            b.synchronize()
+            t64.append(a.elapsed_time(b))
+        diff = float(torch.linalg.vector_norm(x64 - x) / torch.linalg.vector_norm(x64))
+        fp64 = {"time_to_solve_ms": statistics.median(t64), "iterations": it64, "rel_residual": rel64,
+                "solution_rel_diff_vs_fp32mg": diff}
+        s64.close()
+
+    # ---- end to end through the public API with host buffers ----
+    fh = torch.tensor(p.f).pin_memory()
+    gh = torch.tensor(p.g).pin_memory()
+    xh = torch.empty(N, dtype=torch.float64).pin_memory()
+    fd = torch.empty_like(f)
+    gd = torch.empty_like(g)
+    e2e_ms = []
+    for i in range(1 + max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        fd.copy_(fh, non_blocking=True)
+        gd.copy_(gh, non_blocking=True)
+        solver.lift_rhs(fd, gd, rhs)
+        x.zero_()
+        solver.solve(rhs, x, tol=TOL, allow_noconv=True)
+        xh.copy_(x, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_t = statistics.median(e2e_ms)
+
+    if rank == 0:
+        cb = None
+        if not args.skip_cpu_baseline and world == 1:
+            try:
+                cb = cpu_baseline_entry(oracle_subprocess(1, 0))
+            except Exception as ex:  # the baseline must not break the GPU line
+                cb = {"value": None, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+        ts = sorted(times)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"channel {WORKLOAD['nx']}x{WORKLOAD['ny']} Q2-Q1, obstacle + bar (eta 1e4), "
+                                   f"alpha 1e3, {WORKLOAD['levels']} MG levels, FGMRES({args.restart}) FP64 + FP32 MG",
+                       "unknowns": N, "tol": TOL, "l2": "flushed (256 MiB write) between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_solve_ms": {"p50": statistics.median(ts), "p99": ts[min(len(ts) - 1, int(math.ceil(0.99 * len(ts))) - 1)]},
+            "iterations": statistics.median(its), "rel_residual": max(rels),
+            "ax_gdofs": {"fp64": ax64, "fp32": ax32},
+            "fp64_multigrid": fp64,
+            "roofline": roof,
+            "kernel_profile_ms": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+            "cpu_baseline": cb,
+            "e2e": {"value": N / (e2e_t * 1e-3) / 1e9, "unit": "GDoF/s", "ms": e2e_t,
+                    "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--restart", type=int, default=50)
+    ap.add_argument("--fp64-peak-tflops", type=float, default=1.01)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

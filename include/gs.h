@@ -1,0 +1,208 @@
+/*
+ * gs.h -- C ABI of the GB300 matrix-free generalized Stokes solver.
+ *
+ * Problem (Wichrowski et al., Sec. 3.1.2 predictor mode, Eqs. "form_a_j" and "form_b";
+ * matrix form Eq. "stokes-discrete-block"):
+ *
+ *     alpha u - div(2 eta eps(u)) + grad p = f,   div u = g_p,
+ *
+ * discretised with Q2-Q1 Taylor-Hood elements (Sec. 3.2, Eq. "spaces", p1 = 2, p2 = 1) on a
+ * structured Cartesian quad (dim = 2) or hex (dim = 3) mesh with one viscosity value per
+ * cell.  The saddle matrix is K = [A B^T; B 0] with
+ *     A[i a, j b] = sum_K alpha int phi_i phi_j delta_ab + eta_K int 2 eps(phi_j e_b):eps(phi_i e_a)
+ *     B[q, j b]   = - sum_K int psi_q d phi_j / d x_b      (physical pressure sign).
+ *
+ * Solver (Sec. 4 and Sec. 5 "Linear solver settings"): FGMRES(m) with classical Gram-Schmidt
+ * applied twice, right-preconditioned by the block upper-triangular operator
+ *     z_p = -S^{-1} r_p,   z_u = V(r_u - B^T z_p),
+ * where V is a velocity geometric-multigrid V-cycle with Chebyshev-Jacobi smoothing
+ * (Cheb(A, diag(A), k_A)) and S = M_p(1/eta) is the 1/eta-weighted Q1 pressure mass matrix,
+ * inverted approximately by Chebyshev-Jacobi iterations on Wathen's interval [2^-d, (3/2)^d].
+ *
+ * Vector layout (every vector argument): full length N = d*N_v + N_p, component-blocked,
+ *     [u_x | u_y | (u_z) | p],
+ * velocity nodes on the (2n_x+1) x (2n_y+1) [x (2n_z+1)] grid, pressure nodes on the
+ * (n_x+1) x (n_y+1) [x (n_z+1)] grid, both lexicographic with x fastest.  Velocity-only
+ * vectors (gs_vmult_A, gs_vcycle) have length d*N_v.
+ *
+ * Constraints: velocity nodes on a Dirichlet face (bit set in dirichlet_faces) or touching an
+ * obstacle cell are constrained (all components); pressure nodes touched by no active cell
+ * are constrained.  Constrained rows of K are identity rows and constrained columns are zero,
+ * so a right-hand side holds the Dirichlet value at constrained entries (gs_lift_rhs builds
+ * it).  With every face Dirichlet the constant pressure is in the kernel: the solver keeps
+ * the Euclidean mean of the free pressure entries at zero.
+ *
+ * Memory and streams: all vector pointers are DEVICE pointers owned by the caller.  The
+ * context owns no device allocation: the caller passes one device workspace of
+ * gs_footprint_bytes() bytes (256-byte aligned) to gs_create and keeps it alive until
+ * gs_destroy.  All work is enqueued on the stream given to gs_create (a cudaStream_t cast
+ * to void*, NULL = legacy default stream).  gs_vmult, gs_vmult_A, gs_vcycle, gs_lift_rhs
+ * and gs_apply_level only enqueue work; gs_create and gs_solve synchronise that stream.
+ * A context is not thread-safe; use one context per stream.
+ *
+ * Errors: every call returns a gs_status; no exception crosses the ABI.  GS_EINVAL for bad
+ * arguments (null pointers, sizes, unsupported dim, non-coarsenable mesh), GS_ECUDA when a
+ * CUDA call fails (gs_last_error() gives the CUDA message), GS_ENOCONV when FGMRES stops at
+ * max_iter or cannot reach tol (the best iterate and its residual are still written),
+ * GS_EBREAKDOWN on a non-finite residual (NaN/Inf inputs).
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_ctx gs_ctx; /* opaque; level hierarchy + Krylov workspace */
+
+typedef enum {
+  GS_OK = 0,
+  GS_EINVAL = 1,
+  GS_ENOMEM = 2, /* workspace smaller than gs_footprint_bytes() */
+  GS_ECUDA = 3,
+  GS_ENOCONV = 4,
+  GS_EBREAKDOWN = 5,
+  GS_ETIMEOUT = 6
+} gs_status;
+
+/* Dirichlet face bits */
+#define GS_FACE_XM 1u
+#define GS_FACE_XP 2u
+#define GS_FACE_YM 4u
+#define GS_FACE_YP 8u
+#define GS_FACE_ZM 16u
+#define GS_FACE_ZP 32u
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int n[3];                 /* cells per axis on the FINEST level (n[2] ignored for dim 2) */
+  double len[3];            /* domain extent per axis; origin at 0 */
+  const uint8_t* cell_void; /* HOST array of N_c flags (1 = obstacle cell, excluded) or NULL */
+  uint32_t dirichlet_faces; /* GS_FACE_* bits; faces without a bit are do-nothing (natural) */
+} gs_mesh;
+
+typedef struct {            /* zero-initialised = defaults */
+  int cheb_degree;          /* k_A of Cheb(A, diag A, k_A); 0 -> 4 (Table NS-solver-parameters-1) */
+  int smooth_steps;         /* Chebyshev calls before and after the coarse correction; 0 -> 1 */
+  int restart;              /* FGMRES restart length m; 0 -> 50 */
+  int max_iter;             /* total FGMRES iterations; 0 -> 1000 */
+  int mg_precision;         /* 0 or 32: V-cycle + Schur step in FP32; 64: all FP64 */
+  int schur_degree;         /* Chebyshev steps for S^{-1}; 0 -> 4 */
+  int lanczos_steps;        /* eigenvalue-estimate steps per level; 0 -> 12 */
+  int seed;                 /* SplitMix64 seed of the Lanczos start vectors */
+  int coarse_mode;          /* 0: exact dense FP64 solve on level 0 (default);
+                               1: Chebyshev smoothing only on level 0 (for meshes whose coarsest
+                                  level is too large for a dense factorisation, e.g. 1280 x 210) */
+} gs_options;
+
+/* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */
+size_t gs_footprint_bytes(const gs_mesh* mesh, int levels, const gs_options* opts);
+
+/* Build the hierarchy: levels l = 0 (coarsest, n / 2^(levels-1) cells per axis) ... levels-1
+ * (finest, mesh->n).  eta_per_cell: HOST array of N_c positive finite values (finest level,
+ * cell-lexicographic, x fastest); coarse eta = mean of the active children.  alpha >= 0.
+ * opts may be NULL.  stream: cudaStream_t or NULL.  workspace: device pointer of at least
+ * gs_footprint_bytes() bytes.  On success *out receives the context. */
+gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell, double alpha,
+                    const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
+                    gs_ctx** out);
+
+/* y = K x on the finest level, FP64 (Eq. "stokes-discrete-block" with constraints).
+ * x, y: device, length N, must not alias. */
+gs_status gs_vmult(gs_ctx* ctx, const double* x, double* y);
+
+/* y = A x (velocity block, constrained) on the finest level.  fp32 = 0: x, y are double*;
+ * fp32 = 1: x, y are float* (the operator the FP32 multigrid uses).  Length d*N_v. */
+gs_status gs_vmult_A(gs_ctx* ctx, const void* x, void* y, int fp32);
+
+/* z = V(r): one velocity V-cycle (FP64 in/out; inside in the context's mg_precision).
+ * Length d*N_v, device.  Constrained rows act as identity rows inside the smoother and never
+ * couple to free entries; the block preconditioner overwrites them with r. */
+gs_status gs_vcycle(gs_ctx* ctx, const double* r, double* z);
+
+/* Solve K x = rhs with FGMRES to ||rhs - K x|| / ||rhs|| <= tol (explicit residual).
+ * x: in = initial guess, out = solution (device, length N).  *iterations and *rel_residual
+ * receive the FGMRES iteration count and the explicit relative residual (either may be NULL).
+ * Returns GS_ENOCONV if tol was not reached within max_iter (x holds the last iterate). */
+gs_status gs_solve(gs_ctx* ctx, const double* rhs, double* x, double tol, int* iterations,
+                   double* rel_residual);
+
+/* rhs = [M_u f_u ; M_p f_p] - K_raw g on free entries, rhs = g on constrained entries, where
+ * f is a nodal load field (full layout) and g holds Dirichlet values (full layout; only its
+ * constrained entries are used).  K_raw is the saddle matrix without constraint elimination.
+ * All pointers device, length N; rhs must not alias f or g. */
+gs_status gs_lift_rhs(gs_ctx* ctx, const double* f, const double* g, double* rhs);
+
+/* Solve `count` independent systems; ctxs[i] with rhs[i] -> x[i] (device pointers).
+ * iterations / rel_residuals: host arrays of `count` entries or NULL.  Returns the first
+ * non-OK status (all systems are still attempted). */
+gs_status gs_batch_solve(gs_ctx* const* ctxs, int count, const double* const* rhs,
+                         double* const* x, double tol, int* iterations, double* rel_residuals);
+
+/* ---- level operators (the individual kernels of the path, for checking and profiling) ---- */
+typedef enum {
+  GS_OP_A = 0,           /* y = A_l x            (velocity, constrained)            */
+  GS_OP_RESIDUAL_A = 1,  /* y = b - A_l x        (aux = b)                          */
+  GS_OP_DIAG_A = 2,      /* y = diag(A_l)        (x ignored; velocity length)       */
+  GS_OP_SMOOTH = 3,      /* y = Cheb(A_l, diag, k_A) from x0 = aux (NULL -> 0), rhs x */
+  GS_OP_RESTRICT = 4,    /* y (level l-1) = P_l^T x (level l)                       */
+  GS_OP_PROLONGATE = 5,  /* y (level l) += P_l x (level l-1)                        */
+  GS_OP_B = 6,           /* y (pressure, N_p) = B x (velocity)      finest level only */
+  GS_OP_BT = 7,          /* y (velocity) = B^T x (pressure)         finest level only */
+  GS_OP_SCHUR_MASS = 8,  /* y = M_p(1/eta) x     (pressure)         finest level only */
+  GS_OP_SCHUR_INV = 9,   /* y = Cheb(M_p(1/eta), diag, schur_degree) x, from 0       */
+  GS_OP_COARSE = 10,     /* y = A_0^{-1} x       (level 0, dense FP64)               */
+  GS_OP_PRECOND = 11,    /* y = P^{-1} x         (full block preconditioner)         */
+  GS_OP_A_RAW = 12       /* y = A_l x without constraint elimination                 */
+} gs_op;
+
+/* Apply one operator of level `level` (0 = coarsest).  prec = 64: x, y, aux are double*;
+ * prec = 32: float* (GS_OP_COARSE and GS_OP_PRECOND take double* always).  Enqueue only. */
+gs_status gs_apply_level(gs_ctx* ctx, int level, gs_op op, int prec, const void* x, void* y,
+                         const void* aux);
+
+/* Introspection: sizes and eigenvalue bounds. */
+typedef struct {
+  int levels;
+  int dim;
+  long long n_total;       /* N of the finest level */
+  long long n_u;           /* d * N_v of the finest level */
+  long long n_p;           /* N_p of the finest level */
+  int pressure_nullspace;  /* 1 if every face is Dirichlet */
+  int last_iterations;
+  double last_rel_residual;
+  double lambda_max[16];   /* Chebyshev upper bound (1.2 x Lanczos estimate) per level */
+  long long level_n_u[16];
+  int coarse_free;         /* unknowns of the dense coarse solve */
+  size_t footprint_bytes;
+  long long kernel_launches; /* kernels this library has launched in this process (all contexts) */
+} gs_info;
+gs_status gs_get_info(const gs_ctx* ctx, gs_info* out);
+
+/* Per-kernel-class timing of the work a context enqueues (tracing aid, no paper counterpart in
+ * the method itself; the paper reports time per unknown, Sec. 5).  gs_profile(ctx, 1) starts
+ * recording a CUDA event pair around every launch of gs_solve / gs_vcycle / gs_vmult work;
+ * gs_profile(ctx, 0) stops.  gs_profile_read synchronises the stream and fills up to `max`
+ * entries (one per class: launches and summed device milliseconds); returns the count. */
+typedef struct {
+  const char* name;        /* static string */
+  long long launches;
+  double total_ms;
+} gs_kernel_stat;
+gs_status gs_profile(gs_ctx* ctx, int enable);
+int gs_profile_read(gs_ctx* ctx, gs_kernel_stat* out, int max);
+
+/* Change the stream work is enqueued on. */
+gs_status gs_set_stream(gs_ctx* ctx, void* stream);
+
+void gs_destroy(gs_ctx* ctx);
+const char* gs_strerror(gs_status s);
+const char* gs_last_error(void); /* thread-local text of the last GS_ECUDA / GS_EINVAL cause */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

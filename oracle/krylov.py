@@ -12,7 +12,7 @@ Sec. 4; it stops on the Euclidean norm of the residual.  Readings taken here:
   most 3 extra times;
 * restart length m = 50; orthogonalisation = classical Gram-Schmidt applied twice;
 * preconditioner (block upper triangular):  z_p = -S^{-1} r_p,
-  z_u = V-cycle(r_u - B^T z_p);
+  z_u = V-cycle(r_u - B^T z_p); on constrained entries (identity rows of K) z = r;
 * pure-Dirichlet problems have the constant pressure in the kernel; the mean of
   the free pressure entries is subtracted from every preconditioned vector and
   from the final iterate.
@@ -133,7 +133,10 @@ class StokesOracle:
         ru, rp = r[:n_u], r[n_u:]
         zp = -schur_apply_inv(self.sys.Mpw, rp, self.mesh.dim)
         zu = self.mg.vcycle(ru - self.sys.B.T @ zp)
-        return self.project(np.concatenate([zu, zp]))
+        z = np.concatenate([zu, zp])
+        # K is the identity on constrained rows: invert that block exactly
+        z[self.sys.constrained] = r[self.sys.constrained]
+        return self.project(z)
 
     def solve(self, b, tol=1e-8, x0=None, max_iter=1000):
         x, it, rel, hist = fgmres(self.apply_K, self.precond, b, x0, tol, self.restart, max_iter)

@@ -21,7 +21,8 @@ is silent on several details, read here as follows:
   with SplitMix64 (constrained entries zeroed);
 * one pre- and one post-smoothing Chebyshev call per level, degree k_A = 4
   (Table "NS-solver-parameters-1", predictor column);
-* coarsest level solved exactly by a dense FP64 Cholesky factorisation;
+* coarsest level solved exactly by a dense FP64 Cholesky factorisation (option: Chebyshev
+  smoothing only, for meshes whose coarsest level is too large to factor);
 * Schur approximation S^ = M_p(1/eta); S^{-1} applied by 4 Chebyshev-Jacobi
   steps on the fixed interval [2^-d, (3/2)^d] (Wathen's bounds for the
   Jacobi-scaled Q1 mass matrix, which hold for any positive cell weights).
@@ -153,7 +154,7 @@ class Hierarchy:
     """Velocity multigrid hierarchy, levels[0] = coarsest."""
 
     def __init__(self, fine: Mesh, eta_fine, alpha, nlevels, degree=4, seed=0,
-                 lanczos_steps=12, safety=1.2, ratio=15.0):
+                 lanczos_steps=12, safety=1.2, ratio=15.0, coarse="cholesky"):
         meshes = [fine]
         etas = [np.asarray(eta_fine, dtype=float)]
         for _ in range(nlevels - 1):
@@ -166,12 +167,14 @@ class Hierarchy:
         self.levels = [Level(m, e, alpha, i) for i, (m, e) in enumerate(zip(meshes, etas))]
         for i in range(1, len(self.levels)):
             self.levels[i].P = prolongation(meshes[i - 1], meshes[i])
-        for lv in self.levels[1:]:
+        self.coarse = coarse
+        for lv in self.levels[(0 if coarse == "chebyshev" else 1):]:
             v0 = lanczos_start(lv.mesh.n_u, seed, lv.index)
             v0[lv.sys.u_constrained] = 0.0
             lv.lam_hi = safety * lanczos_max(lv.A, lv.D, v0, lanczos_steps)
-        A0 = self.levels[0].A.toarray()
-        self.levels[0].chol = sla.cho_factor(A0, lower=True)
+        if coarse == "cholesky":
+            A0 = self.levels[0].A.toarray()
+            self.levels[0].chol = sla.cho_factor(A0, lower=True)
 
     def vcycle(self, b, level=None):
         """Velocity V-cycle V(l, b) (Sec. 4): pre-smooth from 0, residual, restrict, recurse,
@@ -180,6 +183,8 @@ class Hierarchy:
             level = len(self.levels) - 1
         lv = self.levels[level]
         if level == 0:
+            if self.coarse == "chebyshev":   # smoothing only, for coarse meshes too large to factor
+                return chebyshev(lv.A, 1.0 / lv.D, b, None, self.degree, lv.lam_hi / self.ratio, lv.lam_hi)
             return sla.cho_solve(lv.chol, b)
         lo, hi = lv.lam_hi / self.ratio, lv.lam_hi
         Dinv = 1.0 / lv.D

@@ -1,0 +1,1157 @@
+// Host side of libgs.so: level hierarchy, setup (diagonals, Lanczos bounds, dense coarse
+// inverse), the velocity V-cycle, the block-triangular preconditioner, FGMRES with CGS2, and
+// the extern "C" entry points declared in include/gs.h.
+//
+// Every device buffer is carved out of the caller's workspace (no device allocation here);
+// every launch goes to the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gs.h"
+#include "gs_kernels.h"
+
+using namespace gs;
+
+namespace {
+
+thread_local std::string g_err;
+
+gs_status fail(gs_status s, const std::string& why) {
+  g_err = why;
+  return s;
+}
+
+#define CK(...)                                                                        \
+  do {                                                                                 \
+    cudaError_t e__ = (__VA_ARGS__);                                                   \
+    if (e__ != cudaSuccess)                                                            \
+      return fail(GS_ECUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
+
+#define CKS(...)                               \
+  do {                                         \
+    gs_status s__ = (__VA_ARGS__);             \
+    if (s__ != GS_OK) return s__;              \
+  } while (0)
+
+// kernel classes reported by gs_profile_read
+enum KClass { K_SADDLE64 = 0, K_CHEB, K_RESID, K_BT, K_TRANSFER, K_COARSE, K_SCHUR, K_DOTS, K_AXPY, K_VEC, K_NCLASS };
+const char* const kclass_name[K_NCLASS] = {"saddle_fp64", "cheb_step", "residual_A", "gradient_BT", "transfer",
+                                           "coarse_solve", "schur_step", "gram_schmidt_dots", "krylov_axpy",
+                                           "vector_misc"};
+
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(long long count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += (size_t)(count > 0 ? count : 1) * sizeof(T);
+    return p;
+  }
+};
+
+struct Level {
+  int n[3] = {1, 1, 1};
+  double h[3] = {1, 1, 1};
+  long long Nv = 0, Np = 0, Nc = 0, nu = 0;
+  bool has_void = false;
+  std::vector<uint8_t> hvoid, hvmask, hpmask;
+  std::vector<double> heta;
+  Geom g{};
+  OpCoef<double> c64{};
+  OpCoef<float> c32{};
+  double* eta64 = nullptr;
+  float* eta32 = nullptr;
+  uint8_t *vmask = nullptr, *pmask = nullptr, *cvoid = nullptr;
+  void *xA = nullptr, *xB = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
+  double lam_hi = 0.0;
+};
+
+}  // namespace
+
+struct gs_ctx {
+  int dim = 2, L = 1;
+  gs_options opt{};
+  double alpha = 0.0;
+  cudaStream_t st = nullptr;
+  bool fp32 = true;
+  std::vector<Level> lv;
+  long long N = 0, nu = 0, np = 0;
+  bool nullspace = false;
+  long long n_pfree = 0;
+  // Schur step vectors (finest level, MG precision)
+  void *p_b = nullptr, *p_xA = nullptr, *p_xB = nullptr, *p_d = nullptr, *p_dinv = nullptr;
+  // dense coarse inverse
+  int nf = 0;
+  std::vector<int> hfree;
+  double* Ainv = nullptr;
+  int* cfree = nullptr;
+  double *ctmp = nullptr, *gjrow = nullptr, *gjcol = nullptr;
+  // Krylov (FP64)
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double* part = nullptr;
+  int G = 1;
+  double* dsc = nullptr;
+  double* hpin = nullptr;
+  int last_it = 0;
+  double last_rel = 0.0;
+  size_t footprint = 0;
+  // optional per-kernel-class timing (CUDA event pairs on the context stream)
+  bool prof = false;
+  std::vector<cudaEvent_t> evs;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> recs;
+};
+
+namespace {
+
+long prof_begin(gs_ctx* c, int cls) {
+  if (!c->prof) return -1;
+  if (c->ev_used + 2 > c->evs.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { c->prof = false; return -1; }
+      c->evs.push_back(e);
+    }
+  }
+  const size_t i = c->ev_used;
+  c->ev_used += 2;
+  cudaEventRecord(c->evs[i], c->st);
+  c->recs.push_back({cls, i});
+  return (long)i;
+}
+void prof_end(gs_ctx* c, long i) {
+  if (i >= 0) cudaEventRecord(c->evs[(size_t)i + 1], c->st);
+}
+
+#define KL(cls, ...)                      \
+  do {                                    \
+    const long p__ = prof_begin(c, cls);  \
+    CK(__VA_ARGS__);                      \
+    prof_end(c, p__);                     \
+  } while (0)
+
+int opt_or(int v, int d) { return v > 0 ? v : d; }
+
+gs_options normalize_opts(const gs_options* o) {
+  gs_options r{};
+  if (o) r = *o;
+  r.cheb_degree = opt_or(r.cheb_degree, 4);
+  r.smooth_steps = opt_or(r.smooth_steps, 1);
+  r.restart = opt_or(r.restart, 50);
+  r.max_iter = opt_or(r.max_iter, 1000);
+  r.mg_precision = (r.mg_precision == 64) ? 64 : 32;
+  r.schur_degree = opt_or(r.schur_degree, 4);
+  r.lanczos_steps = opt_or(r.lanczos_steps, 12);
+  r.coarse_mode = r.coarse_mode == 1 ? 1 : 0;
+  return r;
+}
+
+template <typename T>
+OpCoef<T> make_coef(int dim, const double* h, double alpha) {
+  OpCoef<T> c{};
+  if (dim == 2) {
+    const double hx = h[0], hy = h[1];
+    c.mm = (T)(alpha * hx * hy / 900.0);
+    c.km[0] = (T)(hy / (90.0 * hx));
+    c.km[1] = (T)(hx / (90.0 * hy));
+    c.km[2] = 0;
+    c.ex[0] = c.ex[1] = c.ex[2] = (T)(1.0 / 36.0);
+    c.bd[0] = (T)(hy / 36.0);
+    c.bd[1] = (T)(hx / 36.0);
+    c.bd[2] = 0;
+    c.pm = (T)(hx * hy / 36.0);
+  } else {
+    const double hx = h[0], hy = h[1], hz = h[2];
+    c.mm = (T)(alpha * hx * hy * hz / 27000.0);
+    c.km[0] = (T)(hy * hz / (2700.0 * hx));
+    c.km[1] = (T)(hx * hz / (2700.0 * hy));
+    c.km[2] = (T)(hx * hy / (2700.0 * hz));
+    c.ex[0] = (T)(hx / 1080.0);
+    c.ex[1] = (T)(hy / 1080.0);
+    c.ex[2] = (T)(hz / 1080.0);
+    c.bd[0] = (T)(hy * hz / 216.0);
+    c.bd[1] = (T)(hx * hz / 216.0);
+    c.bd[2] = (T)(hx * hy / 216.0);
+    c.pm = (T)(hx * hy * hz / 216.0);
+  }
+  c.eta_scale = (T)1;
+  return c;
+}
+
+// ---- host planning: level sizes, obstacle flags, constraint masks, coarse eta -----------------
+gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
+  if (!m) return fail(GS_EINVAL, "mesh is NULL");
+  if (m->dim != 2 && m->dim != 3) return fail(GS_EINVAL, "dim must be 2 or 3");
+  if (L < 1 || L > 16) return fail(GS_EINVAL, "levels must be in [1, 16]");
+  const int dim = m->dim;
+  for (int a = 0; a < dim; ++a) {
+    if (m->n[a] < 1) return fail(GS_EINVAL, "cells per axis must be >= 1");
+    if (!(m->len[a] > 0.0)) return fail(GS_EINVAL, "domain extent must be > 0");
+    if (m->n[a] % (1 << (L - 1)) != 0)
+      return fail(GS_EINVAL, "cells per axis must be divisible by 2^(levels-1)");
+    if (m->n[a] > (1 << 24)) return fail(GS_EINVAL, "mesh too large");
+  }
+  c->dim = dim;
+  c->L = L;
+  c->lv.assign(L, Level());
+  for (int l = L - 1; l >= 0; --l) {
+    Level& lv = c->lv[l];
+    for (int a = 0; a < 3; ++a) {
+      lv.n[a] = a < dim ? (m->n[a] >> (L - 1 - l)) : 1;
+      lv.h[a] = a < dim ? m->len[a] / lv.n[a] : 1.0;
+    }
+    lv.Nc = (long long)lv.n[0] * lv.n[1] * lv.n[2];
+    lv.Nv = (long long)(2 * lv.n[0] + 1) * (2 * lv.n[1] + 1) * (dim == 3 ? 2 * lv.n[2] + 1 : 1);
+    lv.Np = (long long)(lv.n[0] + 1) * (lv.n[1] + 1) * (dim == 3 ? lv.n[2] + 1 : 1);
+    lv.nu = dim * lv.Nv;
+  }
+  // obstacle flags and eta per level (finest from input; coarse: all children void / mean of active)
+  Level& F = c->lv[L - 1];
+  F.hvoid.assign(F.Nc, 0);
+  bool any_void = false;
+  if (m->cell_void) {
+    for (long long i = 0; i < F.Nc; ++i) {
+      F.hvoid[i] = m->cell_void[i] ? 1 : 0;
+      any_void |= F.hvoid[i] != 0;
+    }
+  }
+  if (eta) {
+    F.heta.assign(eta, eta + F.Nc);
+    for (long long i = 0; i < F.Nc; ++i)
+      if (!(std::isfinite(eta[i]) && eta[i] > 0.0) && !F.hvoid[i])
+        return fail(GS_EINVAL, "eta must be positive and finite on active cells");
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    Level& C = c->lv[l];
+    const Level& Fi = c->lv[l + 1];
+    C.hvoid.assign(C.Nc, 0);
+    if (eta) C.heta.assign(C.Nc, 1.0);
+    for (int k = 0; k < C.n[2]; ++k)
+      for (int j = 0; j < C.n[1]; ++j)
+        for (int i = 0; i < C.n[0]; ++i) {
+          const long long cc = i + (long long)C.n[0] * (j + (long long)C.n[1] * k);
+          int nact = 0, nch = 0;
+          double s = 0.0;
+          for (int dk = 0; dk < (dim == 3 ? 2 : 1); ++dk)
+            for (int dj = 0; dj < 2; ++dj)
+              for (int di = 0; di < 2; ++di) {
+                const long long fc = (2 * i + di) + (long long)Fi.n[0] * ((2 * j + dj) + (long long)Fi.n[1] * (dim == 3 ? 2 * k + dk : 0));
+                nch++;
+                if (!Fi.hvoid[fc]) {
+                  nact++;
+                  if (eta) s += Fi.heta[fc];
+                }
+              }
+          C.hvoid[cc] = (nact == 0) ? 1 : 0;
+          if (eta && nact > 0) C.heta[cc] = s / nact;
+          (void)nch;
+        }
+  }
+  for (int l = 0; l < L; ++l) {
+    Level& lv = c->lv[l];
+    lv.has_void = any_void;
+    if (!any_void) continue;
+    const int nv0 = 2 * lv.n[0] + 1, nv1 = 2 * lv.n[1] + 1, nv2 = dim == 3 ? 2 * lv.n[2] + 1 : 1;
+    lv.hvmask.assign(lv.Nv, 0);
+    Geom gtmp{};
+    gtmp.dim = dim;
+    gtmp.faces = m->dirichlet_faces;
+    gtmp.nv[0] = nv0; gtmp.nv[1] = nv1; gtmp.nv[2] = nv2;
+    for (int K = 0; K < nv2; ++K)
+      for (int J = 0; J < nv1; ++J)
+        for (int I = 0; I < nv0; ++I)
+          if (face_constrained(gtmp, I, J, K)) lv.hvmask[I + (long long)nv0 * (J + (long long)nv1 * K)] = 1;
+    for (int k = 0; k < lv.n[2]; ++k)
+      for (int j = 0; j < lv.n[1]; ++j)
+        for (int i = 0; i < lv.n[0]; ++i) {
+          const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+          if (!lv.hvoid[cc]) continue;
+          for (int lc = 0; lc < (dim == 3 ? 3 : 1); ++lc)
+            for (int lb = 0; lb < 3; ++lb)
+              for (int la = 0; la < 3; ++la)
+                lv.hvmask[(2 * i + la) + (long long)nv0 * ((2 * j + lb) + (long long)nv1 * (dim == 3 ? 2 * k + lc : 0))] = 1;
+        }
+    if (l == L - 1) {
+      const int np0 = lv.n[0] + 1, np1 = lv.n[1] + 1;
+      lv.hpmask.assign(lv.Np, 1);
+      for (int k = 0; k < lv.n[2]; ++k)
+        for (int j = 0; j < lv.n[1]; ++j)
+          for (int i = 0; i < lv.n[0]; ++i) {
+            const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+            if (lv.hvoid[cc]) continue;
+            for (int lc = 0; lc < (dim == 3 ? 2 : 1); ++lc)
+              for (int lb = 0; lb < 2; ++lb)
+                for (int la = 0; la < 2; ++la)
+                  lv.hpmask[(i + la) + (long long)np0 * ((j + lb) + (long long)np1 * (dim == 3 ? k + lc : 0))] = 0;
+          }
+    }
+  }
+  // free unknowns of the coarse level
+  Level& C0 = c->lv[0];
+  c->hfree.clear();
+  if (c->opt.coarse_mode != 1) {
+    Geom gtmp{};
+    gtmp.dim = dim;
+    gtmp.faces = m->dirichlet_faces;
+    gtmp.nv[0] = 2 * C0.n[0] + 1; gtmp.nv[1] = 2 * C0.n[1] + 1; gtmp.nv[2] = dim == 3 ? 2 * C0.n[2] + 1 : 1;
+    for (int a = 0; a < dim; ++a)
+      for (long long node = 0; node < C0.Nv; ++node) {
+        const int I = (int)(node % gtmp.nv[0]);
+        const int J = (int)((node / gtmp.nv[0]) % gtmp.nv[1]);
+        const int K = (int)(node / ((long long)gtmp.nv[0] * gtmp.nv[1]));
+        const bool con = C0.has_void ? C0.hvmask[node] != 0 : face_constrained(gtmp, I, J, K);
+        if (!con) c->hfree.push_back((int)(a * C0.Nv + node));
+      }
+  }
+  c->nf = (int)c->hfree.size();
+  if ((long long)c->nf * c->nf > (1LL << 31)) return fail(GS_EINVAL, "coarsest level too large for the dense solve; use more levels");
+  const Level& Fl = c->lv[L - 1];
+  c->nu = Fl.nu;
+  c->np = Fl.Np;
+  c->N = Fl.nu + Fl.Np;
+  c->nullspace = m->dirichlet_faces == ((1u << (2 * dim)) - 1u);
+  c->n_pfree = Fl.Np;
+  if (Fl.has_void) {
+    c->n_pfree = 0;
+    for (auto v : Fl.hpmask) c->n_pfree += v ? 0 : 1;
+  }
+  return GS_OK;
+}
+
+// ---- device layout (dry run when ar.base == nullptr) -------------------------------------------
+void layout(gs_ctx* c, Arena& ar) {
+  const size_t S = c->fp32 ? 4 : 8;
+  auto takeT = [&](long long n) -> void* { return S == 4 ? (void*)ar.take<float>(n) : (void*)ar.take<double>(n); };
+  for (int l = 0; l < c->L; ++l) {
+    Level& lv = c->lv[l];
+    lv.eta64 = ar.take<double>(lv.Nc);
+    lv.eta32 = ar.take<float>(lv.Nc);
+    if (lv.has_void) {
+      lv.cvoid = ar.take<uint8_t>(lv.Nc);
+      lv.vmask = ar.take<uint8_t>(lv.Nv);
+      if (l == c->L - 1) lv.pmask = ar.take<uint8_t>(lv.Np);
+    }
+    lv.xA = takeT(lv.nu);
+    lv.xB = takeT(lv.nu);
+    lv.b = takeT(lv.nu);
+    lv.d = takeT(lv.nu);
+    lv.dinv = takeT(lv.nu);
+  }
+  const Level& F = c->lv[c->L - 1];
+  c->p_b = takeT(F.Np);
+  c->p_xA = takeT(F.Np);
+  c->p_xB = takeT(F.Np);
+  c->p_d = takeT(F.Np);
+  c->p_dinv = takeT(F.Np);
+  c->Ainv = ar.take<double>((long long)c->nf * c->nf);
+  c->cfree = ar.take<int>(c->nf);
+  c->ctmp = ar.take<double>(c->nf);
+  c->gjrow = ar.take<double>(c->nf);
+  c->gjcol = ar.take<double>(c->nf);
+  const int m = c->opt.restart;
+  c->V = ar.take<double>((long long)(m + 1) * c->N);
+  c->Z = ar.take<double>((long long)m * c->N);
+  c->w = ar.take<double>(c->N);
+  c->r = ar.take<double>(c->N);
+  c->t1 = ar.take<double>(c->N);
+  c->t2 = ar.take<double>(c->N);
+  long long G = (c->N + 4095) / 4096;
+  if (G > 304) G = 304;
+  if (G < 1) G = 1;
+  c->G = (int)G;
+  c->part = ar.take<double>((long long)c->G * (m + 2));
+  c->dsc = ar.take<double>(4 * (m + 4));
+  c->footprint = ar.off + 256;
+}
+
+void set_geom(gs_ctx* c, const gs_mesh* m) {
+  for (int l = 0; l < c->L; ++l) {
+    Level& lv = c->lv[l];
+    Geom& g = lv.g;
+    g.dim = c->dim;
+    for (int a = 0; a < 3; ++a) {
+      g.n[a] = lv.n[a];
+      g.nv[a] = a < c->dim ? 2 * lv.n[a] + 1 : 1;
+      g.npn[a] = a < c->dim ? lv.n[a] + 1 : 1;
+      g.h[a] = lv.h[a];
+    }
+    g.Nv = lv.Nv;
+    g.Np = lv.Np;
+    g.Nc = lv.Nc;
+    g.faces = m->dirichlet_faces;
+    g.vmask = lv.vmask;
+    g.pmask = lv.pmask;
+    g.cvoid = lv.cvoid;
+    lv.c64 = make_coef<double>(c->dim, lv.h, c->alpha);
+    lv.c32 = make_coef<float>(c->dim, lv.h, c->alpha);
+  }
+}
+
+// ---- small helpers ----------------------------------------------------------------------------
+template <typename T>
+OpCoef<T> coef(const Level& lv);
+template <>
+OpCoef<double> coef<double>(const Level& lv) { return lv.c64; }
+template <>
+OpCoef<float> coef<float>(const Level& lv) { return lv.c32; }
+template <typename T>
+const T* etap(const Level& lv);
+template <>
+const double* etap<double>(const Level& lv) { return lv.eta64; }
+template <>
+const float* etap<float>(const Level& lv) { return lv.eta32; }
+
+template <typename T>
+TileArgs<T> tile_args(const Level& lv) {
+  TileArgs<T> a{};
+  a.g = lv.g;
+  a.c = coef<T>(lv);
+  a.eta = etap<T>(lv);
+  return a;
+}
+
+// dot products of T vectors accumulated in FP64, result copied to host
+template <typename T>
+gs_status dot_host(gs_ctx* c, const T* V, long long ldv, int k, const T* w, long long n, double* out) {
+  KL(K_DOTS, launch_dots_partial<T>(V, ldv, k, w, n, c->part, c->G, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, k, c->G, c->dsc, c->st));
+  CK(cudaMemcpyAsync(c->hpin, c->dsc, sizeof(double) * k, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int i = 0; i < k; ++i) out[i] = c->hpin[i];
+  return GS_OK;
+}
+
+// largest eigenvalue of the symmetric tridiagonal matrix (a, b) by Sturm-sequence bisection
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int k = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(b[i]) : 0.0);
+    lo = std::fmin(lo, a[i] - r);
+    hi = std::fmax(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int cnt = 0;
+    double q = a[0] - x;
+    if (q < 0) cnt++;
+    for (int i = 1; i < k; ++i) {
+      if (q == 0.0) q = 1e-300;
+      q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+      if (q < 0) cnt++;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (count_below(mid) >= k) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Lanczos estimate of lambda_max(D^{-1} A_l) on level l (Sec. 4 Chebyshev bounds)
+template <typename T>
+gs_status lanczos(gs_ctx* c, int l) {
+  Level& lv = c->lv[l];
+  const long long n = lv.nu;
+  std::vector<T> h0(n);
+  const uint64_t base = ((uint64_t)((uint32_t)c->opt.seed) << 32) ^ ((uint64_t)(l & 0xFF) << 56);
+  for (long long i = 0; i < n; ++i) {
+    const uint64_t r = splitmix64(base ^ (uint64_t)i);
+    h0[i] = (T)(2.0 * ((double)(r >> 11) * (1.0 / 9007199254740992.0)) - 1.0);
+  }
+  T* v = (T*)lv.xA;
+  T* vprev = (T*)lv.xB;
+  T* t = (T*)lv.d;
+  T* w = (T*)lv.b;
+  CK(cudaMemcpyAsync(v, h0.data(), sizeof(T) * n, cudaMemcpyHostToDevice, c->st));
+  CK(launch_zero_constrained_u<T>(lv.g, v, c->st));
+  double nrm2;
+  CKS(dot_host<T>(c, v, n, 1, v, n, &nrm2));
+  CK(launch_cast<T, T>(v, v, n, (T)(1.0 / std::sqrt(nrm2)), c->st));
+  CK(cudaMemsetAsync(vprev, 0, sizeof(T) * n, c->st));
+  std::vector<double> al, be;
+  double beta_prev = 0.0;
+  const T* dinv = (const T*)lv.dinv;
+  for (int j = 0; j < c->opt.lanczos_steps; ++j) {
+    CK(launch_lanczos_pre<T>(dinv, v, t, n, c->st));
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = t;
+    a.yu = w;
+    CK(launch_tile<T>(c->dim, TILE_APPLY, OPS_A, a, c->st));
+    CK(launch_lanczos_post<T>(dinv, w, vprev, (T)beta_prev, w, n, c->st));
+    double alpha;
+    CKS(dot_host<T>(c, w, n, 1, v, n, &alpha));
+    CK(launch_axpby<T>(v, w, (T)(-alpha), (T)1, n, c->st));
+    double bb;
+    CKS(dot_host<T>(c, w, n, 1, w, n, &bb));
+    const double beta = std::sqrt(bb);
+    al.push_back(alpha);
+    if (j == c->opt.lanczos_steps - 1 || beta == 0.0) break;
+    be.push_back(beta);
+    // vprev <- v ; v <- w / beta
+    CK(launch_cast<T, T>(w, vprev, n, (T)(1.0 / beta), c->st));
+    std::swap(v, vprev);
+    beta_prev = beta;
+  }
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  lv.lam_hi = 1.2 * tridiag_max_eig(al, be);
+  if (!std::isfinite(lv.lam_hi) || lv.lam_hi <= 0.0) return fail(GS_EBREAKDOWN, "eigenvalue estimate failed");
+  return GS_OK;
+}
+
+// host assembly of the dense coarse matrix on its free unknowns (same closed-form 1D matrices)
+void assemble_coarse(gs_ctx* c, std::vector<double>& A) {
+  const Level& lv = c->lv[0];
+  const int dim = c->dim;
+  const int nf = c->nf;
+  A.assign((size_t)nf * nf, 0.0);
+  std::vector<int> map(lv.nu, -1);
+  for (int i = 0; i < nf; ++i) map[c->hfree[i]] = i;
+  static const int Mi[3][3] = {{4, 2, -1}, {2, 16, 2}, {-1, 2, 4}};
+  static const int Ki[3][3] = {{7, -8, 1}, {-8, 16, -8}, {1, -8, 7}};
+  static const int Ei[3][3] = {{-3, -4, 1}, {4, 0, -4}, {-1, 4, 3}};
+  const OpCoef<double>& cf = lv.c64;
+  const int nb = dim == 2 ? 9 : 27;
+  const int nv0 = 2 * lv.n[0] + 1, nv1 = 2 * lv.n[1] + 1;
+  std::vector<long long> gn(nb);
+  for (int k = 0; k < lv.n[2]; ++k)
+    for (int j = 0; j < lv.n[1]; ++j)
+      for (int i = 0; i < lv.n[0]; ++i) {
+        const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+        if (lv.has_void && lv.hvoid[cc]) continue;
+        const double eta = lv.heta[cc];
+        for (int q = 0; q < nb; ++q) {
+          const int la = q % 3, lb = (q / 3) % 3, lc = q / 9;
+          gn[q] = (2 * i + la) + (long long)nv0 * ((2 * j + lb) + (long long)nv1 * (dim == 3 ? 2 * k + lc : 0));
+        }
+        for (int al = 0; al < dim; ++al)
+          for (int be = 0; be < dim; ++be)
+            for (int p = 0; p < nb; ++p) {
+              const int row = map[al * lv.Nv + gn[p]];
+              if (row < 0) continue;
+              const int pi[3] = {p % 3, (p / 3) % 3, p / 9};
+              for (int q = 0; q < nb; ++q) {
+                const int col = map[be * lv.Nv + gn[q]];
+                if (col < 0) continue;
+                const int qi[3] = {q % 3, (q / 3) % 3, q / 9};
+                double v = 0.0;
+                if (al == be) {
+                  const double cz = (al == 2 ? 2.0 : 1.0) * eta * cf.km[2];
+                  const double cy = (al == 1 ? 2.0 : 1.0) * eta * cf.km[1];
+                  const double cx = (al == 0 ? 2.0 : 1.0) * eta * cf.km[0];
+                  const double Mx = Mi[pi[0]][qi[0]], My = Mi[pi[1]][qi[1]];
+                  const double Kx = Ki[pi[0]][qi[0]], Ky = Ki[pi[1]][qi[1]];
+                  if (dim == 2) {
+                    v = Mx * (cf.mm * My + cy * Ky) + Kx * (cx * My);
+                  } else {
+                    const double Mz = Mi[pi[2]][qi[2]], Kz = Ki[pi[2]][qi[2]];
+                    v = Mx * (My * (cf.mm * Mz + cz * Kz) + cy * Ky * Mz) + Kx * (cx * My * Mz);
+                  }
+                } else {
+                  // eta (E in direction be) (E^T in direction al) (M in the third direction)
+                  double prod = 1.0;
+                  int third = 3 - al - be;
+                  for (int ax = 0; ax < dim; ++ax) {
+                    if (ax == be) prod *= Ei[pi[ax]][qi[ax]];
+                    else if (ax == al) prod *= Ei[qi[ax]][pi[ax]];
+                    else prod *= Mi[pi[ax]][qi[ax]];
+                  }
+                  const double ce = dim == 2 ? cf.ex[0] : cf.ex[third];
+                  v = eta * ce * prod;
+                }
+                A[(size_t)row * nf + col] += v;
+              }
+            }
+      }
+}
+
+template <typename T>
+gs_status setup_T(gs_ctx* c) {
+  for (int l = 0; l < c->L; ++l) {
+    Level& lv = c->lv[l];
+    CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), (T*)lv.dinv, 1, c->st));
+  }
+  for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(lanczos<T>(c, l));
+  const Level& F = c->lv[c->L - 1];
+  CK(launch_pdiag<T>(F.g, coef<T>(F), etap<T>(F), (T*)c->p_dinv, c->st));
+  return GS_OK;
+}
+
+gs_status setup(gs_ctx* c) {
+  // upload per-level data
+  for (int l = 0; l < c->L; ++l) {
+    Level& lv = c->lv[l];
+    std::vector<float> e32(lv.Nc);
+    for (long long i = 0; i < lv.Nc; ++i) e32[i] = (float)lv.heta[i];
+    CK(cudaMemcpyAsync(lv.eta64, lv.heta.data(), sizeof(double) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(lv.eta32, e32.data(), sizeof(float) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+    if (lv.has_void) {
+      CK(cudaMemcpyAsync(lv.cvoid, lv.hvoid.data(), lv.Nc, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(lv.vmask, lv.hvmask.data(), lv.Nv, cudaMemcpyHostToDevice, c->st));
+      if (lv.pmask) CK(cudaMemcpyAsync(lv.pmask, lv.hpmask.data(), lv.Np, cudaMemcpyHostToDevice, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));  // host staging vectors go out of scope
+  }
+  // coarse inverse: host assembly, device Gauss-Jordan
+  if (c->nf > 0) {
+    std::vector<double> A;
+    assemble_coarse(c, A);
+    CK(cudaMemcpyAsync(c->Ainv, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->cfree, c->hfree.data(), sizeof(int) * c->nf, cudaMemcpyHostToDevice, c->st));
+    for (int k = 0; k < c->nf; ++k) {
+      CK(launch_gj_save(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
+      CK(launch_gj_update(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+  }
+  if (c->fp32) CKS(setup_T<float>(c)); else CKS(setup_T<double>(c));
+  CK(cudaStreamSynchronize(c->st));
+  return GS_OK;
+}
+
+// ---- Chebyshev smoother on level l: result in lv.xA (Sec. 4, Cheb(A, diag(A), k)) -------------
+template <typename T>
+gs_status cheb(gs_ctx* c, int l, const T* b, bool zero_init) {
+  Level& lv = c->lv[l];
+  const double hi = lv.lam_hi, lo = hi / 15.0;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  const int k = c->opt.cheb_degree;
+  T* dinv = (T*)lv.dinv;
+  T* d = (T*)lv.d;
+  if (zero_init) {
+    KL(K_VEC, launch_cheb_init0<T>(b, dinv, (T)(1.0 / theta), d, (T*)lv.xA, lv.nu, c->st));
+  } else {
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = (const T*)lv.xA; a.bu = b; a.d = d; a.dinv = dinv; a.xout = (T*)lv.xB;
+    a.c1 = 0; a.c2 = (T)(1.0 / theta); a.use_d = 0;
+    KL(K_CHEB, launch_tile<T>(c->dim, TILE_CHEB, OPS_A, a, c->st));
+    std::swap(lv.xA, lv.xB);
+  }
+  double rho = 1.0 / sigma;
+  for (int t = 1; t < k; ++t) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = (const T*)lv.xA; a.bu = b; a.d = d; a.dinv = dinv; a.xout = (T*)lv.xB;
+    a.c1 = (T)(rn * rho); a.c2 = (T)(2.0 * rn / delta); a.use_d = 1;
+    KL(K_CHEB, launch_tile<T>(c->dim, TILE_CHEB, OPS_A, a, c->st));
+    std::swap(lv.xA, lv.xB);
+    rho = rn;
+  }
+  return GS_OK;
+}
+
+// V-cycle on level l: input lv.b, output lv.xA
+template <typename T>
+gs_status vcycle(gs_ctx* c, int l) {
+  Level& lv = c->lv[l];
+  if (l == 0) {
+    if (c->opt.coarse_mode == 1) return cheb<T>(c, 0, (const T*)lv.b, true);
+    KL(K_COARSE, launch_coarse_solve<T>(c->Ainv, c->cfree, c->nf, (const T*)lv.b, (T*)lv.xA, lv.nu, c->ctmp, c->st));
+    return GS_OK;
+  }
+  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, s == 0));
+  {
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = (const T*)lv.xA; a.bu = (const T*)lv.b; a.yu = (T*)lv.d;
+    KL(K_RESID, launch_tile<T>(c->dim, TILE_RESID, OPS_A, a, c->st));
+  }
+  Level& cl = c->lv[l - 1];
+  KL(K_TRANSFER, launch_restrict<T>(lv.g, cl.g, (const T*)lv.d, (T*)cl.b, c->st));
+  CKS(vcycle<T>(c, l - 1));
+  KL(K_TRANSFER, launch_prolong_add<T>(lv.g, cl.g, (const T*)cl.xA, (T*)lv.xA, c->st));
+  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, false));
+  return GS_OK;
+}
+
+// S^{-1} b ~ Chebyshev-Jacobi on M_p(1/eta) from zero, Wathen interval: result in c->p_xA
+template <typename T>
+gs_status schur_inv(gs_ctx* c, const T* b) {
+  const Level& F = c->lv[c->L - 1];
+  const double lo = std::pow(0.5, c->dim), hi = std::pow(1.5, c->dim);
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  KL(K_VEC, launch_cheb_init0<T>(b, (const T*)c->p_dinv, (T)(1.0 / theta), (T*)c->p_d, (T*)c->p_xA, F.Np, c->st));
+  double rho = 1.0 / sigma;
+  for (int t = 1; t < c->opt.schur_degree; ++t) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    PMassArgs<T> a{};
+    a.g = F.g; a.c = coef<T>(F); a.eta = etap<T>(F);
+    a.x = (const T*)c->p_xA; a.b = b; a.d = (T*)c->p_d; a.dinv = (const T*)c->p_dinv; a.xout = (T*)c->p_xB;
+    a.c1 = (T)(rn * rho); a.c2 = (T)(2.0 * rn / delta); a.use_d = 1;
+    KL(K_SCHUR, launch_pmass<T>(TILE_CHEB, a, c->st));
+    std::swap(c->p_xA, c->p_xB);
+    rho = rn;
+  }
+  return GS_OK;
+}
+
+gs_status project_pressure(gs_ctx* c, double* x) {
+  if (!c->nullspace) return GS_OK;
+  const Level& F = c->lv[c->L - 1];
+  double* p = x + c->nu;
+  KL(K_VEC, launch_masked_sum_partial(p, F.pmask, F.Np, c->part, c->G, c->st));
+  KL(K_VEC, launch_reduce_partials(c->part, 1, c->G, c->dsc + 3 * (c->opt.restart + 4) , c->st));
+  KL(K_VEC, launch_sub_scalar_masked(p, F.pmask, F.Np, c->dsc + 3 * (c->opt.restart + 4), 1.0 / (double)c->n_pfree, c->st));
+  return GS_OK;
+}
+
+// block upper-triangular preconditioner: z_p = -S^{-1} v_p, z_u = V(v_u - B^T z_p); constrained
+// entries of z copied from v (K is the identity there); pressure mean removed
+template <typename T>
+gs_status precond_T(gs_ctx* c, const double* v, double* z) {
+  Level& F = c->lv[c->L - 1];
+  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)c->p_b, F.Np, (T)1, c->st));
+  CKS(schur_inv<T>(c, (const T*)c->p_b));
+  KL(K_VEC, launch_cast<T, T>((const T*)c->p_xA, (T*)c->p_xB, F.Np, (T)(-1), c->st));  // z_p in p_xB
+  KL(K_VEC, launch_cast<double, T>(v, (T*)F.d, F.nu, (T)1, c->st));
+  {
+    TileArgs<T> a = tile_args<T>(F);
+    a.xp = (const T*)c->p_xB; a.bu = (const T*)F.d; a.yu = (T*)F.b;
+    KL(K_BT, launch_tile<T>(c->dim, TILE_RESID, OPS_BT, a, c->st));
+  }
+  CKS(vcycle<T>(c, c->L - 1));
+  KL(K_VEC, launch_cast<T, double>((const T*)F.xA, z, F.nu, 1.0, c->st));
+  KL(K_VEC, launch_cast<T, double>((const T*)c->p_xB, z + c->nu, F.Np, 1.0, c->st));
+  KL(K_VEC, launch_copy_constrained(v, z, F.g, c->st));
+  CKS(project_pressure(c, z));
+  return GS_OK;
+}
+
+gs_status precond(gs_ctx* c, const double* v, double* z) {
+  return c->fp32 ? precond_T<float>(c, v, z) : precond_T<double>(c, v, z);
+}
+
+// FP64 saddle operator on the finest level: y = K x (APPLY) or y = b - K x (RESID)
+gs_status saddle(gs_ctx* c, int mode, const double* x, double* y, const double* b, int raw = 0) {
+  const Level& F = c->lv[c->L - 1];
+  TileArgs<double> a = tile_args<double>(F);
+  a.xu = x; a.xp = x + c->nu; a.yu = y; a.yp = y + c->nu;
+  a.bu = b; a.bp = b ? b + c->nu : nullptr; a.raw = raw;
+  KL(K_SADDLE64, launch_tile<double>(c->dim, mode, OPS_A | OPS_BT | OPS_B, a, c->st));
+  return GS_OK;
+}
+
+gs_status norm2_host(gs_ctx* c, const double* x, double* out) {
+  return dot_host<double>(c, x, c->N, 1, x, c->N, out);
+}
+
+gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, double* relres) {
+  const long long N = c->N;
+  const int m = c->opt.restart;
+  double bn2;
+  CKS(norm2_host(c, b, &bn2));
+  const double bnorm = std::sqrt(bn2);
+  if (!std::isfinite(bnorm)) return fail(GS_EBREAKDOWN, "right-hand side is not finite");
+  c->last_it = 0;
+  c->last_rel = 0.0;
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * N, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (its) *its = 0;
+    if (relres) *relres = 0.0;
+    return GS_OK;
+  }
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  int it = 0, extra = 0;
+  double* h1 = c->dsc;
+  double* h2 = c->dsc + (m + 4);
+  double* nrm = c->dsc + 2 * (m + 4);
+  gs_status result = GS_OK;
+  double rel = 0.0;
+  for (;;) {
+    CKS(saddle(c, TILE_RESID, x, c->r, b));
+    double beta2;
+    CKS(norm2_host(c, c->r, &beta2));
+    const double beta = std::sqrt(beta2);
+    if (!std::isfinite(beta)) return fail(GS_EBREAKDOWN, "residual is not finite");
+    rel = beta / bnorm;
+    if (rel <= tol) break;
+    if (it >= c->opt.max_iter) { result = GS_ENOCONV; break; }
+    CK(cudaMemcpyAsync(nrm, &beta2, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    KL(K_AXPY, launch_scale_by_rnorm(c->r, nrm, c->V, N, c->st));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    bool converged = false;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = c->V + (long long)j * N;
+      double* Zj = c->Z + (long long)j * N;
+      CKS(precond(c, Vj, Zj));
+      CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
+      // classical Gram-Schmidt, applied twice
+      KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h1, c->st));
+      KL(K_AXPY, launch_multi_axpy(c->V, N, j + 1, h1, -1.0, c->w, N, c->st));
+      KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
+      KL(K_AXPY, launch_multi_axpy(c->V, N, j + 1, h2, -1.0, c->w, N, c->st));
+      KL(K_DOTS, launch_add_vec(h1, h2, j + 1, c->st));
+      KL(K_DOTS, launch_dots_partial<double>(c->w, N, 1, c->w, N, c->part, c->G, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->G, nrm, c->st));
+      CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      for (int i = 0; i <= j; ++i) Hc(i, j) = c->hpin[i];
+      const double hn = std::sqrt(c->hpin[m + 1]);
+      if (!std::isfinite(hn)) return fail(GS_EBREAKDOWN, "Arnoldi vector is not finite");
+      Hc(j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {
+        const double tmp = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+        Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+        Hc(i, j) = tmp;
+      }
+      const double rr = std::hypot(Hc(j, j), Hc(j + 1, j));
+      cs[j] = Hc(j, j) / rr;
+      sn[j] = Hc(j + 1, j) / rr;
+      Hc(j, j) = rr;
+      Hc(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      it++;
+      k = j + 1;
+      if (std::fabs(g[j + 1]) / bnorm <= tol || hn == 0.0) { converged = true; break; }
+      if (it >= c->opt.max_iter) break;
+      KL(K_AXPY, launch_scale_by_rnorm(c->w, nrm, c->V + (long long)(j + 1) * N, N, c->st));
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int q = i + 1; q < k; ++q) s -= Hc(i, q) * y[q];
+      y[i] = s / Hc(i, i);
+    }
+    CK(cudaMemcpyAsync(h1, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, c->st));
+    KL(K_AXPY, launch_multi_axpy(c->Z, N, k, h1, 1.0, x, N, c->st));
+    if (converged) {
+      CKS(saddle(c, TILE_RESID, x, c->r, b));
+      double r2;
+      CKS(norm2_host(c, c->r, &r2));
+      rel = std::sqrt(r2) / bnorm;
+      if (!std::isfinite(rel)) return fail(GS_EBREAKDOWN, "residual is not finite");
+      if (rel <= tol) break;
+      if (extra >= 3) { result = GS_ENOCONV; break; }
+      extra++;
+    } else if (it >= c->opt.max_iter) {
+      CKS(saddle(c, TILE_RESID, x, c->r, b));
+      double r2;
+      CKS(norm2_host(c, c->r, &r2));
+      rel = std::sqrt(r2) / bnorm;
+      result = rel <= tol ? GS_OK : GS_ENOCONV;
+      break;
+    }
+  }
+  CKS(project_pressure(c, x));
+  CK(cudaStreamSynchronize(c->st));
+  c->last_it = it;
+  c->last_rel = rel;
+  if (its) *its = it;
+  if (relres) *relres = rel;
+  if (result == GS_ENOCONV) g_err = "FGMRES did not reach the tolerance";
+  return result;
+}
+
+template <typename T>
+gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, const void* auxv) {
+  Level& lv = c->lv[l];
+  const T* x = (const T*)xv;
+  T* y = (T*)yv;
+  const T* aux = (const T*)auxv;
+  const bool finest = l == c->L - 1;
+  const bool mgprec = (sizeof(T) == 4) == c->fp32;
+  switch (op) {
+    case GS_OP_A:
+    case GS_OP_A_RAW: {
+      TileArgs<T> a = tile_args<T>(lv);
+      a.xu = x; a.yu = y; a.raw = op == GS_OP_A_RAW;
+      CK(launch_tile<T>(c->dim, TILE_APPLY, OPS_A, a, c->st));
+      return GS_OK;
+    }
+    case GS_OP_RESIDUAL_A: {
+      if (!aux) return fail(GS_EINVAL, "residual needs aux = b");
+      TileArgs<T> a = tile_args<T>(lv);
+      a.xu = x; a.yu = y; a.bu = aux;
+      CK(launch_tile<T>(c->dim, TILE_RESID, OPS_A, a, c->st));
+      return GS_OK;
+    }
+    case GS_OP_DIAG_A:
+      CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), y, 0, c->st));
+      return GS_OK;
+    case GS_OP_SMOOTH: {
+      if (!mgprec || (l == 0 && c->opt.coarse_mode != 1))
+        return fail(GS_EINVAL, "smoother: level >= 1 (or level 0 with coarse_mode 1), MG precision");
+      if (aux) CK(cudaMemcpyAsync(lv.xA, aux, sizeof(T) * lv.nu, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(lv.b, x, sizeof(T) * lv.nu, cudaMemcpyDeviceToDevice, c->st));
+      for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, s == 0 && !aux));
+      CK(cudaMemcpyAsync(y, lv.xA, sizeof(T) * lv.nu, cudaMemcpyDeviceToDevice, c->st));
+      return GS_OK;
+    }
+    case GS_OP_RESTRICT:
+      if (l == 0) return fail(GS_EINVAL, "restriction needs level >= 1");
+      CK(launch_restrict<T>(lv.g, c->lv[l - 1].g, x, y, c->st));
+      return GS_OK;
+    case GS_OP_PROLONGATE:
+      if (l == 0) return fail(GS_EINVAL, "prolongation needs level >= 1");
+      CK(launch_prolong_add<T>(lv.g, c->lv[l - 1].g, x, y, c->st));
+      return GS_OK;
+    case GS_OP_B:
+    case GS_OP_BT: {
+      if (!finest) return fail(GS_EINVAL, "B / B^T on the finest level only");
+      TileArgs<T> a = tile_args<T>(lv);
+      if (op == GS_OP_B) { a.xu = x; a.yp = y; } else { a.xp = x; a.yu = y; }
+      CK(launch_tile<T>(c->dim, TILE_APPLY, op == GS_OP_B ? OPS_B : OPS_BT, a, c->st));
+      return GS_OK;
+    }
+    case GS_OP_SCHUR_MASS: {
+      if (!finest) return fail(GS_EINVAL, "Schur mass on the finest level only");
+      PMassArgs<T> a{};
+      a.g = lv.g; a.c = coef<T>(lv); a.eta = etap<T>(lv); a.x = x; a.y = y;
+      CK(launch_pmass<T>(TILE_APPLY, a, c->st));
+      return GS_OK;
+    }
+    case GS_OP_SCHUR_INV: {
+      if (!finest || !mgprec) return fail(GS_EINVAL, "Schur inverse: finest level, MG precision");
+      CKS(schur_inv<T>(c, x));
+      CK(cudaMemcpyAsync(y, c->p_xA, sizeof(T) * lv.Np, cudaMemcpyDeviceToDevice, c->st));
+      return GS_OK;
+    }
+    default:
+      return fail(GS_EINVAL, "unknown operator");
+  }
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+size_t gs_footprint_bytes(const gs_mesh* mesh, int levels, const gs_options* opts) {
+  gs_ctx c;
+  c.opt = normalize_opts(opts);
+  c.fp32 = c.opt.mg_precision == 32;
+  if (plan(mesh, levels, nullptr, &c) != GS_OK) return 0;
+  Arena ar;
+  layout(&c, ar);
+  return c.footprint;
+}
+
+gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell, double alpha,
+                    const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
+                    gs_ctx** out) {
+  if (!out) return fail(GS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!eta_per_cell) return fail(GS_EINVAL, "eta_per_cell is NULL");
+  if (!(alpha >= 0.0) || !std::isfinite(alpha)) return fail(GS_EINVAL, "alpha must be finite and >= 0");
+  if (!workspace) return fail(GS_EINVAL, "workspace is NULL");
+  if (((uintptr_t)workspace & 255u) != 0) return fail(GS_EINVAL, "workspace must be 256-byte aligned");
+  gs_ctx* c = new gs_ctx();
+  c->opt = normalize_opts(opts);
+  c->fp32 = c->opt.mg_precision == 32;
+  c->alpha = alpha;
+  c->st = (cudaStream_t)stream;
+  gs_status s = plan(mesh, levels, eta_per_cell, c);
+  if (s != GS_OK) { delete c; return s; }
+  {
+    Arena dry;
+    layout(c, dry);
+  }
+  if (workspace_bytes < c->footprint) {
+    delete c;
+    return fail(GS_ENOMEM, "workspace smaller than gs_footprint_bytes()");
+  }
+  Arena ar;
+  ar.base = (char*)workspace;
+  layout(c, ar);
+  set_geom(c, mesh);
+  cudaError_t e = cudaMallocHost(&c->hpin, sizeof(double) * (c->opt.restart + 8));
+  if (e != cudaSuccess) { delete c; return fail(GS_ECUDA, std::string("pinned buffer: ") + cudaGetErrorString(e)); }
+  s = setup(c);
+  if (s != GS_OK) { cudaFreeHost(c->hpin); delete c; return s; }
+  *out = c;
+  return GS_OK;
+}
+
+gs_status gs_vmult(gs_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(GS_EINVAL, "NULL argument");
+  if (x == y) return fail(GS_EINVAL, "x and y must not alias");
+  return saddle(c, TILE_APPLY, x, y, nullptr);
+}
+
+gs_status gs_vmult_A(gs_ctx* c, const void* x, void* y, int fp32) {
+  if (!c || !x || !y) return fail(GS_EINVAL, "NULL argument");
+  if (x == y) return fail(GS_EINVAL, "x and y must not alias");
+  return fp32 ? apply_level_T<float>(c, c->L - 1, GS_OP_A, x, y, nullptr)
+              : apply_level_T<double>(c, c->L - 1, GS_OP_A, x, y, nullptr);
+}
+
+gs_status gs_vcycle(gs_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z) return fail(GS_EINVAL, "NULL argument");
+  Level& F = c->lv[c->L - 1];
+  if (c->fp32) {
+    CK(launch_cast<double, float>(r, (float*)F.b, F.nu, 1.0f, c->st));
+    CKS(vcycle<float>(c, c->L - 1));
+    CK(launch_cast<float, double>((const float*)F.xA, z, F.nu, 1.0, c->st));
+  } else {
+    CK(cudaMemcpyAsync(F.b, r, sizeof(double) * F.nu, cudaMemcpyDeviceToDevice, c->st));
+    CKS(vcycle<double>(c, c->L - 1));
+    CK(cudaMemcpyAsync(z, F.xA, sizeof(double) * F.nu, cudaMemcpyDeviceToDevice, c->st));
+  }
+  return GS_OK;
+}
+
+gs_status gs_solve(gs_ctx* c, const double* rhs, double* x, double tol, int* iterations, double* rel_residual) {
+  if (!c || !rhs || !x) return fail(GS_EINVAL, "NULL argument");
+  if (!(tol > 0.0)) return fail(GS_EINVAL, "tol must be > 0");
+  return fgmres(c, rhs, x, tol, iterations, rel_residual);
+}
+
+gs_status gs_lift_rhs(gs_ctx* c, const double* f, const double* g, double* rhs) {
+  if (!c || !f || !g || !rhs) return fail(GS_EINVAL, "NULL argument");
+  if (rhs == f || rhs == g) return fail(GS_EINVAL, "rhs must not alias f or g");
+  Level& F = c->lv[c->L - 1];
+  // M f: velocity mass (alpha = 1, no viscous part) and plain Q1 pressure mass, unconstrained
+  {
+    TileArgs<double> a = tile_args<double>(F);
+    a.c = make_coef<double>(c->dim, F.h, 1.0);
+    a.c.eta_scale = 0.0;
+    a.xu = f; a.yu = c->t1; a.raw = 1;
+    CK(launch_tile<double>(c->dim, TILE_APPLY, OPS_A, a, c->st));
+    PMassArgs<double> p{};
+    p.g = F.g; p.c = F.c64; p.eta = F.eta64; p.x = f + c->nu; p.y = c->t1 + c->nu; p.raw = 1; p.unit = 1;
+    CK(launch_pmass<double>(TILE_APPLY, p, c->st));
+  }
+  // K_raw applied to the Dirichlet data (g restricted to the constrained entries)
+  CK(cudaMemsetAsync(c->w, 0, sizeof(double) * c->N, c->st));
+  CK(launch_copy_constrained(g, c->w, F.g, c->st));
+  CKS(saddle(c, TILE_APPLY, c->w, c->t2, nullptr, 1));
+  CK(launch_combine_lift(c->t1, c->t2, g, F.vmask, F.pmask, F.g, rhs, c->st));
+  return GS_OK;
+}
+
+gs_status gs_batch_solve(gs_ctx* const* ctxs, int count, const double* const* rhs, double* const* x, double tol,
+                         int* iterations, double* rel_residuals) {
+  if (!ctxs || !rhs || !x || count < 0) return fail(GS_EINVAL, "NULL argument");
+  gs_status first = GS_OK;
+  for (int i = 0; i < count; ++i) {
+    int it = 0;
+    double rr = 0.0;
+    gs_status s = gs_solve(ctxs[i], rhs[i], x[i], tol, &it, &rr);
+    if (iterations) iterations[i] = it;
+    if (rel_residuals) rel_residuals[i] = rr;
+    if (s != GS_OK && first == GS_OK) first = s;
+  }
+  return first;
+}
+
+gs_status gs_apply_level(gs_ctx* c, int level, gs_op op, int prec, const void* x, void* y, const void* aux) {
+  if (!c || !y) return fail(GS_EINVAL, "NULL argument");
+  if (level < 0 || level >= c->L) return fail(GS_EINVAL, "level out of range");
+  if (op == GS_OP_COARSE) {
+    if (level != 0 || !x || c->nf == 0) return fail(GS_EINVAL, "coarse solve: level 0, x required, coarse_mode 0");
+    CK(launch_coarse_solve<double>(c->Ainv, c->cfree, c->nf, (const double*)x, (double*)y, c->lv[0].nu, c->ctmp, c->st));
+    return GS_OK;
+  }
+  if (op == GS_OP_PRECOND) {
+    if (level != c->L - 1 || !x) return fail(GS_EINVAL, "preconditioner: finest level, x required");
+    return precond(c, (const double*)x, (double*)y);
+  }
+  if (!x && op != GS_OP_DIAG_A) return fail(GS_EINVAL, "x is NULL");
+  if (prec == 32) return apply_level_T<float>(c, level, op, x, y, aux);
+  if (prec == 64) return apply_level_T<double>(c, level, op, x, y, aux);
+  return fail(GS_EINVAL, "prec must be 32 or 64");
+}
+
+gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
+  if (!c || !out) return fail(GS_EINVAL, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->levels = c->L;
+  out->dim = c->dim;
+  out->n_total = c->N;
+  out->n_u = c->nu;
+  out->n_p = c->np;
+  out->pressure_nullspace = c->nullspace ? 1 : 0;
+  out->last_iterations = c->last_it;
+  out->last_rel_residual = c->last_rel;
+  for (int l = 0; l < c->L && l < 16; ++l) {
+    out->lambda_max[l] = c->lv[l].lam_hi;
+    out->level_n_u[l] = c->lv[l].nu;
+  }
+  out->coarse_free = c->nf;
+  out->footprint_bytes = c->footprint;
+  out->kernel_launches = launches_total();
+  return GS_OK;
+}
+
+gs_status gs_profile(gs_ctx* c, int enable) {
+  if (!c) return fail(GS_EINVAL, "NULL argument");
+  if (enable) {
+    CK(cudaStreamSynchronize(c->st));
+    c->recs.clear();
+    c->ev_used = 0;
+  }
+  c->prof = enable != 0;
+  return GS_OK;
+}
+
+int gs_profile_read(gs_ctx* c, gs_kernel_stat* out, int max) {
+  if (!c || !out || max <= 0) return 0;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return 0;
+  double ms[K_NCLASS] = {0};
+  long long cnt[K_NCLASS] = {0};
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->evs[r.second], c->evs[r.second + 1]) == cudaSuccess) {
+      ms[r.first] += t;
+      cnt[r.first] += 1;
+    }
+  }
+  int n = 0;
+  for (int k = 0; k < K_NCLASS && n < max; ++k) {
+    out[n].name = kclass_name[k];
+    out[n].launches = cnt[k];
+    out[n].total_ms = ms[k];
+    ++n;
+  }
+  return n;
+}
+
+gs_status gs_set_stream(gs_ctx* c, void* stream) {
+  if (!c) return fail(GS_EINVAL, "NULL argument");
+  c->st = (cudaStream_t)stream;
+  return GS_OK;
+}
+
+void gs_destroy(gs_ctx* c) {
+  if (!c) return;
+  for (auto e : c->evs) cudaEventDestroy(e);
+  if (c->hpin) cudaFreeHost(c->hpin);
+  delete c;
+}
+
+const char* gs_strerror(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_EINVAL: return "invalid argument";
+    case GS_ENOMEM: return "workspace too small";
+    case GS_ECUDA: return "CUDA error";
+    case GS_ENOCONV: return "no convergence";
+    case GS_EBREAKDOWN: return "breakdown (non-finite values)";
+    case GS_ETIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+const char* gs_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,342 @@
+// Vector kernels of the Krylov / multigrid path: casts, Chebyshev start, Lanczos helpers,
+// deterministic multi-dot reductions (FGMRES Gram-Schmidt, Sec. 5), multi-axpy updates,
+// pressure-mean projection, lifting, and the dense FP64 coarse solve.
+#include <atomic>
+
+#include "gs_kernels.h"
+
+namespace gs {
+
+static std::atomic<long long> g_launches{0};
+cudaError_t launched(cudaError_t e, int kernels) {
+  if (e == cudaSuccess) g_launches.fetch_add(kernels, std::memory_order_relaxed);
+  return e;
+}
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+constexpr int TPB = 256;
+inline unsigned nblk(long long n) {
+  long long b = (n + TPB - 1) / TPB;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// deterministic block sum (fixed tree); result valid in thread 0
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (wid == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+}  // namespace
+
+template <typename T>
+__global__ void k_cheb_init0(const T* __restrict__ b, const T* __restrict__ dinv, T inv_theta,
+                             T* __restrict__ d, T* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T v = dinv[i] * b[i] * inv_theta;
+    d[i] = v;
+    x[i] = v;
+  }
+}
+template <typename T>
+cudaError_t launch_cheb_init0(const T* b, const T* dinv, T inv_theta, T* d, T* x, long long n, cudaStream_t st) {
+  k_cheb_init0<T><<<nblk(n), TPB, 0, st>>>(b, dinv, inv_theta, d, x, n);
+  return launched(cudaGetLastError());
+}
+
+template <typename TI, typename TO>
+__global__ void k_cast(const TI* in, TO* out, long long n, TO scale) {  // may run in place
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = scale * (TO)in[i];
+}
+template <typename TI, typename TO>
+cudaError_t launch_cast(const TI* in, TO* out, long long n, TO scale, cudaStream_t st) {
+  k_cast<TI, TO><<<nblk(n), TPB, 0, st>>>(in, out, n, scale);
+  return launched(cudaGetLastError());
+}
+
+template <typename T>
+__global__ void k_zero_constrained_u(const Geom g, T* v) {
+  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= g.Nv) return;
+  const int I = (int)(node % g.nv[0]);
+  const int J = (int)((node / g.nv[0]) % g.nv[1]);
+  const int K = g.dim == 3 ? (int)(node / ((long long)g.nv[0] * g.nv[1])) : 0;
+  if (vnode_constrained(g, node, I, J, K))
+    for (int a = 0; a < g.dim; ++a) v[a * g.Nv + node] = T(0);
+}
+template <typename T>
+cudaError_t launch_zero_constrained_u(const Geom& g, T* v, cudaStream_t st) {
+  k_zero_constrained_u<T><<<nblk(g.Nv), TPB, 0, st>>>(g, v);
+  return launched(cudaGetLastError());
+}
+
+// Lanczos on S = D^{-1/2} A D^{-1/2}:  t = sqrt(dinv) v ;  w = sqrt(dinv) (A t) - beta v_prev
+template <typename T>
+__global__ void k_lanczos_pre(const T* __restrict__ dinv, const T* __restrict__ v, T* __restrict__ t, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    t[i] = sqrt(dinv[i]) * v[i];
+}
+template <typename T>
+__global__ void k_lanczos_post(const T* __restrict__ dinv, const T* y, const T* __restrict__ vprev,
+                               T beta_prev, T* w, long long n) {  // y and w may alias
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    w[i] = sqrt(dinv[i]) * y[i] - beta_prev * vprev[i];
+}
+template <typename T>
+cudaError_t launch_lanczos_pre(const T* dinv, const T* v, T* t, long long n, cudaStream_t st) {
+  k_lanczos_pre<T><<<nblk(n), TPB, 0, st>>>(dinv, v, t, n);
+  return launched(cudaGetLastError());
+}
+template <typename T>
+cudaError_t launch_lanczos_post(const T* dinv, const T* y, const T* vprev, T beta_prev, T* w, long long n,
+                                cudaStream_t st) {
+  k_lanczos_post<T><<<nblk(n), TPB, 0, st>>>(dinv, y, vprev, beta_prev, w, n);
+  return launched(cudaGetLastError());
+}
+
+// ---- multi-dot: part[i*G + blk] = sum_{e in chunk(blk)} V[i][e] w[e] ------------------------------
+template <typename T>
+__global__ void k_dots_partial(const T* __restrict__ V, long long ldv, int k, const T* __restrict__ w,
+                               long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long lo = blockIdx.x * chunk;
+  const long long hi = min(n, lo + chunk);
+  for (int i = 0; i < k; ++i) {
+    const T* v = V + i * ldv;
+    double s = 0.0;
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s += (double)v[e] * (double)w[e];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = s;
+  }
+}
+template <typename T>
+cudaError_t launch_dots_partial(const T* V, long long ldv, int k, const T* w, long long n, double* part, int G,
+                                cudaStream_t st) {
+  k_dots_partial<T><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part);
+  return launched(cudaGetLastError());
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ part, int G, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[(long long)i * G + b];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[i] = s;
+}
+cudaError_t launch_reduce_partials(const double* part, int k, int G, double* out, cudaStream_t st) {
+  k_reduce_partials<<<k, TPB, 0, st>>>(part, G, out);
+  return launched(cudaGetLastError());
+}
+
+__global__ void k_multi_axpy(const double* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
+                             double sign, double* __restrict__ w, long long n) {
+  extern __shared__ double cs[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = sign * coef[i];
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double acc = w[e];
+    for (int i = 0; i < k; ++i) acc += cs[i] * V[i * ldv + e];
+    w[e] = acc;
+  }
+}
+cudaError_t launch_multi_axpy(const double* V, long long ldv, int k, const double* coef, double sign, double* w,
+                              long long n, cudaStream_t st) {
+  unsigned g = nblk(n);
+  if (g > 152u * 16u) g = 152u * 16u;
+  k_multi_axpy<<<g, TPB, sizeof(double) * (k > 0 ? k : 1), st>>>(V, ldv, k, coef, sign, w, n);
+  return launched(cudaGetLastError());
+}
+
+__global__ void k_scale_by_rnorm(const double* __restrict__ w, const double* __restrict__ nrm2,
+                                 double* __restrict__ v, long long n) {
+  const double s = 1.0 / sqrt(nrm2[0]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] = w[i] * s;
+}
+cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, long long n, cudaStream_t st) {
+  unsigned g = nblk(n);
+  if (g > 152u * 16u) g = 152u * 16u;
+  k_scale_by_rnorm<<<g, TPB, 0, st>>>(w, nrm2, v, n);
+  return launched(cudaGetLastError());
+}
+
+__global__ void k_add_vec(double* a, const double* b, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) a[i] += b[i];
+}
+cudaError_t launch_add_vec(double* a, const double* b, int k, cudaStream_t st) {
+  k_add_vec<<<(k + 63) / 64, 64, 0, st>>>(a, b, k);
+  return launched(cudaGetLastError());
+}
+
+__global__ void k_masked_sum_partial(const double* __restrict__ x, const uint8_t* __restrict__ mask, long long n,
+                                     double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    if (!mask || !mask[e]) s += x[e];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+cudaError_t launch_masked_sum_partial(const double* x, const uint8_t* mask, long long n, double* part, int G,
+                                      cudaStream_t st) {
+  k_masked_sum_partial<<<G, TPB, 0, st>>>(x, mask, n, part);
+  return launched(cudaGetLastError());
+}
+__global__ void k_sub_scalar_masked(double* __restrict__ x, const uint8_t* __restrict__ mask, long long n,
+                                    const double* __restrict__ sum, double inv_count) {
+  const double m = sum[0] * inv_count;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    if (!mask || !mask[e]) x[e] -= m;
+}
+cudaError_t launch_sub_scalar_masked(double* x, const uint8_t* mask, long long n, const double* sum,
+                                     double inv_count, cudaStream_t st) {
+  k_sub_scalar_masked<<<nblk(n), TPB, 0, st>>>(x, mask, n, sum, inv_count);
+  return launched(cudaGetLastError());
+}
+
+// ---- dense coarse solve (explicit inverse of A_0 on its free unknowns) ------------------------------
+template <typename T>
+__global__ void k_coarse_gather(const T* __restrict__ b, const int* __restrict__ freeidx, int nf, double* __restrict__ tmp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nf) tmp[i] = (double)b[freeidx[i]];
+}
+template <typename T>
+__global__ void k_coarse_gemv(const double* __restrict__ Ainv, const int* __restrict__ freeidx, int nf,
+                              const double* __restrict__ tmp, T* __restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nf) return;
+  const double* row = Ainv + (long long)warp * nf;
+  double s = 0.0;
+  for (int j = lane; j < nf; j += 32) s += row[j] * tmp[j];
+  s = warp_sum(s);
+  if (lane == 0) y[freeidx[warp]] = (T)s;
+}
+template <typename T>
+__global__ void k_zero(T* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = T(0);
+}
+template <typename T>
+cudaError_t launch_coarse_solve(const double* Ainv, const int* freeidx, int nf, const T* b, T* y, long long n,
+                                double* tmp, cudaStream_t st) {
+  k_coarse_gather<T><<<(nf + TPB - 1) / TPB, TPB, 0, st>>>(b, freeidx, nf, tmp);
+  k_zero<T><<<nblk(n), TPB, 0, st>>>(y, n);
+  k_coarse_gemv<T><<<(unsigned)(((long long)nf * 32 + TPB - 1) / TPB), TPB, 0, st>>>(Ainv, freeidx, nf, tmp, y);
+  return launched(cudaGetLastError(), 3);
+}
+
+// Gauss-Jordan inversion of an SPD matrix (no pivoting), one pivot per pair of launches.
+__global__ void k_gj_save(const double* __restrict__ A, int n, int k, double* __restrict__ row, double* __restrict__ col) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    row[i] = A[(long long)k * n + i];
+    col[i] = A[(long long)i * n + k];
+  }
+}
+__global__ void k_gj_update(double* __restrict__ A, int n, int k, const double* __restrict__ row,
+                            const double* __restrict__ col) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  const double p = row[k];
+  double v;
+  if (i == k && j == k) v = 1.0 / p;
+  else if (i == k) v = row[j] / p;
+  else if (j == k) v = -col[i] / p;
+  else v = A[idx] - col[i] * row[j] / p;
+  A[idx] = v;
+}
+cudaError_t launch_gj_save(const double* A, int n, int k, double* row, double* col, cudaStream_t st) {
+  k_gj_save<<<(n + TPB - 1) / TPB, TPB, 0, st>>>(A, n, k, row, col);
+  return launched(cudaGetLastError());
+}
+cudaError_t launch_gj_update(double* A, int n, int k, const double* row, const double* col, cudaStream_t st) {
+  k_gj_update<<<nblk((long long)n * n), TPB, 0, st>>>(A, n, k, row, col);
+  return launched(cudaGetLastError());
+}
+
+template <typename T>
+__global__ void k_axpby(const T* __restrict__ x, T* __restrict__ y, T a, T b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+template <typename T>
+cudaError_t launch_axpby(const T* x, T* y, T a, T b, long long n, cudaStream_t st) {
+  k_axpby<T><<<nblk(n), TPB, 0, st>>>(x, y, a, b, n);
+  return launched(cudaGetLastError());
+}
+
+__device__ __forceinline__ bool full_constrained(const Geom& geo, long long i) {
+  const long long n_u = geo.dim * geo.Nv;
+  if (i < n_u) {
+    const long long node = i % geo.Nv;
+    const int I = (int)(node % geo.nv[0]);
+    const int J = (int)((node / geo.nv[0]) % geo.nv[1]);
+    const int K = geo.dim == 3 ? (int)(node / ((long long)geo.nv[0] * geo.nv[1])) : 0;
+    return geo.vmask ? geo.vmask[node] != 0 : face_constrained(geo, I, J, K);
+  }
+  return geo.pmask ? geo.pmask[i - n_u] != 0 : false;
+}
+
+__global__ void k_copy_constrained(const double* __restrict__ v, double* __restrict__ z, const Geom geo) {
+  const long long N = geo.dim * geo.Nv + geo.Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    if (full_constrained(geo, i)) z[i] = v[i];
+}
+cudaError_t launch_copy_constrained(const double* v, double* z, const Geom& geo, cudaStream_t st) {
+  const long long N = geo.dim * geo.Nv + geo.Np;
+  k_copy_constrained<<<nblk(N), TPB, 0, st>>>(v, z, geo);
+  return launched(cudaGetLastError());
+}
+
+// rhs = Mf - Kg on free entries, g on constrained entries (velocity then pressure)
+__global__ void k_combine_lift(const double* __restrict__ Mf, const double* __restrict__ Kg,
+                               const double* __restrict__ g, const Geom geo, double* __restrict__ rhs) {
+  const long long N = geo.dim * geo.Nv + geo.Np;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    rhs[i] = full_constrained(geo, i) ? g[i] : Mf[i] - Kg[i];
+  }
+}
+cudaError_t launch_combine_lift(const double* Mf, const double* Kg, const double* g, const uint8_t*, const uint8_t*,
+                                const Geom& geo, double* rhs, cudaStream_t st) {
+  const long long N = geo.dim * geo.Nv + geo.Np;
+  k_combine_lift<<<nblk(N), TPB, 0, st>>>(Mf, Kg, g, geo, rhs);
+  return launched(cudaGetLastError());
+}
+
+#define INST(T)                                                                                       \
+  template cudaError_t launch_cheb_init0<T>(const T*, const T*, T, T*, T*, long long, cudaStream_t); \
+  template cudaError_t launch_zero_constrained_u<T>(const Geom&, T*, cudaStream_t);                   \
+  template cudaError_t launch_lanczos_pre<T>(const T*, const T*, T*, long long, cudaStream_t);        \
+  template cudaError_t launch_lanczos_post<T>(const T*, const T*, const T*, T, T*, long long, cudaStream_t); \
+  template cudaError_t launch_dots_partial<T>(const T*, long long, int, const T*, long long, double*, int, cudaStream_t); \
+  template cudaError_t launch_axpby<T>(const T*, T*, T, T, long long, cudaStream_t);                 \
+  template cudaError_t launch_coarse_solve<T>(const double*, const int*, int, const T*, T*, long long, double*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+template cudaError_t launch_cast<double, float>(const double*, float*, long long, float, cudaStream_t);
+template cudaError_t launch_cast<float, double>(const float*, double*, long long, double, cudaStream_t);
+template cudaError_t launch_cast<double, double>(const double*, double*, long long, double, cudaStream_t);
+template cudaError_t launch_cast<float, float>(const float*, float*, long long, float, cudaStream_t);
+
+}  // namespace gs

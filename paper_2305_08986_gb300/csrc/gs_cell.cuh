@@ -1,0 +1,294 @@
+// Cell-level operators of the Q2-Q1 generalized Stokes system on Cartesian cells.
+//
+// On a Cartesian cell every term of the bilinear forms a(u, v) (Sec. 3.1.2, Eq. "form_a_j",
+// with the stress factor 2 eta eps) and b(u, q) (Eq. "form_b") is a Kronecker product of 1D
+// matrices, so the cell operators are applied by sweeps of 3x3 (or 2x3) matrices along one
+// axis at a time ("sum factorisation" of Kronbichler-Kormann matrix-free operators, Sec. 4).
+// The 1D matrices are exact rationals; they are stored here as small integers, and the
+// denominators and mesh widths live in the level coefficients OpCoef:
+//
+//   Mi/30  = int_0^1 phi_i phi_j          Mi = [4 2 -1; 2 16 2; -1 2 4]
+//   Ki/3   = int_0^1 phi_i' phi_j'        Ki = [7 -8 1; -8 16 -8; 1 -8 7]
+//   Ei/6   = int_0^1 phi_i' phi_j         Ei = [-3 -4 1; 4 0 -4; -1 4 3]   (test derivative)
+//   Ni/6   = int_0^1 psi_a phi_b          Ni = [1 2 0; 0 2 1]
+//   Gi/6   = int_0^1 psi_a phi_b'         Gi = [-5 4 1; -1 -4 5]
+//   Pi/6   = int_0^1 psi_a psi_b          Pi = [2 1; 1 2]
+//
+// with phi the Q2 Lagrange basis on nodes {0, 1/2, 1} and psi the Q1 basis on {0, 1}.
+// Local arrays are indexed a + 3 b (+ 9 c) (x fastest), Q1 arrays a + 2 b (+ 4 c).
+#pragma once
+#include "gs_common.cuh"
+
+namespace gs {
+
+// ---- 1D line operators ----------------------------------------------------------------------
+struct OpM {
+  static constexpr int NIN = 3, NOUT = 3;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = T(4) * a[0] + T(2) * a[1] - a[2];
+    o[1] = T(2) * (a[0] + a[2]) + T(16) * a[1];
+    o[2] = -a[0] + T(2) * a[1] + T(4) * a[2];
+  }
+};
+struct OpK {
+  static constexpr int NIN = 3, NOUT = 3;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = T(7) * a[0] - T(8) * a[1] + a[2];
+    o[1] = T(-8) * (a[0] + a[2]) + T(16) * a[1];
+    o[2] = a[0] - T(8) * a[1] + T(7) * a[2];
+  }
+};
+struct OpE {  // Ei
+  static constexpr int NIN = 3, NOUT = 3;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = T(-3) * a[0] - T(4) * a[1] + a[2];
+    o[1] = T(4) * (a[0] - a[2]);
+    o[2] = -a[0] + T(4) * a[1] + T(3) * a[2];
+  }
+};
+struct OpET {  // Ei^T
+  static constexpr int NIN = 3, NOUT = 3;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = T(-3) * a[0] + T(4) * a[1] - a[2];
+    o[1] = T(-4) * (a[0] - a[2]);
+    o[2] = a[0] - T(4) * a[1] + T(3) * a[2];
+  }
+};
+struct OpN {  // Ni: 3 -> 2
+  static constexpr int NIN = 3, NOUT = 2;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = a[0] + T(2) * a[1];
+    o[1] = T(2) * a[1] + a[2];
+  }
+};
+struct OpG {  // Gi: 3 -> 2
+  static constexpr int NIN = 3, NOUT = 2;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = T(-5) * a[0] + T(4) * a[1] + a[2];
+    o[1] = -a[0] - T(4) * a[1] + T(5) * a[2];
+  }
+};
+struct OpNT {  // Ni^T: 2 -> 3
+  static constexpr int NIN = 2, NOUT = 3;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = a[0];
+    o[1] = T(2) * (a[0] + a[1]);
+    o[2] = a[1];
+  }
+};
+struct OpGT {  // Gi^T: 2 -> 3
+  static constexpr int NIN = 2, NOUT = 3;
+  template <typename T> __device__ __forceinline__ static void f(const T* a, T* o) {
+    o[0] = T(-5) * a[0] - a[1];
+    o[1] = T(4) * (a[0] - a[1]);
+    o[2] = a[0] + T(5) * a[1];
+  }
+};
+
+// Apply a line operator along axis AX of an array with extents (E0, E1, E2); the output has
+// extent Op::NOUT along AX.  ACC: add into out instead of overwriting.
+template <class Op, int AX, int E0, int E1, int E2, bool ACC, typename T>
+__device__ __forceinline__ void sweep(const T* __restrict__ in, T* __restrict__ out) {
+  constexpr int O0 = AX == 0 ? Op::NOUT : E0;
+  constexpr int O1 = AX == 1 ? Op::NOUT : E1;
+  constexpr int L0 = AX == 0 ? 1 : E0;
+  constexpr int L1 = AX == 1 ? 1 : E1;
+  constexpr int L2 = AX == 2 ? 1 : E2;
+#pragma unroll
+  for (int k = 0; k < L2; ++k) {
+#pragma unroll
+    for (int j = 0; j < L1; ++j) {
+#pragma unroll
+      for (int i = 0; i < L0; ++i) {
+        T a[Op::NIN], o[Op::NOUT];
+#pragma unroll
+        for (int t = 0; t < Op::NIN; ++t) {
+          const int ii = AX == 0 ? t : i, jj = AX == 1 ? t : j, kk = AX == 2 ? t : k;
+          a[t] = in[ii + E0 * (jj + E1 * kk)];
+        }
+        Op::f(a, o);
+#pragma unroll
+        for (int t = 0; t < Op::NOUT; ++t) {
+          const int ii = AX == 0 ? t : i, jj = AX == 1 ? t : j, kk = AX == 2 ? t : k;
+          if (ACC)
+            out[ii + O0 * (jj + O1 * kk)] += o[t];
+          else
+            out[ii + O0 * (jj + O1 * kk)] = o[t];
+        }
+      }
+    }
+  }
+}
+
+// ---- viscous + mass block -------------------------------------------------------------------
+// y_a = sum_b A_ab^K x_b for one output component a ("comp"), with A^K the cell block of
+// alpha (phi_i, phi_j) delta_ab + eta_K (2 eps(phi_j e_b), eps(phi_i e_a)).  Writes y (not +=).
+//
+// Diagonal block (true 1D matrices M, K):  alpha MMM + eta (1+[a=x]) KMM + eta (1+[a=y]) MKM
+//   + eta (1+[a=z]) MMK;  off-diagonal blocks: eta (E in direction b) (E^T in direction a)
+//   (M in the third direction).
+template <typename T>
+__device__ __forceinline__ void cell_A2(int comp, const T (&x)[2][9], T (&y)[9], T eta,
+                                        const OpCoef<T>& c) {
+  T a[9], k[9], p[9], q[9];
+  sweep<OpM, 1, 3, 3, 1, false>(x[comp], a);
+  sweep<OpK, 1, 3, 3, 1, false>(x[comp], k);
+  const T ck = (comp == 1 ? T(2) : T(1)) * eta * c.km[1];
+  const T cq = (comp == 0 ? T(2) : T(1)) * eta * c.km[0];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    p[i] = c.mm * a[i] + ck * k[i];
+    q[i] = cq * a[i];
+  }
+  sweep<OpM, 0, 3, 3, 1, false>(p, y);
+  sweep<OpK, 0, 3, 3, 1, true>(q, y);
+  const T ce = eta * c.ex[0];
+  if (comp == 0) {
+    sweep<OpE, 1, 3, 3, 1, false>(x[1], a);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a[i] *= ce;
+    sweep<OpET, 0, 3, 3, 1, true>(a, y);
+  } else {
+    sweep<OpET, 1, 3, 3, 1, false>(x[0], a);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a[i] *= ce;
+    sweep<OpE, 0, 3, 3, 1, true>(a, y);
+  }
+}
+
+template <typename T, int COMP>
+__device__ __forceinline__ void cell_A3(const T (&x)[3][27], T (&y)[27], T eta, const OpCoef<T>& c) {
+  T a[27], k[27], b[27];
+  // diagonal block
+  sweep<OpM, 2, 3, 3, 3, false>(x[COMP], a);
+  sweep<OpK, 2, 3, 3, 3, false>(x[COMP], k);
+  {
+    const T ckz = (COMP == 2 ? T(2) : T(1)) * eta * c.km[2];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) b[i] = c.mm * a[i] + ckz * k[i];
+  }
+  // k <- My b + cky Ky a
+  sweep<OpM, 1, 3, 3, 3, false>(b, k);
+  sweep<OpK, 1, 3, 3, 3, false>(a, b);
+  {
+    const T cky = (COMP == 1 ? T(2) : T(1)) * eta * c.km[1];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] += cky * b[i];
+  }
+  // b <- ckx My a
+  sweep<OpM, 1, 3, 3, 3, false>(a, b);
+  {
+    const T ckx = (COMP == 0 ? T(2) : T(1)) * eta * c.km[0];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) b[i] *= ckx;
+  }
+  sweep<OpM, 0, 3, 3, 3, false>(k, y);
+  sweep<OpK, 0, 3, 3, 3, true>(b, y);
+  // off-diagonal blocks; the direction of the output component is applied last
+  if (COMP == 0) {
+    sweep<OpM, 2, 3, 3, 3, false>(x[1], a);
+    sweep<OpE, 1, 3, 3, 3, false>(a, k);
+    sweep<OpE, 2, 3, 3, 3, false>(x[2], a);
+    sweep<OpM, 1, 3, 3, 3, false>(a, b);
+    const T c1 = eta * c.ex[2], c2 = eta * c.ex[1];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
+    sweep<OpET, 0, 3, 3, 3, true>(k, y);
+  } else if (COMP == 1) {
+    sweep<OpM, 2, 3, 3, 3, false>(x[0], a);
+    sweep<OpE, 0, 3, 3, 3, false>(a, k);
+    sweep<OpE, 2, 3, 3, 3, false>(x[2], a);
+    sweep<OpM, 0, 3, 3, 3, false>(a, b);
+    const T c1 = eta * c.ex[2], c2 = eta * c.ex[0];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
+    sweep<OpET, 1, 3, 3, 3, true>(k, y);
+  } else {
+    sweep<OpM, 1, 3, 3, 3, false>(x[0], a);
+    sweep<OpE, 0, 3, 3, 3, false>(a, k);
+    sweep<OpE, 1, 3, 3, 3, false>(x[1], a);
+    sweep<OpM, 0, 3, 3, 3, false>(a, b);
+    const T c1 = eta * c.ex[1], c2 = eta * c.ex[0];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
+    sweep<OpET, 2, 3, 3, 3, true>(k, y);
+  }
+}
+
+// ---- divergence block B and its transpose -----------------------------------------------------
+// (B u)_q = - sum_b int psi_q d phi_j/dx_b u_jb :  -sum_b (G in direction b, N elsewhere) u_b
+template <typename T>
+__device__ __forceinline__ void cell_B2(const T (&u)[2][9], T (&out)[4], const OpCoef<T>& c) {
+  T t[6], s[4];
+  sweep<OpN, 1, 3, 3, 1, false>(u[0], t);  // (3,2)
+  sweep<OpG, 0, 3, 2, 1, false>(t, out);   // (2,2)
+  sweep<OpG, 1, 3, 3, 1, false>(u[1], t);
+  sweep<OpN, 0, 3, 2, 1, false>(t, s);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = -(c.bd[0] * out[i] + c.bd[1] * s[i]);
+}
+
+template <typename T>
+__device__ __forceinline__ void cell_BT2(const T (&p)[4], T (&u)[2][9], const OpCoef<T>& c, bool acc) {
+  T t[6], v[9];
+  sweep<OpNT, 1, 2, 2, 1, false>(p, t);  // (2,3)
+  sweep<OpGT, 0, 2, 3, 1, false>(t, v);  // (3,3)
+#pragma unroll
+  for (int i = 0; i < 9; ++i) u[0][i] = (acc ? u[0][i] : T(0)) - c.bd[0] * v[i];
+  sweep<OpGT, 1, 2, 2, 1, false>(p, t);
+  sweep<OpNT, 0, 2, 3, 1, false>(t, v);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) u[1][i] = (acc ? u[1][i] : T(0)) - c.bd[1] * v[i];
+}
+
+template <typename T>
+__device__ __forceinline__ void cell_B3(const T (&u)[3][27], T (&out)[8], const OpCoef<T>& c) {
+  T t0[18], t1[18], s0[12], s1[12], o[8];
+  sweep<OpN, 2, 3, 3, 3, false>(u[0], t0);  // (3,3,2)
+  sweep<OpN, 2, 3, 3, 3, false>(u[1], t1);
+  sweep<OpN, 1, 3, 3, 2, false>(t0, s0);    // (3,2,2)
+  sweep<OpG, 0, 3, 2, 2, false>(s0, out);   // (2,2,2)
+  sweep<OpG, 1, 3, 3, 2, false>(t1, s1);
+  sweep<OpG, 2, 3, 3, 3, false>(u[2], t0);
+  sweep<OpN, 1, 3, 3, 2, false>(t0, s0);
+  const T c1 = c.bd[1], c2 = c.bd[2];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) s1[i] = c1 * s1[i] + c2 * s0[i];
+  sweep<OpN, 0, 3, 2, 2, false>(s1, o);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) out[i] = -(c.bd[0] * out[i] + o[i]);
+}
+
+// B^T restricted to one output component (3D threads split by component)
+template <typename T, int COMP>
+__device__ __forceinline__ void cell_BT3(const T (&p)[8], T (&u)[27], const OpCoef<T>& c, bool acc) {
+  T a[12], b[18], v[27];
+  if (COMP == 2) sweep<OpGT, 2, 2, 2, 2, false>(p, a); else sweep<OpNT, 2, 2, 2, 2, false>(p, a);  // (2,2,3)
+  if (COMP == 1) sweep<OpGT, 1, 2, 2, 3, false>(a, b); else sweep<OpNT, 1, 2, 2, 3, false>(a, b);  // (2,3,3)
+  if (COMP == 0) sweep<OpGT, 0, 2, 3, 3, false>(b, v); else sweep<OpNT, 0, 2, 3, 3, false>(b, v);  // (3,3,3)
+  const T s = c.bd[COMP];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) u[i] = (acc ? u[i] : T(0)) - s * v[i];
+}
+
+// ---- diagonal of the viscous + mass block at one local node -------------------------------------
+__host__ __device__ inline int mdiag(int a) { return a == 1 ? 16 : 4; }
+__host__ __device__ inline int kdiag(int a) { return a == 1 ? 16 : 7; }
+
+template <typename T>
+__device__ __forceinline__ T cell_diagA(int dim, int comp, int la, int lb, int lc, T eta, const OpCoef<T>& c) {
+  if (dim == 2) {
+    const T Ma = T(mdiag(la)), Mb = T(mdiag(lb)), Ka = T(kdiag(la)), Kb = T(kdiag(lb));
+    const T ck = (comp == 1 ? T(2) : T(1)) * eta * c.km[1];
+    const T cq = (comp == 0 ? T(2) : T(1)) * eta * c.km[0];
+    return Ma * (c.mm * Mb + ck * Kb) + Ka * (cq * Mb);
+  }
+  const T Ma = T(mdiag(la)), Mb = T(mdiag(lb)), Mc = T(mdiag(lc));
+  const T Ka = T(kdiag(la)), Kb = T(kdiag(lb)), Kc = T(kdiag(lc));
+  const T ckz = (comp == 2 ? T(2) : T(1)) * eta * c.km[2];
+  const T cky = (comp == 1 ? T(2) : T(1)) * eta * c.km[1];
+  const T ckx = (comp == 0 ? T(2) : T(1)) * eta * c.km[0];
+  return Ma * (Mb * (c.mm * Mc + ckz * Kc) + cky * Kb * Mc) + Ka * (ckx * Mb * Mc);
+}
+
+}  // namespace gs

@@ -1,0 +1,120 @@
+// Host-side launch wrappers of the device kernels (internal to libgs.so).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+// Process-wide count of kernels this library has launched (returned by every launch wrapper).
+cudaError_t launched(cudaError_t e, int kernels = 1);
+long long launches_total();
+
+enum TileMode { TILE_APPLY = 0, TILE_RESID = 1, TILE_CHEB = 2 };
+
+// Arguments of the cell-tile operator kernel.  Velocity vectors have length dim*Nv
+// (component-blocked), pressure vectors Np.
+template <typename T>
+struct TileArgs {
+  Geom g;
+  OpCoef<T> c;
+  const T* eta;   // per cell
+  const T* xu;    // velocity input (A and B), CHEB: current iterate
+  const T* xp;    // pressure input (B^T)
+  T* yu;          // velocity output (APPLY / RESID)
+  T* yp;          // pressure output (B)
+  const T* bu;    // velocity right-hand side (RESID / CHEB)
+  const T* bp;    // pressure right-hand side (RESID)
+  T* d;           // CHEB: search direction (in/out)
+  const T* dinv;  // CHEB: inverse diagonal
+  T* xout;        // CHEB: next iterate (must not alias xu)
+  T c1, c2;       // CHEB: d <- c1 d + c2 dinv r   (c1 ignored when use_d == 0)
+  int use_d;
+  int raw;        // 1: no constraint elimination (operator of the unconstrained forms)
+  int tiles[3];
+};
+
+// Which blocks of the saddle operator a launch computes.
+enum TileOps { OPS_A = 1, OPS_BT = 2, OPS_B = 4 };
+
+template <typename T>
+cudaError_t launch_tile(int dim, int mode, int ops, TileArgs<T> a, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, T* out, int invert,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong_add(const Geom& gf, const Geom& gc, const T* xc, T* xf, cudaStream_t st);
+
+// Pressure mass M_p(1/eta): APPLY y = M x;  CHEB: r = b - M x_in, d = c1 d + c2 dinv r,
+// x_out = x_in + d.
+template <typename T>
+struct PMassArgs {
+  Geom g;
+  OpCoef<T> c;
+  const T* eta;
+  const T* x;
+  T* y;
+  const T* b;
+  T* d;
+  const T* dinv;
+  T* xout;
+  T c1, c2;
+  int use_d;
+  int raw;   // 1: no constraint elimination
+  int unit;  // 1: unit cell weight (plain Q1 mass) instead of 1/eta
+};
+template <typename T>
+cudaError_t launch_pmass(int mode, PMassArgs<T> a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_pdiag(const Geom& g, const OpCoef<T>& c, const T* eta, T* dinv, cudaStream_t st);
+
+// ---- vector kernels ----
+template <typename T>
+cudaError_t launch_cheb_init0(const T* b, const T* dinv, T inv_theta, T* d, T* x, long long n,
+                              cudaStream_t st);
+template <typename TI, typename TO>
+cudaError_t launch_cast(const TI* in, TO* out, long long n, TO scale, cudaStream_t st);
+template <typename T>
+cudaError_t launch_zero_constrained_u(const Geom& g, T* v, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lanczos_pre(const T* dinv, const T* v, T* t, long long n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lanczos_post(const T* dinv, const T* y, const T* vprev, T beta_prev, T* w,
+                                long long n, cudaStream_t st);
+
+// partial sums: part[i * G + block] = sum over block's chunk of V[i][e] * w[e], i < k
+template <typename T>
+cudaError_t launch_dots_partial(const T* V, long long ldv, int k, const T* w, long long n,
+                                double* part, int G, cudaStream_t st);
+cudaError_t launch_reduce_partials(const double* part, int k, int G, double* out, cudaStream_t st);
+// w <- w + sign * sum_i coef[i] V[i]   (coef on device)
+cudaError_t launch_multi_axpy(const double* V, long long ldv, int k, const double* coef, double sign,
+                              double* w, long long n, cudaStream_t st);
+// v <- w * (1 / sqrt(nrm2[0]))   (nrm2 on device)
+cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, long long n,
+                                  cudaStream_t st);
+cudaError_t launch_add_vec(double* a, const double* b, int k, cudaStream_t st);  // a += b (small)
+// x[i] -= mean over pressure entries that are free; pmask may be NULL; sum on device
+cudaError_t launch_masked_sum_partial(const double* x, const uint8_t* mask, long long n,
+                                      double* part, int G, cudaStream_t st);
+cudaError_t launch_sub_scalar_masked(double* x, const uint8_t* mask, long long n, const double* sum,
+                                     double inv_count, cudaStream_t st);
+// coarse dense solve: y[free[i]] = sum_j Ainv[i][j] b[free[j]], y[constrained] = 0
+template <typename T>
+cudaError_t launch_coarse_solve(const double* Ainv, const int* freeidx, int nf, const T* b, T* y,
+                                long long n, double* tmp, cudaStream_t st);
+cudaError_t launch_gj_save(const double* A, int n, int k, double* row, double* col, cudaStream_t st);
+cudaError_t launch_gj_update(double* A, int n, int k, const double* row, const double* col,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_axpby(const T* x, T* y, T a, T b, long long n, cudaStream_t st);  // y = a x + b y
+// z[i] = v[i] on every constrained entry of a full vector [u | p] (finest level)
+cudaError_t launch_copy_constrained(const double* v, double* z, const Geom& geo, cudaStream_t st);
+cudaError_t launch_combine_lift(const double* Mf, const double* Kg, const double* g,
+                                const uint8_t* vmask, const uint8_t* pmask, const Geom& geo,
+                                double* rhs, cudaStream_t st);
+
+}  // namespace gs

@@ -1,0 +1,304 @@
+// Node-gather kernels: diagonal of A, multigrid transfers, and the 1/eta-weighted pressure
+// mass (Schur approximation).  One thread per output node; every output is written once.
+#include "gs_cell.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+namespace {
+constexpr int TPB = 256;
+
+__device__ __forceinline__ void unflat(long long idx, const int* ext, int dim, int& I, int& J, int& K) {
+  I = (int)(idx % ext[0]);
+  idx /= ext[0];
+  J = (int)(idx % ext[1]);
+  K = dim == 3 ? (int)(idx / ext[1]) : 0;
+}
+
+inline unsigned nblk(long long n) { return (unsigned)((n + TPB - 1) / TPB); }
+}  // namespace
+
+// ---- diag(A) (Sec. 4: the Jacobi preconditioner of Cheb(A, diag(A), k_A)) ----------------------
+template <typename T, int DIM>
+__global__ void k_diagA(const Geom g, const OpCoef<T> c, const T* __restrict__ eta, T* __restrict__ out,
+                        int invert) {
+  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= g.Nv) return;
+  int I, J, K;
+  unflat(node, g.nv, DIM, I, J, K);
+  const bool con = vnode_constrained(g, node, I, J, K);
+  T acc[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) acc[a] = T(0);
+  if (!con) {
+    // cells touching the node along each axis and the node's local index in them
+    int cl[3][2], ll[3][2], cnt[3];
+    const int idx[3] = {I, J, K};
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int v = idx[ax];
+      cnt[ax] = 0;
+      if (v & 1) {
+        cl[ax][0] = v >> 1; ll[ax][0] = 1; cnt[ax] = 1;
+      } else {
+        if ((v >> 1) - 1 >= 0) { cl[ax][cnt[ax]] = (v >> 1) - 1; ll[ax][cnt[ax]] = 2; cnt[ax]++; }
+        if ((v >> 1) < g.n[ax]) { cl[ax][cnt[ax]] = v >> 1; ll[ax][cnt[ax]] = 0; cnt[ax]++; }
+      }
+    }
+    const int c2n = DIM == 3 ? cnt[2] : 1;
+    for (int k = 0; k < c2n; ++k)
+      for (int j = 0; j < cnt[1]; ++j)
+        for (int i = 0; i < cnt[0]; ++i) {
+          const long long cell = cl[0][i] + (long long)g.n[0] * (cl[1][j] + (long long)g.n[1] * (DIM == 3 ? cl[2][k] : 0));
+          if (cell_void(g, cell)) continue;
+          const T e = eta[cell] * c.eta_scale;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a)
+            acc[a] += cell_diagA<T>(DIM, a, ll[0][i], ll[1][j], DIM == 3 ? ll[2][k] : 0, e, c);
+        }
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    T v = con ? T(1) : acc[a];
+    out[a * g.Nv + node] = invert ? T(1) / v : v;
+  }
+}
+
+template <typename T>
+cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, T* out, int invert, cudaStream_t st) {
+  if (g.dim == 2)
+    k_diagA<T, 2><<<nblk(g.Nv), TPB, 0, st>>>(g, c, eta, out, invert);
+  else
+    k_diagA<T, 3><<<nblk(g.Nv), TPB, 0, st>>>(g, c, eta, out, invert);
+  return launched(cudaGetLastError());
+}
+
+// ---- transfers: P = Q2 interpolation of the coarse field at the fine nodes (Sec. 4, nested
+// meshes); R = P^T.  1D weights: fine 2C <- coarse C (1); fine 4c+1 <- (3/8, 3/4, -1/8) on
+// coarse (2c, 2c+1, 2c+2); fine 4c+3 <- (-1/8, 3/4, 3/8).  Constrained fine rows and
+// constrained coarse columns are removed. -----------------------------------------------------
+
+// weights of coarse node C seen from fine nodes: offsets f - 2C and weights
+__device__ __forceinline__ int restrict_stencil(int C, int nvf, int* fi, double* w) {
+  int m = 0;
+  if (C & 1) {
+    const int f[3] = {2 * C - 1, 2 * C, 2 * C + 1};
+    const double ww[3] = {0.75, 1.0, 0.75};
+    for (int t = 0; t < 3; ++t)
+      if (f[t] >= 0 && f[t] < nvf) { fi[m] = f[t]; w[m] = ww[t]; m++; }
+  } else {
+    const int f[5] = {2 * C - 3, 2 * C - 1, 2 * C, 2 * C + 1, 2 * C + 3};
+    const double ww[5] = {-0.125, 0.375, 1.0, 0.375, -0.125};
+    for (int t = 0; t < 5; ++t)
+      if (f[t] >= 0 && f[t] < nvf) { fi[m] = f[t]; w[m] = ww[t]; m++; }
+  }
+  return m;
+}
+
+template <typename T, int DIM>
+__global__ void k_restrict(const Geom gf, const Geom gc, const T* __restrict__ rf, T* __restrict__ rc) {
+  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= gc.Nv) return;
+  int I, J, K;
+  unflat(node, gc.nv, DIM, I, J, K);
+  const bool con = vnode_constrained(gc, node, I, J, K);
+  T acc[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) acc[a] = T(0);
+  if (!con) {
+    int fx[5], fy[5], fz[5];
+    double wx[5], wy[5], wz[5];
+    const int mx = restrict_stencil(I, gf.nv[0], fx, wx);
+    const int my = restrict_stencil(J, gf.nv[1], fy, wy);
+    int mz = 1;
+    fz[0] = 0; wz[0] = 1.0;
+    if (DIM == 3) mz = restrict_stencil(K, gf.nv[2], fz, wz);
+    for (int k = 0; k < mz; ++k)
+      for (int j = 0; j < my; ++j) {
+        const T wjk = T(wy[j] * wz[k]);
+        for (int i = 0; i < mx; ++i) {
+          const long long fn = fx[i] + (long long)gf.nv[0] * (fy[j] + (long long)gf.nv[1] * fz[k]);
+          if (vnode_constrained(gf, fn, fx[i], fy[j], fz[k])) continue;
+          const T w = T(wx[i]) * wjk;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) acc[a] += w * rf[a * gf.Nv + fn];
+        }
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) rc[a * gc.Nv + node] = acc[a];
+}
+
+__device__ __forceinline__ int prolong_stencil(int I, int* ci, double* w) {
+  if (!(I & 1)) { ci[0] = I >> 1; w[0] = 1.0; return 1; }
+  const int c = I >> 2;  // coarse cell
+  if ((I & 3) == 1) {
+    ci[0] = 2 * c; ci[1] = 2 * c + 1; ci[2] = 2 * c + 2;
+    w[0] = 0.375; w[1] = 0.75; w[2] = -0.125;
+  } else {
+    ci[0] = 2 * c; ci[1] = 2 * c + 1; ci[2] = 2 * c + 2;
+    w[0] = -0.125; w[1] = 0.75; w[2] = 0.375;
+  }
+  return 3;
+}
+
+template <typename T, int DIM>
+__global__ void k_prolong_add(const Geom gf, const Geom gc, const T* __restrict__ xc, T* __restrict__ xf) {
+  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= gf.Nv) return;
+  int I, J, K;
+  unflat(node, gf.nv, DIM, I, J, K);
+  if (vnode_constrained(gf, node, I, J, K)) return;
+  int cx[3], cy[3], cz[3];
+  double wx[3], wy[3], wz[3];
+  const int mx = prolong_stencil(I, cx, wx);
+  const int my = prolong_stencil(J, cy, wy);
+  int mz = 1;
+  cz[0] = 0; wz[0] = 1.0;
+  if (DIM == 3) mz = prolong_stencil(K, cz, wz);
+  T acc[DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) acc[a] = T(0);
+  for (int k = 0; k < mz; ++k)
+    for (int j = 0; j < my; ++j) {
+      const T wjk = T(wy[j] * wz[k]);
+      for (int i = 0; i < mx; ++i) {
+        const long long cn = cx[i] + (long long)gc.nv[0] * (cy[j] + (long long)gc.nv[1] * cz[k]);
+        if (vnode_constrained(gc, cn, cx[i], cy[j], cz[k])) continue;
+        const T w = T(wx[i]) * wjk;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) acc[a] += w * xc[a * gc.Nv + cn];
+      }
+    }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) xf[a * gf.Nv + node] += acc[a];
+}
+
+template <typename T>
+cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st) {
+  if (gf.dim == 2)
+    k_restrict<T, 2><<<nblk(gc.Nv), TPB, 0, st>>>(gf, gc, rf, rc);
+  else
+    k_restrict<T, 3><<<nblk(gc.Nv), TPB, 0, st>>>(gf, gc, rf, rc);
+  return launched(cudaGetLastError());
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const Geom& gf, const Geom& gc, const T* xc, T* xf, cudaStream_t st) {
+  if (gf.dim == 2)
+    k_prolong_add<T, 2><<<nblk(gf.Nv), TPB, 0, st>>>(gf, gc, xc, xf);
+  else
+    k_prolong_add<T, 3><<<nblk(gf.Nv), TPB, 0, st>>>(gf, gc, xc, xf);
+  return launched(cudaGetLastError());
+}
+
+// ---- pressure mass M_p(1/eta): cell matrix (prod h / 6^d) eta_K^{-1} Pi x Pi (x Pi) ---------------
+template <typename T, int DIM, int MODE>
+__global__ void k_pmass(const PMassArgs<T> A) {
+  const Geom& g = A.g;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.Np) return;
+  int I, J, K;
+  unflat(q, g.npn, DIM, I, J, K);
+  const bool con = !A.raw && pnode_constrained(g, q);
+  T mx = T(0);
+  if (!con) {
+    const int idx[3] = {I, J, K};
+    int cl[3][2], cnt[3];
+    for (int ax = 0; ax < DIM; ++ax) {
+      cnt[ax] = 0;
+      if (idx[ax] - 1 >= 0) cl[ax][cnt[ax]++] = idx[ax] - 1;
+      if (idx[ax] < g.n[ax]) cl[ax][cnt[ax]++] = idx[ax];
+    }
+    const int c2n = DIM == 3 ? cnt[2] : 1;
+    for (int k = 0; k < c2n; ++k)
+      for (int j = 0; j < cnt[1]; ++j)
+        for (int i = 0; i < cnt[0]; ++i) {
+          const int c0 = cl[0][i], c1 = cl[1][j], c2 = DIM == 3 ? cl[2][k] : 0;
+          const long long cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
+          if (cell_void(g, cell)) continue;
+          const int la = I - c0, lb = J - c1, lc = DIM == 3 ? K - c2 : 0;  // local node of q
+          T s = T(0);
+          for (int rc = 0; rc < (DIM == 3 ? 2 : 1); ++rc)
+            for (int rb = 0; rb < 2; ++rb)
+              for (int ra = 0; ra < 2; ++ra) {
+                const long long r = (c0 + ra) + (long long)g.npn[0] * ((c1 + rb) + (long long)g.npn[1] * (c2 + rc));
+                if (!A.raw && pnode_constrained(g, r)) continue;
+                int w = (la == ra ? 2 : 1) * (lb == rb ? 2 : 1);
+                if (DIM == 3) w *= (lc == rc ? 2 : 1);
+                s += T(w) * A.x[r];
+              }
+          mx += A.unit ? s : s / A.eta[cell];
+        }
+    mx *= A.c.pm;
+  }
+  const T mq = con ? A.x[q] : mx;
+  if (MODE == TILE_APPLY) {
+    A.y[q] = mq;
+  } else {
+    const T r = A.b[q] - mq;
+    T dn = A.c2 * A.dinv[q] * r;
+    if (A.use_d) dn += A.c1 * A.d[q];
+    A.d[q] = dn;
+    A.xout[q] = A.x[q] + dn;
+  }
+}
+
+template <typename T, int DIM>
+__global__ void k_pdiag(const Geom g, const OpCoef<T> c, const T* __restrict__ eta, T* __restrict__ dinv) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.Np) return;
+  int I, J, K;
+  unflat(q, g.npn, DIM, I, J, K);
+  if (pnode_constrained(g, q)) { dinv[q] = T(1); return; }
+  const int idx[3] = {I, J, K};
+  int cl[3][2], cnt[3];
+  for (int ax = 0; ax < DIM; ++ax) {
+    cnt[ax] = 0;
+    if (idx[ax] - 1 >= 0) cl[ax][cnt[ax]++] = idx[ax] - 1;
+    if (idx[ax] < g.n[ax]) cl[ax][cnt[ax]++] = idx[ax];
+  }
+  T s = T(0);
+  const int c2n = DIM == 3 ? cnt[2] : 1;
+  for (int k = 0; k < c2n; ++k)
+    for (int j = 0; j < cnt[1]; ++j)
+      for (int i = 0; i < cnt[0]; ++i) {
+        const long long cell = cl[0][i] + (long long)g.n[0] * (cl[1][j] + (long long)g.n[1] * (DIM == 3 ? cl[2][k] : 0));
+        if (cell_void(g, cell)) continue;
+        s += T(1) / eta[cell];
+      }
+  dinv[q] = T(1) / (s * c.pm * T(DIM == 3 ? 8 : 4));
+}
+
+template <typename T>
+cudaError_t launch_pmass(int mode, PMassArgs<T> a, cudaStream_t st) {
+  const unsigned nb = nblk(a.g.Np);
+  if (a.g.dim == 2) {
+    if (mode == TILE_APPLY) k_pmass<T, 2, TILE_APPLY><<<nb, TPB, 0, st>>>(a);
+    else k_pmass<T, 2, TILE_CHEB><<<nb, TPB, 0, st>>>(a);
+  } else {
+    if (mode == TILE_APPLY) k_pmass<T, 3, TILE_APPLY><<<nb, TPB, 0, st>>>(a);
+    else k_pmass<T, 3, TILE_CHEB><<<nb, TPB, 0, st>>>(a);
+  }
+  return launched(cudaGetLastError());
+}
+
+template <typename T>
+cudaError_t launch_pdiag(const Geom& g, const OpCoef<T>& c, const T* eta, T* dinv, cudaStream_t st) {
+  if (g.dim == 2)
+    k_pdiag<T, 2><<<nblk(g.Np), TPB, 0, st>>>(g, c, eta, dinv);
+  else
+    k_pdiag<T, 3><<<nblk(g.Np), TPB, 0, st>>>(g, c, eta, dinv);
+  return launched(cudaGetLastError());
+}
+
+#define INST(T)                                                                                    \
+  template cudaError_t launch_diagA<T>(const Geom&, const OpCoef<T>&, const T*, T*, int, cudaStream_t); \
+  template cudaError_t launch_restrict<T>(const Geom&, const Geom&, const T*, T*, cudaStream_t);   \
+  template cudaError_t launch_prolong_add<T>(const Geom&, const Geom&, const T*, T*, cudaStream_t); \
+  template cudaError_t launch_pmass<T>(int, PMassArgs<T>, cudaStream_t);                           \
+  template cudaError_t launch_pdiag<T>(const Geom&, const OpCoef<T>&, const T*, T*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace gs

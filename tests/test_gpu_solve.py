@@ -1,0 +1,146 @@
+"""GPU parity of the V-cycle and of the full FGMRES solve (through the C ABI) against the oracle.
+
+Solution parity: both sides solve to rel-res 1e-11 and the pressure-normalised solutions
+must agree to 1e-8 (the systems have condition numbers up to ~1e12, so the residual
+tolerance, not the method, bounds the solution difference).  FP64-multigrid iteration
+counts must match the oracle's within one iteration.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle.fem import System
+from oracle.krylov import StokesOracle, direct_solve, normalize_pressure
+from oracle.mesh import mesh_from_problem
+from oracle.mg import Hierarchy
+from paper_2305_08986_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+PROBLEMS = {
+    "disc16": lambda: inputs.config_disc(n=16, levels=3),
+    "channel_small": lambda: inputs.config_channel(nx=160, ny=28, levels=3),
+    "box3d": lambda: inputs.config_box_inclusion(3, (8, 8, 8), 2, 1e4, 50.0, seed=3),
+    "rand2d_void": lambda: inputs.config_random_field(2, (48, 32), levels=3, seed=8, contrast=1e3, alpha=20.0,
+                                                      faces=inputs.FACE_XM | inputs.FACE_YM | inputs.FACE_YP,
+                                                      void_fraction=0.03),
+}
+
+
+@pytest.mark.parametrize("name", ["disc16", "channel_small", "box3d"])
+def test_vcycle_fp64_parity(name):
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS[name]()
+    m = mesh_from_problem(p)
+    H = Hierarchy(m, p.eta, p.alpha, p.levels)
+    s = gs.Solver.from_problem(p, mg_precision=64)
+    b = np.random.default_rng(0).standard_normal(m.n_u)
+    z = torch.empty(m.n_u, dtype=torch.float64, device="cuda")
+    s.vcycle(torch.tensor(b, device="cuda"), z)
+    assert rel(z.cpu().numpy(), H.vcycle(b)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["disc16", "box3d"])
+def test_vcycle_fp32_close(name):
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS[name]()
+    m = mesh_from_problem(p)
+    H = Hierarchy(m, p.eta, p.alpha, p.levels)
+    s = gs.Solver.from_problem(p, mg_precision=32)
+    b = np.random.default_rng(0).standard_normal(m.n_u)
+    z = torch.empty(m.n_u, dtype=torch.float64, device="cuda")
+    s.vcycle(torch.tensor(b, device="cuda"), z)
+    assert rel(z.cpu().numpy(), H.vcycle(b)) <= 1e-3
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("prec", [64, 32])
+def test_solve_parity(name, prec):
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS[name]()
+    m = mesh_from_problem(p)
+    o = StokesOracle(m, p.eta, p.alpha, p.levels)
+    b_ref = o.sys.lift_rhs(p.f, p.g)
+    s = gs.Solver.from_problem(p, mg_precision=prec)
+    f = torch.tensor(p.f, device="cuda")
+    g = torch.tensor(p.g, device="cuda")
+    b = torch.empty_like(f)
+    s.lift_rhs(f, g, b)
+    assert rel(b.cpu().numpy(), b_ref) <= 1e-12
+    x = torch.zeros_like(b)
+    it, rr, _ = s.solve(b, x, tol=1e-11)
+    xo, ito, relo, _ = o.solve(b_ref, tol=1e-11)
+    assert rr <= 1e-11
+    xg = normalize_pressure(m, o.sys, x.cpu().numpy())
+    assert rel(xg, normalize_pressure(m, o.sys, xo)) <= 1e-8
+    # the oracle's own residual of the GPU solution
+    assert np.linalg.norm(b_ref - o.sys.K @ x.cpu().numpy()) <= 2e-11 * np.linalg.norm(b_ref)
+    if prec == 64:
+        assert abs(it - ito) <= 1, (it, ito)
+
+
+def test_solve_tolerance_1e8_oracle_residual():
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS["channel_small"]()
+    m = mesh_from_problem(p)
+    sysm = System(m, p.eta, p.alpha)
+    s = gs.Solver.from_problem(p)
+    b = torch.empty(m.N, dtype=torch.float64, device="cuda")
+    s.lift_rhs(torch.tensor(p.f, device="cuda"), torch.tensor(p.g, device="cuda"), b)
+    x = torch.zeros_like(b)
+    it, rr, _ = s.solve(b, x, tol=1e-8)
+    bn = b.cpu().numpy()
+    assert rr <= 1e-8
+    assert np.linalg.norm(bn - sysm.K @ x.cpu().numpy()) <= 1.01e-8 * np.linalg.norm(bn)
+
+
+def test_solve_edge_cases():
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS["disc16"]()
+    s = gs.Solver.from_problem(p)
+    n = s.n_total
+    z = torch.zeros(n, dtype=torch.float64, device="cuda")
+    x = torch.full((n,), 3.0, dtype=torch.float64, device="cuda")
+    it, rr, st = s.solve(z, x, tol=1e-8)
+    assert it == 0 and rr == 0.0 and float(x.abs().max()) == 0.0
+    b = torch.empty_like(z)
+    s.lift_rhs(torch.tensor(p.f, device="cuda"), torch.tensor(p.g, device="cuda"), b)
+    x = torch.zeros_like(b)
+    s.solve(b, x, tol=1e-10)
+    it, rr, _ = s.solve(b, x, tol=1e-8)          # warm start at the solution
+    assert it == 0 and rr <= 1e-8
+    s2 = gs.Solver.from_problem(p, max_iter=2)
+    x = torch.zeros_like(b)
+    it, rr, st = s2.solve(b, x, tol=1e-12, allow_noconv=True)
+    assert st == gs.GS_ENOCONV and it == 2 and rr > 1e-12
+
+
+def test_create_rejects_bad_input():
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS["disc16"]()
+    bad = p.eta.copy()
+    bad[5] = np.nan
+    with pytest.raises(gs.GsError) as e:
+        gs.Solver(p.dim, p.n, p.length, p.levels, bad, p.alpha)
+    assert e.value.status == gs.GS_EINVAL
+    mesh, _ = gs.make_mesh(p.dim, p.n, p.length)
+    o = gs.make_options()
+    need = gs._lib.gs_footprint_bytes(ctypes.byref(mesh), p.levels, ctypes.byref(o))
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    ctx = ctypes.c_void_p()
+    eta = np.ascontiguousarray(p.eta)
+    st = gs._lib.gs_create(ctypes.byref(mesh), p.levels, eta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           1.0, ctypes.byref(o), None, ctypes.c_void_p(ws.data_ptr()), need // 2, ctypes.byref(ctx))
+    assert st == gs.GS_ENOMEM and not ctx.value
