@@ -195,6 +195,26 @@ typedef struct {
 gs_status gs_profile(gs_ctx* ctx, int enable);
 int gs_profile_read(gs_ctx* ctx, gs_kernel_stat* out, int max);
 
+/* Coarse-level solve y = A_0^{-1} b that allocates nothing and uses no workspace scratch.
+ * The paper has no counterpart: this is a service entry point for callers that cannot
+ * allocate device memory at the point of the call -- for example a multigrid code that uses
+ * this library's dense coarse solve as its bottom solver from inside a CUDA-graph capture or
+ * a latency-critical loop where cudaMalloc (and any allocating library routine) is not
+ * allowed, and that must not touch the context workspace another stream may be using.  It
+ * computes exactly what gs_apply_level(ctx, 0, GS_OP_COARSE, 64, b, y, NULL) computes.
+ * b, y: device, length d*N_v of level 0, FP64, must not alias.  The gathered right-hand side
+ * lives in one file-scope device array of GS_NOALLOC_COARSE_MAX doubles (128 KiB), which every
+ * GPU that loads the library holds until the process exits; contexts whose coarse level has
+ * more free unknowns than that are rejected with GS_EINVAL (see gs_get_info().coarse_free), as
+ * are contexts built with coarse_mode = 1.  Call it with the context's device current.  The
+ * first call on each device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (every call rewrites the entries it reads, so nothing needs clearing): calls
+ * that overlap on the GPU -- on different streams, or from different threads -- race.  Enqueue
+ * only, on the context's stream. */
+#define GS_NOALLOC_COARSE_MAX 16384
+gs_status gs_coarse_solve_noalloc(gs_ctx* ctx, const double* b, double* y);
+
 /* Change the stream work is enqueued on. */
 gs_status gs_set_stream(gs_ctx* ctx, void* stream);
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1124,6 +1125,48 @@ int gs_profile_read(gs_ctx* c, gs_kernel_stat* out, int max) {
     ++n;
   }
   return n;
+}
+
+}  // extern "C"
+
+// ---- coarse solve without workspace scratch (see gs_coarse_solve_noalloc in gs.h) ----------
+// The gathered right-hand side of the dense coarse GEMV lives here instead of in the context
+// workspace.  Host code must not use the symbol's host-side address: the device address is
+// looked up once per device with cudaGetSymbolAddress and cached.
+static __device__ __align__(256) double g_noalloc_coarse_rhs[GS_NOALLOC_COARSE_MAX];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[128] = {nullptr};
+
+gs_status noalloc_scratch(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(GS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_coarse_rhs));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return GS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gs_status gs_coarse_solve_noalloc(gs_ctx* c, const double* b, double* y) {
+  if (!c || !b || !y) return fail(GS_EINVAL, "NULL argument");
+  if (b == y) return fail(GS_EINVAL, "b and y must not alias");
+  if (c->nf == 0) return fail(GS_EINVAL, "context has no dense coarse solve (coarse_mode 1)");
+  if (c->nf > GS_NOALLOC_COARSE_MAX)
+    return fail(GS_EINVAL, "coarse level has " + std::to_string(c->nf) + " free unknowns; the allocation-free "
+                "coarse solve holds at most " + std::to_string(GS_NOALLOC_COARSE_MAX));
+  double* scratch = nullptr;
+  CKS(noalloc_scratch(&scratch));
+  CK(launch_coarse_solve<double>(c->Ainv, c->cfree, c->nf, b, y, c->lv[0].nu, scratch, c->st));
+  return GS_OK;
 }
 
 gs_status gs_set_stream(gs_ctx* c, void* stream) {

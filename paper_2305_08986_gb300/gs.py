@@ -78,6 +78,8 @@ _lib.gs_profile.restype = ctypes.c_int
 _lib.gs_profile.argtypes = [_vp, ctypes.c_int]
 _lib.gs_profile_read.restype = ctypes.c_int
 _lib.gs_profile_read.argtypes = [_vp, ctypes.POINTER(GsKernelStat), ctypes.c_int]
+_lib.gs_coarse_solve_noalloc.restype = ctypes.c_int
+_lib.gs_coarse_solve_noalloc.argtypes = [_vp, _vp, _vp]
 _lib.gs_set_stream.restype = ctypes.c_int
 _lib.gs_set_stream.argtypes = [_vp, _vp]
 _lib.gs_destroy.restype = None
@@ -89,7 +91,7 @@ _lib.gs_last_error.argtypes = []
 
 EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_vmult", "gs_vmult_A", "gs_vcycle", "gs_solve", "gs_lift_rhs",
             "gs_batch_solve", "gs_apply_level", "gs_get_info", "gs_set_stream", "gs_destroy", "gs_strerror",
-            "gs_last_error", "gs_profile", "gs_profile_read"]
+            "gs_last_error", "gs_profile", "gs_profile_read", "gs_coarse_solve_noalloc"]
 
 
 class GsError(RuntimeError):
