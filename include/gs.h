@@ -96,6 +96,11 @@ typedef struct {            /* zero-initialised = defaults */
   int coarse_mode;          /* 0: exact dense FP64 solve on level 0 (default);
                                1: Chebyshev smoothing only on level 0 (for meshes whose coarsest
                                   level is too large for a dense factorisation, e.g. 1280 x 210) */
+  int schur_kind;           /* 0: Cahouet-Chabard when alpha > 0, else pressure mass (default);
+                               1: 1/eta-weighted pressure mass M_p(1/eta) only;
+                               2: Cahouet-Chabard S^{-1} ~ M_p(1/eta)^{-1} + alpha K_p^{-1}, K_p the
+                                  Q1 pressure Laplacian (p = 0 on faces without a velocity
+                                  Dirichlet condition), inverted by one multigrid V-cycle */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */
@@ -156,7 +161,11 @@ typedef enum {
   GS_OP_SCHUR_INV = 9,   /* y = Cheb(M_p(1/eta), diag, schur_degree) x, from 0       */
   GS_OP_COARSE = 10,     /* y = A_0^{-1} x       (level 0, dense FP64)               */
   GS_OP_PRECOND = 11,    /* y = P^{-1} x         (full block preconditioner)         */
-  GS_OP_A_RAW = 12       /* y = A_l x without constraint elimination                 */
+  GS_OP_A_RAW = 12,      /* y = A_l x without constraint elimination                 */
+  GS_OP_PLAP = 13,       /* y = K_p,l x          (pressure Laplacian of level l)     */
+  GS_OP_PLAP_INV = 14,   /* y = V_p(x) ~ K_p^{-1} x (finest level, MG precision)    */
+  GS_OP_PRESTRICT = 15,  /* y (level l-1) = P_p,l^T x (Q1 restriction)               */
+  GS_OP_PPROLONGATE = 16 /* y (level l) += P_p,l x (level l-1) (Q1 interpolation)    */
 } gs_op;
 
 /* Apply one operator of level `level` (0 = coarsest).  prec = 64: x, y, aux are double*;
@@ -179,6 +188,9 @@ typedef struct {
   int coarse_free;         /* unknowns of the dense coarse solve */
   size_t footprint_bytes;
   long long kernel_launches; /* kernels this library has launched in this process (all contexts) */
+  int schur_cc;            /* 1 if the Cahouet-Chabard term is active */
+  int pressure_coarse_free;/* unknowns of the dense coarse pressure-Laplacian solve */
+  double plambda_max[16];  /* Chebyshev upper bound of the pressure Laplacian per level */
 } gs_info;
 gs_status gs_get_info(const gs_ctx* ctx, gs_info* out);
 

@@ -11,6 +11,8 @@ Sec. 4; it stops on the Euclidean norm of the residual.  Readings taken here:
   check b - K x at exit; if the explicit check fails, the method restarts, at
   most 3 extra times;
 * restart length m = 50; orthogonalisation = classical Gram-Schmidt applied twice;
+* Schur approximation S^{-1} ~ M_p(1/eta)^{-1} (+ alpha K_p^{-1}, Cahouet-Chabard, when alpha > 0;
+  see pressure.py);
 * preconditioner (block upper triangular):  z_p = -S^{-1} r_p,
   z_u = V-cycle(r_u - B^T z_p); on constrained entries (identity rows of K) z = r;
 * pure-Dirichlet problems have the constant pressure in the kernel; the mean of
@@ -31,6 +33,7 @@ import scipy.sparse.linalg as spla
 from .fem import System
 from .mesh import Mesh
 from .mg import Hierarchy, schur_apply_inv
+from .pressure import PressureHierarchy
 
 
 def fgmres(apply_K, apply_M, b, x0=None, tol=1e-8, restart=50, max_iter=1000, max_extra=3):
@@ -106,12 +109,19 @@ def fgmres(apply_K, apply_M, b, x0=None, tol=1e-8, restart=50, max_iter=1000, ma
 class StokesOracle:
     """FP64 reference solver for one problem: assembled system + velocity hierarchy."""
 
-    def __init__(self, mesh: Mesh, eta, alpha, levels, degree=4, seed=0, restart=50):
+    def __init__(self, mesh: Mesh, eta, alpha, levels, degree=4, seed=0, restart=50, schur="auto",
+                 coarse="cholesky"):
         self.mesh = mesh
+        self.alpha = float(alpha)
         self.sys = System(mesh, eta, alpha)
         self.levels = levels
         self.restart = restart
-        self.mg = Hierarchy(mesh, eta, alpha, levels, degree=degree, seed=seed)
+        self.mg = Hierarchy(mesh, eta, alpha, levels, degree=degree, seed=seed, coarse=coarse)
+        # Schur approximation: "mass" = M_p(1/eta) only; "cc" = Cahouet-Chabard
+        # M_p(1/eta)^{-1} + alpha K_p^{-1}; "auto" = cc when alpha > 0
+        self.schur = ("cc" if self.alpha > 0 else "mass") if schur == "auto" else schur
+        self.pmg = (PressureHierarchy(mesh, levels, degree=degree, seed=seed, coarse=coarse)
+                    if self.schur == "cc" else None)
         # the finest level of the hierarchy re-assembles A; both are identical by construction
         self.nullspace = mesh.has_pressure_nullspace()
         self.free_p = ~self.sys.p_constrained
@@ -132,6 +142,8 @@ class StokesOracle:
         n_u = self.mesh.n_u
         ru, rp = r[:n_u], r[n_u:]
         zp = -schur_apply_inv(self.sys.Mpw, rp, self.mesh.dim)
+        if self.pmg is not None:
+            zp = zp - self.alpha * self.pmg.apply_inverse(rp)
         zu = self.mg.vcycle(ru - self.sys.B.T @ zp)
         z = np.concatenate([zu, zp])
         # K is the identity on constrained rows: invert that block exactly

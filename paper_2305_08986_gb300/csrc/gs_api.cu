@@ -71,6 +71,12 @@ struct Level {
   uint8_t *vmask = nullptr, *pmask = nullptr, *cvoid = nullptr;
   void *xA = nullptr, *xB = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
   double lam_hi = 0.0;
+  // pressure Laplacian level (Cahouet-Chabard term): constraint mask, MG vectors, bound
+  std::vector<uint8_t> hpc;
+  uint8_t* pcmask = nullptr;
+  void *pxA = nullptr, *pxB = nullptr, *pb = nullptr, *pd = nullptr, *pdinv = nullptr;
+  double plam_hi = 0.0;
+  double pkc[3] = {0, 0, 0};
 };
 
 }  // namespace
@@ -87,6 +93,13 @@ struct gs_ctx {
   long long n_pfree = 0;
   // Schur step vectors (finest level, MG precision)
   void *p_b = nullptr, *p_xA = nullptr, *p_xB = nullptr, *p_d = nullptr, *p_dinv = nullptr;
+  // Cahouet-Chabard Schur term: allocated unless schur_kind == 1, active when cc is set
+  bool cc_alloc = false, cc = false, psingular = false;
+  int nfp = 0;
+  std::vector<int> hpfree;
+  double* PAinv = nullptr;
+  int* pcfree = nullptr;
+  double* pctmp = nullptr;
   // dense coarse inverse
   int nf = 0;
   std::vector<int> hfree;
@@ -150,6 +163,7 @@ gs_options normalize_opts(const gs_options* o) {
   r.schur_degree = opt_or(r.schur_degree, 4);
   r.lanczos_steps = opt_or(r.lanczos_steps, 12);
   r.coarse_mode = r.coarse_mode == 1 ? 1 : 0;
+  r.schur_kind = (r.schur_kind == 1 || r.schur_kind == 2) ? r.schur_kind : 0;
   return r;
 }
 
@@ -322,6 +336,43 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
     c->n_pfree = 0;
     for (auto v : Fl.hpmask) c->n_pfree += v ? 0 : 1;
   }
+  // pressure Laplacian of the Cahouet-Chabard term: p = 0 on pressure nodes touched by no active
+  // cell and on faces without a velocity Dirichlet condition; pure Neumann if every face is
+  // Dirichlet (then singular with the constant in its kernel)
+  c->cc_alloc = c->opt.schur_kind != 1;
+  c->hpfree.clear();
+  c->nfp = 0;
+  c->psingular = c->nullspace;
+  if (c->cc_alloc) {
+    for (int l = 0; l < L; ++l) {
+      Level& lv = c->lv[l];
+      const int np0 = lv.n[0] + 1, np1 = lv.n[1] + 1, np2 = dim == 3 ? lv.n[2] + 1 : 1;
+      lv.hpc.assign(lv.Np, 1);
+      for (int k = 0; k < lv.n[2]; ++k)
+        for (int j = 0; j < lv.n[1]; ++j)
+          for (int i = 0; i < lv.n[0]; ++i) {
+            const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+            if (lv.hvoid[cc]) continue;
+            for (int lc = 0; lc < (dim == 3 ? 2 : 1); ++lc)
+              for (int lb = 0; lb < 2; ++lb)
+                for (int la = 0; la < 2; ++la)
+                  lv.hpc[(i + la) + (long long)np0 * ((j + lb) + (long long)np1 * (dim == 3 ? k + lc : 0))] = 0;
+          }
+      const int npa[3] = {np0, np1, np2};
+      for (long long q = 0; q < lv.Np; ++q) {
+        const int idx[3] = {(int)(q % np0), (int)((q / np0) % np1), (int)(q / ((long long)np0 * np1))};
+        for (int a = 0; a < dim; ++a) {
+          if (!(m->dirichlet_faces & (1u << (2 * a))) && idx[a] == 0) lv.hpc[q] = 1;
+          if (!(m->dirichlet_faces & (1u << (2 * a + 1))) && idx[a] == npa[a] - 1) lv.hpc[q] = 1;
+        }
+      }
+    }
+    if (c->opt.coarse_mode != 1)
+      for (long long q = 0; q < c->lv[0].Np; ++q)
+        if (!c->lv[0].hpc[q]) c->hpfree.push_back((int)q);
+    c->nfp = (int)c->hpfree.size();
+    if ((long long)c->nfp * c->nfp > (1LL << 31)) return fail(GS_EINVAL, "coarsest pressure level too large");
+  }
   return GS_OK;
 }
 
@@ -353,8 +404,23 @@ void layout(gs_ctx* c, Arena& ar) {
   c->Ainv = ar.take<double>((long long)c->nf * c->nf);
   c->cfree = ar.take<int>(c->nf);
   c->ctmp = ar.take<double>(c->nf);
-  c->gjrow = ar.take<double>(c->nf);
-  c->gjcol = ar.take<double>(c->nf);
+  const int gjn = c->nf > c->nfp ? c->nf : c->nfp;
+  c->gjrow = ar.take<double>(gjn);
+  c->gjcol = ar.take<double>(gjn);
+  if (c->cc_alloc) {
+    for (int l = 0; l < c->L; ++l) {
+      Level& lv = c->lv[l];
+      lv.pcmask = ar.take<uint8_t>(lv.Np);
+      lv.pxA = takeT(lv.Np);
+      lv.pxB = takeT(lv.Np);
+      lv.pb = takeT(lv.Np);
+      lv.pd = takeT(lv.Np);
+      lv.pdinv = takeT(lv.Np);
+    }
+    c->PAinv = ar.take<double>((long long)c->nfp * c->nfp);
+    c->pcfree = ar.take<int>(c->nfp);
+    c->pctmp = ar.take<double>(c->nfp);
+  }
   const int m = c->opt.restart;
   c->V = ar.take<double>((long long)(m + 1) * c->N);
   c->Z = ar.take<double>((long long)m * c->N);
@@ -391,6 +457,14 @@ void set_geom(gs_ctx* c, const gs_mesh* m) {
     g.cvoid = lv.cvoid;
     lv.c64 = make_coef<double>(c->dim, lv.h, c->alpha);
     lv.c32 = make_coef<float>(c->dim, lv.h, c->alpha);
+    // Q1 stiffness coefficients kc[a] = prod_{b != a} h_b / (6^(d-1) h_a)
+    for (int a = 0; a < 3; ++a) {
+      if (a >= c->dim) { lv.pkc[a] = 0.0; continue; }
+      double v = 1.0 / lv.h[a];
+      for (int b = 0; b < c->dim; ++b)
+        if (b != a) v *= lv.h[b] / 6.0;
+      lv.pkc[a] = v;
+    }
   }
 }
 
@@ -463,36 +537,29 @@ uint64_t splitmix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// Lanczos estimate of lambda_max(D^{-1} A_l) on level l (Sec. 4 Chebyshev bounds)
-template <typename T>
-gs_status lanczos(gs_ctx* c, int l) {
-  Level& lv = c->lv[l];
-  const long long n = lv.nu;
+// Lanczos estimate of lambda_max(D^{-1} M) for a level operator M (Sec. 4 Chebyshev bounds):
+// `steps` Lanczos steps on D^{-1/2} M D^{-1/2} from a SplitMix64 start vector whose 64-bit
+// counter is (seed << 32) ^ (level_code << 56) ^ i; constrained entries are zeroed.
+template <typename T, typename ZeroFn, typename ApplyFn>
+gs_status lanczos_core(gs_ctx* c, long long n, int level_code, T* v, T* vprev, T* t, T* w, const T* dinv,
+                       ZeroFn zero, ApplyFn apply, double* lam) {
   std::vector<T> h0(n);
-  const uint64_t base = ((uint64_t)((uint32_t)c->opt.seed) << 32) ^ ((uint64_t)(l & 0xFF) << 56);
+  const uint64_t base = ((uint64_t)((uint32_t)c->opt.seed) << 32) ^ ((uint64_t)(level_code & 0xFF) << 56);
   for (long long i = 0; i < n; ++i) {
     const uint64_t r = splitmix64(base ^ (uint64_t)i);
     h0[i] = (T)(2.0 * ((double)(r >> 11) * (1.0 / 9007199254740992.0)) - 1.0);
   }
-  T* v = (T*)lv.xA;
-  T* vprev = (T*)lv.xB;
-  T* t = (T*)lv.d;
-  T* w = (T*)lv.b;
   CK(cudaMemcpyAsync(v, h0.data(), sizeof(T) * n, cudaMemcpyHostToDevice, c->st));
-  CK(launch_zero_constrained_u<T>(lv.g, v, c->st));
+  CK(zero(v));
   double nrm2;
   CKS(dot_host<T>(c, v, n, 1, v, n, &nrm2));
   CK(launch_cast<T, T>(v, v, n, (T)(1.0 / std::sqrt(nrm2)), c->st));
   CK(cudaMemsetAsync(vprev, 0, sizeof(T) * n, c->st));
   std::vector<double> al, be;
   double beta_prev = 0.0;
-  const T* dinv = (const T*)lv.dinv;
   for (int j = 0; j < c->opt.lanczos_steps; ++j) {
     CK(launch_lanczos_pre<T>(dinv, v, t, n, c->st));
-    TileArgs<T> a = tile_args<T>(lv);
-    a.xu = t;
-    a.yu = w;
-    CK(launch_tile<T>(c->dim, TILE_APPLY, OPS_A, a, c->st));
+    CK(apply((const T*)t, w));
     CK(launch_lanczos_post<T>(dinv, w, vprev, (T)beta_prev, w, n, c->st));
     double alpha;
     CKS(dot_host<T>(c, w, n, 1, v, n, &alpha));
@@ -509,9 +576,49 @@ gs_status lanczos(gs_ctx* c, int l) {
     beta_prev = beta;
   }
   be.resize(al.size() > 0 ? al.size() - 1 : 0);
-  lv.lam_hi = 1.2 * tridiag_max_eig(al, be);
-  if (!std::isfinite(lv.lam_hi) || lv.lam_hi <= 0.0) return fail(GS_EBREAKDOWN, "eigenvalue estimate failed");
+  *lam = 1.2 * tridiag_max_eig(al, be);
+  if (!std::isfinite(*lam) || *lam <= 0.0) return fail(GS_EBREAKDOWN, "eigenvalue estimate failed");
   return GS_OK;
+}
+
+template <typename T>
+gs_status lanczos(gs_ctx* c, int l) {
+  Level& lv = c->lv[l];
+  return lanczos_core<T>(
+      c, lv.nu, l, (T*)lv.xA, (T*)lv.xB, (T*)lv.d, (T*)lv.b, (const T*)lv.dinv,
+      [&](T* v) { return launch_zero_constrained_u<T>(lv.g, v, c->st); },
+      [&](const T* x, T* y) {
+        TileArgs<T> a = tile_args<T>(lv);
+        a.xu = x;
+        a.yu = y;
+        return launch_tile<T>(c->dim, TILE_APPLY, OPS_A, a, c->st);
+      },
+      &lv.lam_hi);
+}
+
+template <typename T>
+PLapArgs<T> plap_args(const Level& lv) {
+  PLapArgs<T> a{};
+  a.g = lv.g;
+  for (int i = 0; i < 3; ++i) a.kc[i] = (T)lv.pkc[i];
+  a.cmask = lv.pcmask;
+  return a;
+}
+
+// pressure level: the level-code field carries 0x80 | l to separate it from velocity level l
+template <typename T>
+gs_status plap_lanczos(gs_ctx* c, int l) {
+  Level& lv = c->lv[l];
+  return lanczos_core<T>(
+      c, lv.Np, 0x80 | l, (T*)lv.pxA, (T*)lv.pxB, (T*)lv.pd, (T*)lv.pb, (const T*)lv.pdinv,
+      [&](T* v) { return launch_mask_copy<T>(v, lv.pcmask, v, lv.Np, c->st); },
+      [&](const T* x, T* y) {
+        PLapArgs<T> a = plap_args<T>(lv);
+        a.x = x;
+        a.y = y;
+        return launch_plap<T>(TILE_APPLY, a, c->st);
+      },
+      &lv.plam_hi);
 }
 
 // host assembly of the dense coarse matrix on its free unknowns (same closed-form 1D matrices)
@@ -589,7 +696,56 @@ gs_status setup_T(gs_ctx* c) {
   for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(lanczos<T>(c, l));
   const Level& F = c->lv[c->L - 1];
   CK(launch_pdiag<T>(F.g, coef<T>(F), etap<T>(F), (T*)c->p_dinv, c->st));
+  if (c->cc) {
+    for (int l = 0; l < c->L; ++l) {
+      Level& lv = c->lv[l];
+      T kc[3] = {(T)lv.pkc[0], (T)lv.pkc[1], (T)lv.pkc[2]};
+      CK(launch_plap_diag<T>(lv.g, kc, lv.pcmask, (T*)lv.pdinv, c->st));
+    }
+    for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(plap_lanczos<T>(c, l));
+  }
   return GS_OK;
+}
+
+// host assembly of the dense coarse pressure Laplacian on its free nodes; with a pure Neumann
+// problem the rank-one term 1 1^T / n_free makes it invertible without changing its action on
+// mean-free vectors
+void assemble_coarse_plap(gs_ctx* c, std::vector<double>& A) {
+  const Level& lv = c->lv[0];
+  const int dim = c->dim, nf = c->nfp;
+  A.assign((size_t)nf * nf, 0.0);
+  std::vector<int> map(lv.Np, -1);
+  for (int i = 0; i < nf; ++i) map[c->hpfree[i]] = i;
+  const int np0 = lv.n[0] + 1, np1 = lv.n[1] + 1;
+  const int nb = dim == 2 ? 4 : 8;
+  for (int k = 0; k < lv.n[2]; ++k)
+    for (int j = 0; j < lv.n[1]; ++j)
+      for (int i = 0; i < lv.n[0]; ++i) {
+        const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+        if (lv.hvoid[cc]) continue;
+        for (int p = 0; p < nb; ++p) {
+          const int pa = p & 1, pb = (p >> 1) & 1, pc = p >> 2;
+          const int row = map[(i + pa) + (long long)np0 * ((j + pb) + (long long)np1 * (dim == 3 ? k + pc : 0))];
+          if (row < 0) continue;
+          for (int q = 0; q < nb; ++q) {
+            const int qa = q & 1, qb = (q >> 1) & 1, qc = q >> 2;
+            const int col = map[(i + qa) + (long long)np0 * ((j + qb) + (long long)np1 * (dim == 3 ? k + qc : 0))];
+            if (col < 0) continue;
+            const double k1a = pa == qa ? 1 : -1, ia = pa == qa ? 2 : 1;
+            const double k1b = pb == qb ? 1 : -1, ib = pb == qb ? 2 : 1;
+            double v;
+            if (dim == 2) {
+              v = lv.pkc[0] * k1a * ib + lv.pkc[1] * ia * k1b;
+            } else {
+              const double k1c = pc == qc ? 1 : -1, ic = pc == qc ? 2 : 1;
+              v = lv.pkc[0] * k1a * ib * ic + lv.pkc[1] * ia * k1b * ic + lv.pkc[2] * ia * ib * k1c;
+            }
+            A[(size_t)row * nf + col] += v;
+          }
+        }
+      }
+  if (c->psingular)
+    for (size_t q = 0; q < A.size(); ++q) A[q] += 1.0 / nf;
 }
 
 gs_status setup(gs_ctx* c) {
@@ -616,6 +772,23 @@ gs_status setup(gs_ctx* c) {
     for (int k = 0; k < c->nf; ++k) {
       CK(launch_gj_save(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
       CK(launch_gj_update(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+  }
+  if (c->cc) {
+    for (int l = 0; l < c->L; ++l) {
+      Level& lv = c->lv[l];
+      CK(cudaMemcpyAsync(lv.pcmask, lv.hpc.data(), lv.Np, cudaMemcpyHostToDevice, c->st));
+    }
+  }
+  if (c->cc && c->nfp > 0) {
+    std::vector<double> A;
+    assemble_coarse_plap(c, A);
+    CK(cudaMemcpyAsync(c->PAinv, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->pcfree, c->hpfree.data(), sizeof(int) * c->nfp, cudaMemcpyHostToDevice, c->st));
+    for (int k = 0; k < c->nfp; ++k) {
+      CK(launch_gj_save(c->PAinv, c->nfp, k, c->gjrow, c->gjcol, c->st));
+      CK(launch_gj_update(c->PAinv, c->nfp, k, c->gjrow, c->gjcol, c->st));
     }
     CK(cudaStreamSynchronize(c->st));
   }
@@ -699,6 +872,70 @@ gs_status schur_inv(gs_ctx* c, const T* b) {
   return GS_OK;
 }
 
+// Chebyshev smoother of the pressure Laplacian on level l (result in lv.pxA)
+template <typename T>
+gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init) {
+  Level& lv = c->lv[l];
+  const double hi = lv.plam_hi, lo = hi / 15.0;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+  const int k = c->opt.cheb_degree;
+  T* dinv = (T*)lv.pdinv;
+  T* d = (T*)lv.pd;
+  if (zero_init) {
+    KL(K_SCHUR, launch_cheb_init0<T>(b, dinv, (T)(1.0 / theta), d, (T*)lv.pxA, lv.Np, c->st));
+  } else {
+    PLapArgs<T> a = plap_args<T>(lv);
+    a.x = (const T*)lv.pxA; a.b = b; a.d = d; a.dinv = dinv; a.xout = (T*)lv.pxB;
+    a.c1 = 0; a.c2 = (T)(1.0 / theta); a.use_d = 0;
+    KL(K_SCHUR, launch_plap<T>(TILE_CHEB, a, c->st));
+    std::swap(lv.pxA, lv.pxB);
+  }
+  double rho = 1.0 / sigma;
+  for (int t = 1; t < k; ++t) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    PLapArgs<T> a = plap_args<T>(lv);
+    a.x = (const T*)lv.pxA; a.b = b; a.d = d; a.dinv = dinv; a.xout = (T*)lv.pxB;
+    a.c1 = (T)(rn * rho); a.c2 = (T)(2.0 * rn / delta); a.use_d = 1;
+    KL(K_SCHUR, launch_plap<T>(TILE_CHEB, a, c->st));
+    std::swap(lv.pxA, lv.pxB);
+    rho = rn;
+  }
+  return GS_OK;
+}
+
+// V-cycle for the pressure Laplacian: input lv.pb, output lv.pxA
+template <typename T>
+gs_status pvcycle(gs_ctx* c, int l) {
+  Level& lv = c->lv[l];
+  if (l == 0) {
+    if (c->opt.coarse_mode == 1) return pcheb<T>(c, 0, (const T*)lv.pb, true);
+    KL(K_SCHUR, launch_coarse_solve<T>(c->PAinv, c->pcfree, c->nfp, (const T*)lv.pb, (T*)lv.pxA, lv.Np, c->pctmp, c->st));
+    return GS_OK;
+  }
+  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(pcheb<T>(c, l, (const T*)lv.pb, s == 0));
+  {
+    PLapArgs<T> a = plap_args<T>(lv);
+    a.x = (const T*)lv.pxA; a.b = (const T*)lv.pb; a.y = (T*)lv.pd;
+    KL(K_SCHUR, launch_plap<T>(TILE_RESID, a, c->st));
+  }
+  Level& cl = c->lv[l - 1];
+  KL(K_SCHUR, launch_p_restrict<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, (const T*)lv.pd, (T*)cl.pb, c->st));
+  CKS(pvcycle<T>(c, l - 1));
+  KL(K_SCHUR, launch_p_prolong_add<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, (const T*)cl.pxA, (T*)lv.pxA, c->st));
+  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(pcheb<T>(c, l, (const T*)lv.pb, false));
+  return GS_OK;
+}
+
+// Cahouet-Chabard term K_p^{-1} r ~ one pressure V-cycle, constrained entries zero; result in
+// the finest level's pxA
+template <typename T>
+gs_status plap_inverse(gs_ctx* c, const T* r) {
+  Level& F = c->lv[c->L - 1];
+  KL(K_VEC, launch_mask_copy<T>(r, F.pcmask, (T*)F.pb, F.Np, c->st));
+  CKS(pvcycle<T>(c, c->L - 1));
+  return GS_OK;
+}
+
 gs_status project_pressure(gs_ctx* c, double* x) {
   if (!c->nullspace) return GS_OK;
   const Level& F = c->lv[c->L - 1];
@@ -716,7 +953,14 @@ gs_status precond_T(gs_ctx* c, const double* v, double* z) {
   Level& F = c->lv[c->L - 1];
   KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)c->p_b, F.Np, (T)1, c->st));
   CKS(schur_inv<T>(c, (const T*)c->p_b));
-  KL(K_VEC, launch_cast<T, T>((const T*)c->p_xA, (T*)c->p_xB, F.Np, (T)(-1), c->st));  // z_p in p_xB
+  if (c->cc) {
+    // z_p = -(M_p(1/eta)^{-1} r_p + alpha K_p^{-1} r_p)  (Cahouet-Chabard)
+    CKS(plap_inverse<T>(c, (const T*)c->p_b));
+    KL(K_VEC, launch_cc_combine<T>((const T*)c->p_xA, (const T*)F.pxA, F.pcmask, (T)c->alpha, (T*)c->p_xB, F.Np,
+                                   c->st));
+  } else {
+    KL(K_VEC, launch_cast<T, T>((const T*)c->p_xA, (T*)c->p_xB, F.Np, (T)(-1), c->st));  // z_p in p_xB
+  }
   KL(K_VEC, launch_cast<double, T>(v, (T*)F.d, F.nu, (T)1, c->st));
   {
     TileArgs<T> a = tile_args<T>(F);
@@ -921,6 +1165,29 @@ gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, co
       CK(launch_pmass<T>(TILE_APPLY, a, c->st));
       return GS_OK;
     }
+    case GS_OP_PLAP: {
+      if (!c->cc) return fail(GS_EINVAL, "pressure Laplacian needs the Cahouet-Chabard Schur term");
+      PLapArgs<T> a = plap_args<T>(lv);
+      a.x = x; a.y = y;
+      CK(launch_plap<T>(TILE_APPLY, a, c->st));
+      return GS_OK;
+    }
+    case GS_OP_PLAP_INV: {
+      if (!c->cc || !finest || !mgprec) return fail(GS_EINVAL, "pressure V-cycle: CC active, finest level, MG precision");
+      CKS(plap_inverse<T>(c, x));
+      CK(launch_mask_copy<T>((const T*)lv.pxA, lv.pcmask, y, lv.Np, c->st));
+      return GS_OK;
+    }
+    case GS_OP_PRESTRICT:
+    case GS_OP_PPROLONGATE: {
+      if (!c->cc || l == 0) return fail(GS_EINVAL, "pressure transfer: CC active, level >= 1");
+      const Level& cl = c->lv[l - 1];
+      if (op == GS_OP_PRESTRICT)
+        CK(launch_p_restrict<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, x, y, c->st));
+      else
+        CK(launch_p_prolong_add<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, x, y, c->st));
+      return GS_OK;
+    }
     case GS_OP_SCHUR_INV: {
       if (!finest || !mgprec) return fail(GS_EINVAL, "Schur inverse: finest level, MG precision");
       CKS(schur_inv<T>(c, x));
@@ -974,6 +1241,7 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
   Arena ar;
   ar.base = (char*)workspace;
   layout(c, ar);
+  c->cc = c->cc_alloc && (c->opt.schur_kind == 2 || alpha > 0.0);
   set_geom(c, mesh);
   cudaError_t e = cudaMallocHost(&c->hpin, sizeof(double) * (c->opt.restart + 8));
   if (e != cudaSuccess) { delete c; return fail(GS_ECUDA, std::string("pinned buffer: ") + cudaGetErrorString(e)); }
@@ -1091,6 +1359,9 @@ gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
   out->coarse_free = c->nf;
   out->footprint_bytes = c->footprint;
   out->kernel_launches = launches_total();
+  out->schur_cc = c->cc ? 1 : 0;
+  out->pressure_coarse_free = c->nfp;
+  for (int l = 0; l < c->L && l < 16; ++l) out->plambda_max[l] = c->lv[l].plam_hi;
   return GS_OK;
 }
 

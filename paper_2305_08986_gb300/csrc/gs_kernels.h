@@ -71,6 +71,43 @@ cudaError_t launch_pmass(int mode, PMassArgs<T> a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_pdiag(const Geom& g, const OpCoef<T>& c, const T* eta, T* dinv, cudaStream_t st);
 
+// Pressure Laplacian K_p (Q1 stiffness over active cells; nodes with cmask != 0 are identity
+// rows / zero columns).  Cell matrix: sum_a kc[a] (K1 in direction a, Pi elsewhere), with
+// K1 = [1 -1; -1 1], Pi = [2 1; 1 2], kc[a] = prod_{b != a} h_b / (6^(d-1) h_a).
+// Modes as for the tile kernel: APPLY y = K x; RESID y = b - K x; CHEB fused Chebyshev step.
+template <typename T>
+struct PLapArgs {
+  Geom g;
+  T kc[3];
+  const uint8_t* cmask;
+  const T* x;
+  T* y;
+  const T* b;
+  T* d;
+  const T* dinv;
+  T* xout;
+  T c1, c2;
+  int use_d;
+};
+template <typename T>
+cudaError_t launch_plap(int mode, PLapArgs<T> a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_plap_diag(const Geom& g, const T* kc, const uint8_t* cmask, T* dinv, cudaStream_t st);
+// Q1 transfers between pressure levels (bilinear interpolation and its transpose)
+template <typename T>
+cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* rf,
+                              T* rc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_p_prolong_add(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* xc,
+                                 T* xf, cudaStream_t st);
+// out[i] = mask[i] ? 0 : in[i]   (may run in place)
+template <typename T>
+cudaError_t launch_mask_copy(const T* in, const uint8_t* mask, T* out, long long n, cudaStream_t st);
+// z[i] = -(m[i] + alpha * (mask[i] ? 0 : v[i]))   (Cahouet-Chabard combination)
+template <typename T>
+cudaError_t launch_cc_combine(const T* m, const T* v, const uint8_t* mask, T alpha, T* z, long long n,
+                              cudaStream_t st);
+
 // ---- vector kernels ----
 template <typename T>
 cudaError_t launch_cheb_init0(const T* b, const T* dinv, T inv_theta, T* d, T* x, long long n,

@@ -302,3 +302,227 @@ INST(double)
 #undef INST
 
 }  // namespace gs
+
+// ---- pressure Laplacian K_p (Cahouet-Chabard term of the Schur approximation) ----------------------
+namespace gs {
+
+template <typename T, int DIM, int MODE>
+__global__ void k_plap(const PLapArgs<T> A) {
+  const Geom& g = A.g;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.Np) return;
+  int I, J, K;
+  unflat(q, g.npn, DIM, I, J, K);
+  const bool con = A.cmask[q] != 0;
+  T kx = T(0);
+  if (!con) {
+    const int idx[3] = {I, J, K};
+    int cl[3][2], cnt[3];
+    for (int ax = 0; ax < DIM; ++ax) {
+      cnt[ax] = 0;
+      if (idx[ax] - 1 >= 0) cl[ax][cnt[ax]++] = idx[ax] - 1;
+      if (idx[ax] < g.n[ax]) cl[ax][cnt[ax]++] = idx[ax];
+    }
+    const int c2n = DIM == 3 ? cnt[2] : 1;
+    for (int k = 0; k < c2n; ++k)
+      for (int j = 0; j < cnt[1]; ++j)
+        for (int i = 0; i < cnt[0]; ++i) {
+          const int c0 = cl[0][i], c1 = cl[1][j], c2 = DIM == 3 ? cl[2][k] : 0;
+          const long long cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
+          if (cell_void(g, cell)) continue;
+          const int la = I - c0, lb = J - c1, lc = DIM == 3 ? K - c2 : 0;
+          for (int rc = 0; rc < (DIM == 3 ? 2 : 1); ++rc)
+            for (int rb = 0; rb < 2; ++rb)
+              for (int ra = 0; ra < 2; ++ra) {
+                const long long r = (c0 + ra) + (long long)g.npn[0] * ((c1 + rb) + (long long)g.npn[1] * (c2 + rc));
+                if (A.cmask[r]) continue;
+                const T k1a = la == ra ? T(1) : T(-1), pa = la == ra ? T(2) : T(1);
+                const T k1b = lb == rb ? T(1) : T(-1), pb = lb == rb ? T(2) : T(1);
+                T w;
+                if (DIM == 2) {
+                  w = A.kc[0] * k1a * pb + A.kc[1] * pa * k1b;
+                } else {
+                  const T k1c = lc == rc ? T(1) : T(-1), pc = lc == rc ? T(2) : T(1);
+                  w = A.kc[0] * k1a * pb * pc + A.kc[1] * pa * k1b * pc + A.kc[2] * pa * pb * k1c;
+                }
+                kx += w * A.x[r];
+              }
+        }
+  }
+  const T kq = con ? A.x[q] : kx;
+  if (MODE == TILE_APPLY) {
+    A.y[q] = kq;
+  } else if (MODE == TILE_RESID) {
+    A.y[q] = A.b[q] - kq;
+  } else {
+    const T r = A.b[q] - kq;
+    T dn = A.c2 * A.dinv[q] * r;
+    if (A.use_d) dn += A.c1 * A.d[q];
+    A.d[q] = dn;
+    A.xout[q] = A.x[q] + dn;
+  }
+}
+
+template <typename T, int DIM>
+__global__ void k_plap_diag(const Geom g, const T k0, const T k1, const T k2, const uint8_t* __restrict__ cmask,
+                            T* __restrict__ dinv) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= g.Np) return;
+  if (cmask[q]) { dinv[q] = T(1); return; }
+  int I, J, K;
+  unflat(q, g.npn, DIM, I, J, K);
+  const int idx[3] = {I, J, K};
+  int cl[3][2], cnt[3];
+  for (int ax = 0; ax < DIM; ++ax) {
+    cnt[ax] = 0;
+    if (idx[ax] - 1 >= 0) cl[ax][cnt[ax]++] = idx[ax] - 1;
+    if (idx[ax] < g.n[ax]) cl[ax][cnt[ax]++] = idx[ax];
+  }
+  int nact = 0;
+  const int c2n = DIM == 3 ? cnt[2] : 1;
+  for (int k = 0; k < c2n; ++k)
+    for (int j = 0; j < cnt[1]; ++j)
+      for (int i = 0; i < cnt[0]; ++i) {
+        const long long cell = cl[0][i] + (long long)g.n[0] * (cl[1][j] + (long long)g.n[1] * (DIM == 3 ? cl[2][k] : 0));
+        if (!cell_void(g, cell)) nact++;
+      }
+  const T per_cell = DIM == 2 ? T(2) * (k0 + k1) : T(4) * (k0 + k1 + k2);
+  dinv[q] = T(1) / (T(nact) * per_cell);
+}
+
+template <typename T, int DIM>
+__global__ void k_p_restrict(const Geom gf, const Geom gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
+                             const T* __restrict__ rf, T* __restrict__ rc) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= gc.Np) return;
+  if (mc[q]) { rc[q] = T(0); return; }
+  int I, J, K;
+  unflat(q, gc.npn, DIM, I, J, K);
+  const int idx[3] = {I, J, K};
+  int f[3][3], m[3];
+  T w[3][3];
+  for (int ax = 0; ax < 3; ++ax) {
+    m[ax] = 0;
+    if (ax >= DIM) { f[ax][0] = 0; w[ax][0] = T(1); m[ax] = 1; continue; }
+    const int C = idx[ax];
+    const int cand[3] = {2 * C - 1, 2 * C, 2 * C + 1};
+    const T ww[3] = {T(0.5), T(1), T(0.5)};
+    for (int t = 0; t < 3; ++t)
+      if (cand[t] >= 0 && cand[t] < gf.npn[ax]) { f[ax][m[ax]] = cand[t]; w[ax][m[ax]] = ww[t]; m[ax]++; }
+  }
+  T acc = T(0);
+  for (int k = 0; k < m[2]; ++k)
+    for (int j = 0; j < m[1]; ++j)
+      for (int i = 0; i < m[0]; ++i) {
+        const long long fq = f[0][i] + (long long)gf.npn[0] * (f[1][j] + (long long)gf.npn[1] * f[2][k]);
+        if (mf[fq]) continue;
+        acc += w[0][i] * w[1][j] * w[2][k] * rf[fq];
+      }
+  rc[q] = acc;
+}
+
+template <typename T, int DIM>
+__global__ void k_p_prolong_add(const Geom gf, const Geom gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
+                                const T* __restrict__ xc, T* __restrict__ xf) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= gf.Np) return;
+  if (mf[q]) return;
+  int I, J, K;
+  unflat(q, gf.npn, DIM, I, J, K);
+  const int idx[3] = {I, J, K};
+  int cidx[3][2], m[3];
+  T w[3][2];
+  for (int ax = 0; ax < 3; ++ax) {
+    if (ax >= DIM) { cidx[ax][0] = 0; w[ax][0] = T(1); m[ax] = 1; continue; }
+    const int v = idx[ax];
+    if (!(v & 1)) { cidx[ax][0] = v >> 1; w[ax][0] = T(1); m[ax] = 1; }
+    else { cidx[ax][0] = v >> 1; cidx[ax][1] = (v >> 1) + 1; w[ax][0] = w[ax][1] = T(0.5); m[ax] = 2; }
+  }
+  T acc = T(0);
+  for (int k = 0; k < m[2]; ++k)
+    for (int j = 0; j < m[1]; ++j)
+      for (int i = 0; i < m[0]; ++i) {
+        const long long cq = cidx[0][i] + (long long)gc.npn[0] * (cidx[1][j] + (long long)gc.npn[1] * cidx[2][k]);
+        if (mc[cq]) continue;
+        acc += w[0][i] * w[1][j] * w[2][k] * xc[cq];
+      }
+  xf[q] += acc;
+}
+
+template <typename T>
+__global__ void k_mask_copy(const T* in, const uint8_t* __restrict__ mask, T* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = mask[i] ? T(0) : in[i];
+}
+template <typename T>
+__global__ void k_cc_combine(const T* __restrict__ m, const T* __restrict__ v, const uint8_t* __restrict__ mask, T alpha,
+                             T* __restrict__ z, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    z[i] = -(m[i] + alpha * (mask[i] ? T(0) : v[i]));
+}
+
+template <typename T>
+cudaError_t launch_plap(int mode, PLapArgs<T> a, cudaStream_t st) {
+  const unsigned nb = nblk(a.g.Np);
+  if (a.g.dim == 2) {
+    if (mode == TILE_APPLY) k_plap<T, 2, TILE_APPLY><<<nb, TPB, 0, st>>>(a);
+    else if (mode == TILE_RESID) k_plap<T, 2, TILE_RESID><<<nb, TPB, 0, st>>>(a);
+    else k_plap<T, 2, TILE_CHEB><<<nb, TPB, 0, st>>>(a);
+  } else {
+    if (mode == TILE_APPLY) k_plap<T, 3, TILE_APPLY><<<nb, TPB, 0, st>>>(a);
+    else if (mode == TILE_RESID) k_plap<T, 3, TILE_RESID><<<nb, TPB, 0, st>>>(a);
+    else k_plap<T, 3, TILE_CHEB><<<nb, TPB, 0, st>>>(a);
+  }
+  return launched(cudaGetLastError());
+}
+template <typename T>
+cudaError_t launch_plap_diag(const Geom& g, const T* kc, const uint8_t* cmask, T* dinv, cudaStream_t st) {
+  if (g.dim == 2)
+    k_plap_diag<T, 2><<<nblk(g.Np), TPB, 0, st>>>(g, kc[0], kc[1], kc[2], cmask, dinv);
+  else
+    k_plap_diag<T, 3><<<nblk(g.Np), TPB, 0, st>>>(g, kc[0], kc[1], kc[2], cmask, dinv);
+  return launched(cudaGetLastError());
+}
+template <typename T>
+cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* rf, T* rc,
+                              cudaStream_t st) {
+  if (gf.dim == 2)
+    k_p_restrict<T, 2><<<nblk(gc.Np), TPB, 0, st>>>(gf, gc, mf, mc, rf, rc);
+  else
+    k_p_restrict<T, 3><<<nblk(gc.Np), TPB, 0, st>>>(gf, gc, mf, mc, rf, rc);
+  return launched(cudaGetLastError());
+}
+template <typename T>
+cudaError_t launch_p_prolong_add(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* xc,
+                                 T* xf, cudaStream_t st) {
+  if (gf.dim == 2)
+    k_p_prolong_add<T, 2><<<nblk(gf.Np), TPB, 0, st>>>(gf, gc, mf, mc, xc, xf);
+  else
+    k_p_prolong_add<T, 3><<<nblk(gf.Np), TPB, 0, st>>>(gf, gc, mf, mc, xc, xf);
+  return launched(cudaGetLastError());
+}
+template <typename T>
+cudaError_t launch_mask_copy(const T* in, const uint8_t* mask, T* out, long long n, cudaStream_t st) {
+  k_mask_copy<T><<<nblk(n), TPB, 0, st>>>(in, mask, out, n);
+  return launched(cudaGetLastError());
+}
+template <typename T>
+cudaError_t launch_cc_combine(const T* m, const T* v, const uint8_t* mask, T alpha, T* z, long long n, cudaStream_t st) {
+  k_cc_combine<T><<<nblk(n), TPB, 0, st>>>(m, v, mask, alpha, z, n);
+  return launched(cudaGetLastError());
+}
+
+#define INSTP(T)                                                                                          \
+  template cudaError_t launch_plap<T>(int, PLapArgs<T>, cudaStream_t);                                    \
+  template cudaError_t launch_plap_diag<T>(const Geom&, const T*, const uint8_t*, T*, cudaStream_t);      \
+  template cudaError_t launch_p_restrict<T>(const Geom&, const Geom&, const uint8_t*, const uint8_t*,      \
+                                            const T*, T*, cudaStream_t);                                  \
+  template cudaError_t launch_p_prolong_add<T>(const Geom&, const Geom&, const uint8_t*, const uint8_t*,   \
+                                               const T*, T*, cudaStream_t);                               \
+  template cudaError_t launch_mask_copy<T>(const T*, const uint8_t*, T*, long long, cudaStream_t);        \
+  template cudaError_t launch_cc_combine<T>(const T*, const T*, const uint8_t*, T, T*, long long, cudaStream_t);
+INSTP(float)
+INSTP(double)
+#undef INSTP
+
+}  // namespace gs

@@ -23,7 +23,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ENOCONV, GS_EBREAKDOWN, GS_ETIMEOUT = range(7)
 (OP_A, OP_RESIDUAL_A, OP_DIAG_A, OP_SMOOTH, OP_RESTRICT, OP_PROLONGATE, OP_B, OP_BT,
- OP_SCHUR_MASS, OP_SCHUR_INV, OP_COARSE, OP_PRECOND, OP_A_RAW) = range(13)
+ OP_SCHUR_MASS, OP_SCHUR_INV, OP_COARSE, OP_PRECOND, OP_A_RAW, OP_PLAP, OP_PLAP_INV, OP_PRESTRICT,
+ OP_PPROLONGATE) = range(17)
 
 
 class GsMesh(ctypes.Structure):
@@ -34,7 +35,8 @@ class GsMesh(ctypes.Structure):
 class GsOptions(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("smooth_steps", ctypes.c_int), ("restart", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("mg_precision", ctypes.c_int), ("schur_degree", ctypes.c_int),
-                ("lanczos_steps", ctypes.c_int), ("seed", ctypes.c_int), ("coarse_mode", ctypes.c_int)]
+                ("lanczos_steps", ctypes.c_int), ("seed", ctypes.c_int), ("coarse_mode", ctypes.c_int),
+                ("schur_kind", ctypes.c_int)]
 
 
 class GsInfo(ctypes.Structure):
@@ -43,7 +45,8 @@ class GsInfo(ctypes.Structure):
                 ("last_iterations", ctypes.c_int), ("last_rel_residual", ctypes.c_double),
                 ("lambda_max", ctypes.c_double * 16), ("level_n_u", ctypes.c_longlong * 16),
                 ("coarse_free", ctypes.c_int), ("footprint_bytes", ctypes.c_size_t),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("schur_cc", ctypes.c_int),
+                ("pressure_coarse_free", ctypes.c_int), ("plambda_max", ctypes.c_double * 16)]
 
 
 class GsKernelStat(ctypes.Structure):

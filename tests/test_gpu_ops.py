@@ -188,3 +188,33 @@ def test_fullsize_spheres_apply_sampled():
     rows = rng.choice(m.n_u, 200, replace=False)
     ref = apply_A_rows(m, p.eta, p.alpha, x, rows)
     assert np.linalg.norm(yt.cpu().numpy()[rows] - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_pressure_laplacian_transfers_vcycle(case):
+    """Cahouet-Chabard pieces: K_p apply, Q1 transfers, Lanczos bounds and the pressure V-cycle
+    (FP64 multigrid) against oracle/pressure.py."""
+    from oracle.pressure import PressureHierarchy
+    p, s, torch = _setup(case, mg_precision=64)
+    m = mesh_from_problem(p)
+    H = PressureHierarchy(m, p.levels)
+    inf = s.info()
+    assert inf.schur_cc == 1
+    L = p.levels - 1
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal(m.Np)
+    y = torch.empty(m.Np, dtype=torch.float64, device="cuda")
+    s.apply_level(L, 13, torch.tensor(x, device="cuda"), y)
+    assert rel(y.cpu().numpy(), H.levels[L]["K"] @ x) <= 1e-12
+    for l in range(1, p.levels):
+        assert abs(inf.plambda_max[l] - H.levels[l]["lam_hi"]) <= 1e-10 * H.levels[l]["lam_hi"]
+    P = H.levels[L]["P"]
+    rc = torch.empty(P.shape[1], dtype=torch.float64, device="cuda")
+    s.apply_level(L, 15, torch.tensor(x, device="cuda"), rc)
+    assert rel(rc.cpu().numpy(), P.T @ x) <= 1e-14
+    xc = rng.standard_normal(P.shape[1])
+    xf = torch.tensor(x, device="cuda")
+    s.apply_level(L, 16, torch.tensor(xc, device="cuda"), xf)
+    assert rel(xf.cpu().numpy(), x + P @ xc) <= 1e-14
+    s.apply_level(L, 14, torch.tensor(x, device="cuda"), y)
+    assert rel(y.cpu().numpy(), H.apply_inverse(x)) <= 1e-10

@@ -90,6 +90,40 @@ def test_solve_parity(name, prec):
         assert abs(it - ito) <= max(2, 0.05 * ito), (it, ito)
 
 
+@pytest.mark.parametrize("name", ["channel_small", "box3d"])
+def test_solve_parity_mass_schur(name):
+    """The 1/eta-weighted pressure mass alone as Schur approximation (schur_kind = 1)."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS[name]()
+    m = mesh_from_problem(p)
+    o = StokesOracle(m, p.eta, p.alpha, p.levels, schur="mass")
+    b_ref = o.sys.lift_rhs(p.f, p.g)
+    s = gs.Solver.from_problem(p, mg_precision=64, schur_kind=1, max_iter=2000)
+    assert s.info().schur_cc == 0
+    b = torch.tensor(b_ref, device="cuda")
+    x = torch.zeros_like(b)
+    it, rr, _ = s.solve(b, x, tol=1e-9)
+    xo, ito, relo, _ = o.solve(b_ref, tol=1e-9, max_iter=2000)
+    assert rr <= 1e-9
+    assert rel(normalize_pressure(m, o.sys, x.cpu().numpy()), normalize_pressure(m, o.sys, xo)) <= 1e-6
+    assert abs(it - ito) <= max(2, 0.05 * ito), (it, ito)
+
+
+def test_cahouet_chabard_iterations():
+    """alpha = 1e3 channel: FP32 multigrid with the Cahouet-Chabard term stays in the tens of
+    iterations (the mass-only Schur approximation needs several hundred)."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = inputs.config_channel(nx=320, ny=56, levels=4)
+    s = gs.Solver.from_problem(p)
+    b = torch.empty(s.n_total, dtype=torch.float64, device="cuda")
+    s.lift_rhs(torch.tensor(p.f, device="cuda"), torch.tensor(p.g, device="cuda"), b)
+    x = torch.zeros_like(b)
+    it, rr, _ = s.solve(b, x, tol=1e-8)
+    assert rr <= 1e-8 and it < 50, it
+
+
 def test_solve_tolerance_1e8_oracle_residual():
     import torch
     from paper_2305_08986_gb300 import gs
