@@ -109,26 +109,49 @@ cudaError_t launch_lanczos_post(const T* dinv, const T* y, const T* vprev, T bet
   return launched(cudaGetLastError());
 }
 
-// ---- multi-dot: part[i*G + blk] = sum_{e in chunk(blk)} V[i][e] w[e] ------------------------------
-template <typename T>
+// ---- multi-dot: part[i*G + blk] = sum over the block's elements of V[i][e] w[e] ------------------
+// Tall-skinny V^T w: every thread keeps KB accumulators, so w is read once per KB basis vectors
+// and the block reduces KB sums at once (one barrier pair per KB vectors).  Deterministic: the
+// element-to-thread assignment and the reduction tree are fixed by the launch shape.
+template <typename T, int KB>
 __global__ void k_dots_partial(const T* __restrict__ V, long long ldv, int k, const T* __restrict__ w,
                                long long n, double* __restrict__ part) {
-  __shared__ double sh[32];
-  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
-  const long long lo = blockIdx.x * chunk;
-  const long long hi = min(n, lo + chunk);
-  for (int i = 0; i < k; ++i) {
-    const T* v = V + i * ldv;
-    double s = 0.0;
-    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) s += (double)v[e] * (double)w[e];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) part[(long long)i * gridDim.x + blockIdx.x] = s;
+  __shared__ double sh[KB][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 < k; i0 += KB) {
+    const int kb = min(KB, k - i0);
+    double acc[KB];
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+      const double we = (double)w[e];
+#pragma unroll
+      for (int i = 0; i < KB; ++i)
+        if (i < kb) acc[i] += (double)V[(i0 + i) * ldv + e] * we;
+    }
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+      double v = acc[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[i][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kb) {
+      double s = 0.0;
+      for (int q = 0; q < nw; ++q) s += sh[threadIdx.x][q];
+      part[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
   }
 }
 template <typename T>
 cudaError_t launch_dots_partial(const T* V, long long ldv, int k, const T* w, long long n, double* part, int G,
                                 cudaStream_t st) {
-  k_dots_partial<T><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part);
+  if (k <= 1)
+    k_dots_partial<T, 1><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part);
+  else
+    k_dots_partial<T, 8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part);
   return launched(cudaGetLastError());
 }
 

@@ -39,6 +39,8 @@ enum TileOps { OPS_A = 1, OPS_BT = 2, OPS_B = 4 };
 
 template <typename T>
 cudaError_t launch_tile(int dim, int mode, int ops, TileArgs<T> a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, T* out, int invert,

@@ -1,5 +1,6 @@
 // Cell-tile kernel for the blocks A, B^T (velocity rows) and B (pressure rows) of the saddle
-// operator (Eq. "stokes-discrete-block"), matrix-free on Cartesian Q2-Q1 cells.
+// operator (Eq. "stokes-discrete-block"), matrix-free on Cartesian Q2-Q1 hexahedra (3D; the 2D
+// path is gs_tile2d.cu).
 //
 // Work decomposition.  A CTA owns a box of TO^d cells and the velocity / pressure nodes whose
 // global index lies in [2 cs, 2 (cs + TO)) (resp. [cs, cs + TO)) per axis, plus the last node
@@ -19,7 +20,7 @@ namespace gs {
 template <int DIM>
 struct TileShape;
 template <>
-struct TileShape<2> {  // 32 x 16 evaluated cells, 31 x 15 owned; one thread per 2x2 group
+struct TileShape<2> {  // (2D launches use gs_tile2d.cu; kept for completeness of the template)
   static constexpr int TC0 = 32, TC1 = 16, TC2 = 1;
   static constexpr int G0 = 16, G1 = 8, G2 = 1;
   static constexpr int SPLIT = 1;
@@ -298,11 +299,7 @@ static cudaError_t dispatch_ops(int ops, TileArgs<T> a, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_tile(int dim, int mode, int ops, TileArgs<T> a, cudaStream_t st) {
   if (mode == TILE_CHEB && ops != OPS_A) return cudaErrorInvalidValue;
-  if (dim == 2) {
-    if (mode == TILE_APPLY) return dispatch_ops<T, 2, TILE_APPLY>(ops, a, st);
-    if (mode == TILE_RESID) return dispatch_ops<T, 2, TILE_RESID>(ops, a, st);
-    return launch_one<T, 2, TILE_CHEB, true, false, false>(a, st);
-  }
+  if (dim == 2) return launch_tile2d<T>(mode, ops, a, st);  // gs_tile2d.cu
   if (mode == TILE_APPLY) return dispatch_ops<T, 3, TILE_APPLY>(ops, a, st);
   if (mode == TILE_RESID) return dispatch_ops<T, 3, TILE_RESID>(ops, a, st);
   return launch_one<T, 3, TILE_CHEB, true, false, false>(a, st);
