@@ -101,6 +101,11 @@ typedef struct {            /* zero-initialised = defaults */
                                2: Cahouet-Chabard S^{-1} ~ M_p(1/eta)^{-1} + alpha K_p^{-1}, K_p the
                                   Q1 pressure Laplacian (p = 0 on faces without a velocity
                                   Dirichlet condition), inverted by one multigrid V-cycle */
+  int orth;                 /* 0: classical Gram-Schmidt always applied twice (CGS2, default);
+                               1: second pass only when the new vector's norm drops below
+                                  1/sqrt(2) of its value before the projection */
+  int graphs;               /* 0: replay the preconditioner's fixed launch sequence as a CUDA graph
+                                  captured at its second application (default); 1: plain launches */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */

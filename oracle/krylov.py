@@ -10,7 +10,9 @@ Sec. 4; it stops on the Euclidean norm of the residual.  Readings taken here:
   default), with the implicit (Givens) estimate during the cycle and an explicit
   check b - K x at exit; if the explicit check fails, the method restarts, at
   most 3 extra times;
-* restart length m = 50; orthogonalisation = classical Gram-Schmidt applied twice;
+* restart length m = 50; orthogonalisation = classical Gram-Schmidt applied twice ("cgs2");
+  option "selective": the second pass only when the new vector's norm drops below 1/sqrt(2)
+  of its value before the projection (Daniel-Gragg-Kaufman-Stewart criterion);
 * Schur approximation S^{-1} ~ M_p(1/eta)^{-1} (+ alpha K_p^{-1}, Cahouet-Chabard, when alpha > 0;
   see pressure.py);
 * preconditioner (block upper triangular):  z_p = -S^{-1} r_p,
@@ -36,8 +38,16 @@ from .mg import Hierarchy, schur_apply_inv
 from .pressure import PressureHierarchy
 
 
-def fgmres(apply_K, apply_M, b, x0=None, tol=1e-8, restart=50, max_iter=1000, max_extra=3):
-    """Returns (x, iterations, explicit relative residual, history of implicit estimates)."""
+REORTH_KAPPA = 1.0 / math.sqrt(2.0)
+
+
+def fgmres(apply_K, apply_M, b, x0=None, tol=1e-8, restart=50, max_iter=1000, max_extra=3,
+           orth="cgs2"):
+    """Returns (x, iterations, explicit relative residual, history of implicit estimates).
+
+    orth = "cgs2": classical Gram-Schmidt applied twice; "selective": classical Gram-Schmidt
+    with a second pass only when the norm of the new vector drops below 1/sqrt(2) of its norm
+    before the projection (Daniel, Gragg, Kaufman, Stewart 1976)."""
     n = len(b)
     bnorm = float(np.linalg.norm(b))
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=float)
@@ -64,12 +74,15 @@ def fgmres(apply_K, apply_M, b, x0=None, tol=1e-8, restart=50, max_iter=1000, ma
         for j in range(restart):
             Z[j] = apply_M(V[j])
             w = apply_K(Z[j])
+            wn0 = float(np.linalg.norm(w))
             h = V[:j + 1] @ w
             w = w - V[:j + 1].T @ h
-            h2 = V[:j + 1] @ w
-            w = w - V[:j + 1].T @ h2
-            h = h + h2
             hn = float(np.linalg.norm(w))
+            if orth == "cgs2" or hn < REORTH_KAPPA * wn0:
+                h2 = V[:j + 1] @ w
+                w = w - V[:j + 1].T @ h2
+                h = h + h2
+                hn = float(np.linalg.norm(w))
             H[:j + 1, j] = h
             H[j + 1, j] = hn
             for i in range(j):
@@ -110,12 +123,13 @@ class StokesOracle:
     """FP64 reference solver for one problem: assembled system + velocity hierarchy."""
 
     def __init__(self, mesh: Mesh, eta, alpha, levels, degree=4, seed=0, restart=50, schur="auto",
-                 coarse="cholesky"):
+                 coarse="cholesky", orth="cgs2"):
         self.mesh = mesh
         self.alpha = float(alpha)
         self.sys = System(mesh, eta, alpha)
         self.levels = levels
         self.restart = restart
+        self.orth = orth
         self.mg = Hierarchy(mesh, eta, alpha, levels, degree=degree, seed=seed, coarse=coarse)
         # Schur approximation: "mass" = M_p(1/eta) only; "cc" = Cahouet-Chabard
         # M_p(1/eta)^{-1} + alpha K_p^{-1}; "auto" = cc when alpha > 0
@@ -151,7 +165,8 @@ class StokesOracle:
         return self.project(z)
 
     def solve(self, b, tol=1e-8, x0=None, max_iter=1000):
-        x, it, rel, hist = fgmres(self.apply_K, self.precond, b, x0, tol, self.restart, max_iter)
+        x, it, rel, hist = fgmres(self.apply_K, self.precond, b, x0, tol, self.restart, max_iter,
+                                  orth=self.orth)
         return self.project(x), it, rel, hist
 
 

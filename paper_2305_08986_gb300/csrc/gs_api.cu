@@ -109,12 +109,20 @@ struct gs_ctx {
   // Krylov (FP64)
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
   double* part = nullptr;
-  int G = 1;
+  int G = 1;   // blocks of the multi-dot partial sums
+  int GA = 1;  // blocks of the fused axpy + norm (G * (m + 2) >= GA partial sums)
   double* dsc = nullptr;
   double* hpin = nullptr;
   int last_it = 0;
   double last_rel = 0.0;
   size_t footprint = 0;
+  // CUDA graph of the preconditioner body (captured on cap_st at the second application)
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t pgraph = nullptr;
+  const void* g_zu = nullptr;
+  const void* g_zp = nullptr;
+  long long pcalls = 0;
+  int pgraph_kernels = 0;
   // optional per-kernel-class timing (CUDA event pairs on the context stream)
   bool prof = false;
   std::vector<cudaEvent_t> evs;
@@ -152,6 +160,8 @@ void prof_end(gs_ctx* c, long i) {
 
 int opt_or(int v, int d) { return v > 0 ? v : d; }
 
+const double kReorthKappa = 0.70710678118654752440;  // 1/sqrt(2)
+
 gs_options normalize_opts(const gs_options* o) {
   gs_options r{};
   if (o) r = *o;
@@ -164,6 +174,8 @@ gs_options normalize_opts(const gs_options* o) {
   r.lanczos_steps = opt_or(r.lanczos_steps, 12);
   r.coarse_mode = r.coarse_mode == 1 ? 1 : 0;
   r.schur_kind = (r.schur_kind == 1 || r.schur_kind == 2) ? r.schur_kind : 0;
+  r.orth = r.orth == 1 ? 1 : 0;
+  r.graphs = r.graphs == 1 ? 1 : 0;
   return r;
 }
 
@@ -432,6 +444,11 @@ void layout(gs_ctx* c, Arena& ar) {
   if (G > 304) G = 304;
   if (G < 1) G = 1;
   c->G = (int)G;
+  long long GA = (c->N + 1023) / 1024;
+  if (GA > 152 * 16) GA = 152 * 16;
+  if (GA > (long long)c->G * (m + 2)) GA = (long long)c->G * (m + 2);
+  if (GA < 1) GA = 1;
+  c->GA = (int)GA;
   c->part = ar.take<double>((long long)c->G * (m + 2));
   c->dsc = ar.take<double>(4 * (m + 4));
   c->footprint = ar.off + 256;
@@ -948,10 +965,12 @@ gs_status project_pressure(gs_ctx* c, double* x) {
 
 // block upper-triangular preconditioner: z_p = -S^{-1} v_p, z_u = V(v_u - B^T z_p); constrained
 // entries of z copied from v (K is the identity there); pressure mean removed
+// Body of the preconditioner between the staging buffers: r_p in c->p_b, r_u in F.d (both in the
+// MG precision) -> z_p in c->p_xB, z_u in F.xA.  Fixed work, no host synchronisation: captured
+// once into a CUDA graph and replayed.
 template <typename T>
-gs_status precond_T(gs_ctx* c, const double* v, double* z) {
+gs_status precond_body(gs_ctx* c) {
   Level& F = c->lv[c->L - 1];
-  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)c->p_b, F.Np, (T)1, c->st));
   CKS(schur_inv<T>(c, (const T*)c->p_b));
   if (c->cc) {
     // z_p = -(M_p(1/eta)^{-1} r_p + alpha K_p^{-1} r_p)  (Cahouet-Chabard)
@@ -961,15 +980,68 @@ gs_status precond_T(gs_ctx* c, const double* v, double* z) {
   } else {
     KL(K_VEC, launch_cast<T, T>((const T*)c->p_xA, (T*)c->p_xB, F.Np, (T)(-1), c->st));  // z_p in p_xB
   }
-  KL(K_VEC, launch_cast<double, T>(v, (T*)F.d, F.nu, (T)1, c->st));
   {
     TileArgs<T> a = tile_args<T>(F);
     a.xp = (const T*)c->p_xB; a.bu = (const T*)F.d; a.yu = (T*)F.b;
     KL(K_BT, launch_tile<T>(c->dim, TILE_RESID, OPS_BT, a, c->st));
   }
   CKS(vcycle<T>(c, c->L - 1));
-  KL(K_VEC, launch_cast<T, double>((const T*)F.xA, z, F.nu, 1.0, c->st));
-  KL(K_VEC, launch_cast<T, double>((const T*)c->p_xB, z + c->nu, F.Np, 1.0, c->st));
+  return GS_OK;
+}
+
+// capture the preconditioner body into a CUDA graph (on the private capture stream)
+template <typename T>
+gs_status capture_precond(gs_ctx* c) {
+  cudaStream_t user = c->st;
+  CK(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
+  c->st = c->cap_st;
+  gs_status s = precond_body<T>(c);
+  c->st = user;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_st, &graph);
+  if (s != GS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(GS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->pgraph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->pgraph = nullptr;
+    return fail(GS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  // the graph leaves its results where the captured launches put them
+  c->g_zu = c->lv[c->L - 1].xA;
+  c->g_zp = c->p_xB;
+  return GS_OK;
+}
+
+// block upper-triangular preconditioner: z_p = -S^{-1} v_p, z_u = V(v_u - B^T z_p); constrained
+// entries of z copied from v (K is the identity there); pressure mean removed
+template <typename T>
+gs_status precond_T(gs_ctx* c, const double* v, double* z) {
+  Level& F = c->lv[c->L - 1];
+  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)c->p_b, F.Np, (T)1, c->st));
+  KL(K_VEC, launch_cast<double, T>(v, (T*)F.d, F.nu, (T)1, c->st));
+  const void* zu;
+  const void* zp;
+  const bool use_graph = c->opt.graphs == 0 && !c->prof && c->cap_st != nullptr;
+  if (use_graph && !c->pgraph && c->pcalls > 0) CKS(capture_precond<T>(c));
+  if (use_graph && c->pgraph) {
+    CK(cudaGraphLaunch(c->pgraph, c->st));
+    launched(cudaSuccess, c->pgraph_kernels);
+    zu = c->g_zu;
+    zp = c->g_zp;
+  } else {
+    const long long before = launches_total();
+    CKS(precond_body<T>(c));
+    c->pgraph_kernels = (int)(launches_total() - before);
+    zu = F.xA;
+    zp = c->p_xB;
+  }
+  c->pcalls++;
+  KL(K_VEC, launch_cast<T, double>((const T*)zu, z, F.nu, 1.0, c->st));
+  KL(K_VEC, launch_cast<T, double>((const T*)zp, z + c->nu, F.Np, 1.0, c->st));
   KL(K_VEC, launch_copy_constrained(v, z, F.g, c->st));
   CKS(project_pressure(c, z));
   return GS_OK;
@@ -1037,21 +1109,30 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       double* Zj = c->Z + (long long)j * N;
       CKS(precond(c, Vj, Zj));
       CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
-      // classical Gram-Schmidt, applied twice
-      KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h1, c->st));
-      KL(K_AXPY, launch_multi_axpy(c->V, N, j + 1, h1, -1.0, c->w, N, c->st));
-      KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
-      KL(K_AXPY, launch_multi_axpy(c->V, N, j + 1, h2, -1.0, c->w, N, c->st));
-      KL(K_DOTS, launch_add_vec(h1, h2, j + 1, c->st));
-      KL(K_DOTS, launch_dots_partial<double>(c->w, N, 1, c->w, N, c->part, c->G, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->G, nrm, c->st));
-      CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+      // classical Gram-Schmidt: h = V^T w (with |w|^2 in the same pass), w -= V h (with the new
+      // |w|^2 in the same pass); a second pass when |w| fell below 1/sqrt(2) of its value
+      // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, orth = 0)
+      KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, j + 2, c->G, h1, c->st));
+      KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+      CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->st));
       CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
       for (int i = 0; i <= j; ++i) Hc(i, j) = c->hpin[i];
-      const double hn = std::sqrt(c->hpin[m + 1]);
+      const double wn0 = std::sqrt(c->hpin[j + 1]);
+      double hn = std::sqrt(c->hpin[m + 1]);
+      if (c->opt.orth == 0 || hn < kReorthKappa * wn0) {
+        KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+        KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
+        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+        KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+        CK(cudaMemcpyAsync(c->hpin, h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int i = 0; i <= j; ++i) Hc(i, j) += c->hpin[i];
+        hn = std::sqrt(c->hpin[m + 1]);
+      }
       if (!std::isfinite(hn)) return fail(GS_EBREAKDOWN, "Arnoldi vector is not finite");
       Hc(j + 1, j) = hn;
       for (int i = 0; i < j; ++i) {
@@ -1245,8 +1326,15 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
   set_geom(c, mesh);
   cudaError_t e = cudaMallocHost(&c->hpin, sizeof(double) * (c->opt.restart + 8));
   if (e != cudaSuccess) { delete c; return fail(GS_ECUDA, std::string("pinned buffer: ") + cudaGetErrorString(e)); }
+  if (c->opt.graphs == 0 && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess)
+    c->cap_st = nullptr;  // graphs stay off
   s = setup(c);
-  if (s != GS_OK) { cudaFreeHost(c->hpin); delete c; return s; }
+  if (s != GS_OK) {
+    if (c->cap_st) cudaStreamDestroy(c->cap_st);
+    cudaFreeHost(c->hpin);
+    delete c;
+    return s;
+  }
   *out = c;
   return GS_OK;
 }
@@ -1448,6 +1536,8 @@ gs_status gs_set_stream(gs_ctx* c, void* stream) {
 
 void gs_destroy(gs_ctx* c) {
   if (!c) return;
+  if (c->pgraph) cudaGraphExecDestroy(c->pgraph);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   for (auto e : c->evs) cudaEventDestroy(e);
   if (c->hpin) cudaFreeHost(c->hpin);
   delete c;

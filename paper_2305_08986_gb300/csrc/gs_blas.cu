@@ -115,32 +115,39 @@ cudaError_t launch_lanczos_post(const T* dinv, const T* y, const T* vprev, T bet
 // element-to-thread assignment and the reduction tree are fixed by the launch shape.
 template <typename T, int KB>
 __global__ void k_dots_partial(const T* __restrict__ V, long long ldv, int k, const T* __restrict__ w,
-                               long long n, double* __restrict__ part) {
-  __shared__ double sh[KB][32];
+                               long long n, double* __restrict__ part, int self_dot) {
+  __shared__ double sh[KB + 1][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i0 = 0; i0 < k; i0 += KB) {
-    const int kb = min(KB, k - i0);
-    double acc[KB];
+  for (int i0 = 0; i0 < k || (i0 == 0 && self_dot); i0 += KB) {
+    const int kb = max(0, min(KB, k - i0));
+    const bool self = self_dot && i0 == 0;  // w . w rides along with the first block of vectors
+    double acc[KB], accw = 0.0;
 #pragma unroll
     for (int i = 0; i < KB; ++i) acc[i] = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
       const double we = (double)w[e];
+      if (self) accw += we * we;
 #pragma unroll
       for (int i = 0; i < KB; ++i)
         if (i < kb) acc[i] += (double)V[(i0 + i) * ldv + e] * we;
     }
 #pragma unroll
-    for (int i = 0; i < KB; ++i) {
-      double v = acc[i];
+    for (int i = 0; i <= KB; ++i) {
+      double v = i < KB ? acc[i] : accw;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) sh[i][wid] = v;
     }
     __syncthreads();
     if (threadIdx.x < kb) {
-      double s = 0.0;
-      for (int q = 0; q < nw; ++q) s += sh[threadIdx.x][q];
-      part[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += sh[threadIdx.x][q];
+      part[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+    if (self && threadIdx.x == 32) {  // the row after the k dot products
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += sh[KB][q];
+      part[(long long)k * gridDim.x + blockIdx.x] = t;
     }
     __syncthreads();
   }
@@ -149,9 +156,45 @@ template <typename T>
 cudaError_t launch_dots_partial(const T* V, long long ldv, int k, const T* w, long long n, double* part, int G,
                                 cudaStream_t st) {
   if (k <= 1)
-    k_dots_partial<T, 1><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part);
+    k_dots_partial<T, 1><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, 0);
   else
-    k_dots_partial<T, 8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part);
+    k_dots_partial<T, 8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, 0);
+  return launched(cudaGetLastError());
+}
+cudaError_t launch_dots_norm_partial(const double* V, long long ldv, int k, const double* w, long long n, double* part,
+                                     int G, cudaStream_t st) {
+  k_dots_partial<double, 8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, 1);
+  return launched(cudaGetLastError());
+}
+
+// w <- w + sign * sum_i coef[i] V[i], and per-block partial sums of the new |w|^2
+__global__ void k_multi_axpy_norm(const double* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
+                                  double sign, double* __restrict__ w, long long n, double* __restrict__ part) {
+  extern __shared__ double cs[];
+  __shared__ double sh[32];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = sign * coef[i];
+  __syncthreads();
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double acc = w[e];
+    for (int i = 0; i < k; ++i) acc += cs[i] * V[i * ldv + e];
+    w[e] = acc;
+    s += acc * acc;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    part[blockIdx.x] = t;
+  }
+}
+cudaError_t launch_multi_axpy_norm(const double* V, long long ldv, int k, const double* coef, double sign, double* w,
+                                   long long n, double* part, int G, cudaStream_t st) {
+  k_multi_axpy_norm<<<G, TPB, sizeof(double) * (k > 0 ? k : 1), st>>>(V, ldv, k, coef, sign, w, n, part);
   return launched(cudaGetLastError());
 }
 

@@ -129,6 +129,12 @@ template <typename T>
 cudaError_t launch_dots_partial(const T* V, long long ldv, int k, const T* w, long long n,
                                 double* part, int G, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* part, int k, int G, double* out, cudaStream_t st);
+// k dot products V[i] . w plus w . w in row k of part (rows 0..k)
+cudaError_t launch_dots_norm_partial(const double* V, long long ldv, int k, const double* w, long long n,
+                                     double* part, int G, cudaStream_t st);
+// w <- w + sign * sum_i coef[i] V[i]; part[block] = partial sums of the new |w|^2 (G blocks)
+cudaError_t launch_multi_axpy_norm(const double* V, long long ldv, int k, const double* coef, double sign,
+                                   double* w, long long n, double* part, int G, cudaStream_t st);
 // w <- w + sign * sum_i coef[i] V[i]   (coef on device)
 cudaError_t launch_multi_axpy(const double* V, long long ldv, int k, const double* coef, double sign,
                               double* w, long long n, cudaStream_t st);

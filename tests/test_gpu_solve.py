@@ -110,6 +110,23 @@ def test_solve_parity_mass_schur(name):
     assert abs(it - ito) <= max(2, 0.05 * ito), (it, ito)
 
 
+def test_solve_parity_selective_reorth():
+    """Gram-Schmidt with the second pass only when needed (orth = 1) against the oracle."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS["box3d"]()
+    m = mesh_from_problem(p)
+    o = StokesOracle(m, p.eta, p.alpha, p.levels, orth="selective")
+    b_ref = o.sys.lift_rhs(p.f, p.g)
+    s = gs.Solver.from_problem(p, mg_precision=64, orth=1)
+    b = torch.tensor(b_ref, device="cuda")
+    x = torch.zeros_like(b)
+    it, rr, _ = s.solve(b, x, tol=1e-11)
+    xo, ito, relo, _ = o.solve(b_ref, tol=1e-11)
+    assert rr <= 1e-11 and abs(it - ito) <= max(2, 0.05 * ito)
+    assert rel(normalize_pressure(m, o.sys, x.cpu().numpy()), normalize_pressure(m, o.sys, xo)) <= 1e-8
+
+
 def test_cahouet_chabard_iterations():
     """alpha = 1e3 channel: FP32 multigrid with the Cahouet-Chabard term stays in the tens of
     iterations (the mass-only Schur approximation needs several hundred)."""
@@ -180,3 +197,25 @@ def test_create_rejects_bad_input():
     st = gs._lib.gs_create(ctypes.byref(mesh), p.levels, eta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                            1.0, ctypes.byref(o), None, ctypes.c_void_p(ws.data_ptr()), need // 2, ctypes.byref(ctx))
     assert st == gs.GS_ENOMEM and not ctx.value
+
+
+@pytest.mark.parametrize("name", ["channel_small", "box3d"])
+def test_graph_replay_matches_plain_launches(name):
+    """The preconditioner replayed from its captured CUDA graph gives bitwise the same solve as
+    plain launches (every kernel is deterministic; the graph holds the same launches)."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS[name]()
+    out = []
+    for graphs in (0, 1):
+        s = gs.Solver.from_problem(p, graphs=graphs)
+        b = torch.empty(s.n_total, dtype=torch.float64, device="cuda")
+        s.lift_rhs(torch.tensor(p.f, device="cuda"), torch.tensor(p.g, device="cuda"), b)
+        x = torch.zeros_like(b)
+        it, rr, _ = s.solve(b, x, tol=1e-10)
+        x2 = torch.zeros_like(b)
+        it2, rr2, _ = s.solve(b, x2, tol=1e-10)      # second solve: graph already captured
+        assert it == it2 and torch.equal(x, x2)
+        out.append((it, x.cpu()))
+        s.close()
+    assert out[0][0] == out[1][0] and torch.equal(out[0][1], out[1][1])
