@@ -106,6 +106,11 @@ typedef struct {            /* zero-initialised = defaults */
                                   1/sqrt(2) of its value before the projection */
   int graphs;               /* 0: replay the preconditioner's fixed launch sequence as a CUDA graph
                                   captured at its second application (default); 1: plain launches */
+  int plap_degree;          /* Chebyshev degree of the pressure-Laplacian V-cycle of the
+                               Cahouet-Chabard term; 0 -> 2 */
+  int krylov_fp64;          /* 0: FGMRES basis V stored as double-float pairs (hi + lo, 48-bit),
+                                  Gram-Schmidt products on the FP32 pipes (default);
+                               1: basis and Gram-Schmidt in IEEE FP64 */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */

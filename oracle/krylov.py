@@ -14,7 +14,8 @@ Sec. 4; it stops on the Euclidean norm of the residual.  Readings taken here:
   option "selective": the second pass only when the new vector's norm drops below 1/sqrt(2)
   of its value before the projection (Daniel-Gragg-Kaufman-Stewart criterion);
 * Schur approximation S^{-1} ~ M_p(1/eta)^{-1} (+ alpha K_p^{-1}, Cahouet-Chabard, when alpha > 0;
-  see pressure.py);
+  see pressure.py; K_p^{-1} by one V-cycle with Chebyshev degree 2, which keeps the FGMRES
+  iteration count of degree 4 on the channel workload);
 * preconditioner (block upper triangular):  z_p = -S^{-1} r_p,
   z_u = V-cycle(r_u - B^T z_p); on constrained entries (identity rows of K) z = r;
 * pure-Dirichlet problems have the constant pressure in the kernel; the mean of
@@ -123,7 +124,7 @@ class StokesOracle:
     """FP64 reference solver for one problem: assembled system + velocity hierarchy."""
 
     def __init__(self, mesh: Mesh, eta, alpha, levels, degree=4, seed=0, restart=50, schur="auto",
-                 coarse="cholesky", orth="cgs2"):
+                 coarse="cholesky", orth="cgs2", pdegree=2):
         self.mesh = mesh
         self.alpha = float(alpha)
         self.sys = System(mesh, eta, alpha)
@@ -134,7 +135,7 @@ class StokesOracle:
         # Schur approximation: "mass" = M_p(1/eta) only; "cc" = Cahouet-Chabard
         # M_p(1/eta)^{-1} + alpha K_p^{-1}; "auto" = cc when alpha > 0
         self.schur = ("cc" if self.alpha > 0 else "mass") if schur == "auto" else schur
-        self.pmg = (PressureHierarchy(mesh, levels, degree=degree, seed=seed, coarse=coarse)
+        self.pmg = (PressureHierarchy(mesh, levels, degree=pdegree, seed=seed, coarse=coarse)
                     if self.schur == "cc" else None)
         # the finest level of the hierarchy re-assembles A; both are identical by construction
         self.nullspace = mesh.has_pressure_nullspace()

@@ -108,6 +108,7 @@ struct gs_ctx {
   double *ctmp = nullptr, *gjrow = nullptr, *gjcol = nullptr;
   // Krylov (FP64)
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double* vcur = nullptr;  // current basis vector as double (input of the preconditioner)
   double* part = nullptr;
   int G = 1;   // blocks of the multi-dot partial sums
   int GA = 1;  // blocks of the fused axpy + norm (G * (m + 2) >= GA partial sums)
@@ -176,6 +177,8 @@ gs_options normalize_opts(const gs_options* o) {
   r.schur_kind = (r.schur_kind == 1 || r.schur_kind == 2) ? r.schur_kind : 0;
   r.orth = r.orth == 1 ? 1 : 0;
   r.graphs = r.graphs == 1 ? 1 : 0;
+  r.plap_degree = opt_or(r.plap_degree, 2);
+  r.krylov_fp64 = r.krylov_fp64 == 1 ? 1 : 0;
   return r;
 }
 
@@ -440,8 +443,9 @@ void layout(gs_ctx* c, Arena& ar) {
   c->r = ar.take<double>(c->N);
   c->t1 = ar.take<double>(c->N);
   c->t2 = ar.take<double>(c->N);
+  c->vcur = ar.take<double>(c->N);
   long long G = (c->N + 4095) / 4096;
-  if (G > 304) G = 304;
+  if (G > 152 * 3) G = 152 * 3;  // three resident CTAs per SM for the multi-dot
   if (G < 1) G = 1;
   c->G = (int)G;
   long long GA = (c->N + 1023) / 1024;
@@ -895,7 +899,7 @@ gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init) {
   Level& lv = c->lv[l];
   const double hi = lv.plam_hi, lo = hi / 15.0;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
-  const int k = c->opt.cheb_degree;
+  const int k = c->opt.plap_degree;
   T* dinv = (T*)lv.pdinv;
   T* d = (T*)lv.pd;
   if (zero_init) {
@@ -1099,22 +1103,33 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
     if (rel <= tol) break;
     if (it >= c->opt.max_iter) { result = GS_ENOCONV; break; }
     CK(cudaMemcpyAsync(nrm, &beta2, sizeof(double), cudaMemcpyHostToDevice, c->st));
-    KL(K_AXPY, launch_scale_by_rnorm(c->r, nrm, c->V, N, c->st));
+    const bool dfk = c->opt.krylov_fp64 == 0;  // basis in double-float form
+    float2* Vdf = reinterpret_cast<float2*>(c->V);
+    if (dfk)
+      KL(K_AXPY, launch_scale_by_rnorm_df(c->r, nrm, Vdf, c->vcur, N, c->st));
+    else
+      KL(K_AXPY, launch_scale_by_rnorm(c->r, nrm, c->V, N, c->st));
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int k = 0;
     bool converged = false;
     for (int j = 0; j < m; ++j) {
-      double* Vj = c->V + (long long)j * N;
+      const double* Vj = dfk ? c->vcur : c->V + (long long)j * N;
       double* Zj = c->Z + (long long)j * N;
       CKS(precond(c, Vj, Zj));
       CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
       // classical Gram-Schmidt: h = V^T w (with |w|^2 in the same pass), w -= V h (with the new
       // |w|^2 in the same pass); a second pass when |w| fell below 1/sqrt(2) of its value
       // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, orth = 0)
-      KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+      if (dfk)
+        KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 1, c->st));
+      else
+        KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
       KL(K_DOTS, launch_reduce_partials(c->part, j + 2, c->G, h1, c->st));
-      KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
+      if (dfk)
+        KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
+      else
+        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
       KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
       CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->st));
       CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -1123,9 +1138,15 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       const double wn0 = std::sqrt(c->hpin[j + 1]);
       double hn = std::sqrt(c->hpin[m + 1]);
       if (c->opt.orth == 0 || hn < kReorthKappa * wn0) {
-        KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+        if (dfk)
+          KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
+        else
+          KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
         KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
-        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+        if (dfk)
+          KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+        else
+          KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
         KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
         CK(cudaMemcpyAsync(c->hpin, h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -1151,7 +1172,10 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       k = j + 1;
       if (std::fabs(g[j + 1]) / bnorm <= tol || hn == 0.0) { converged = true; break; }
       if (it >= c->opt.max_iter) break;
-      KL(K_AXPY, launch_scale_by_rnorm(c->w, nrm, c->V + (long long)(j + 1) * N, N, c->st));
+      if (dfk)
+        KL(K_AXPY, launch_scale_by_rnorm_df(c->w, nrm, Vdf + (long long)(j + 1) * N, c->vcur, N, c->st));
+      else
+        KL(K_AXPY, launch_scale_by_rnorm(c->w, nrm, c->V + (long long)(j + 1) * N, N, c->st));
     }
     for (int i = k - 1; i >= 0; --i) {
       double s = g[i];

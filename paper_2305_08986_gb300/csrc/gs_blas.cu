@@ -198,6 +198,158 @@ cudaError_t launch_multi_axpy_norm(const double* V, long long ldv, int k, const 
   return launched(cudaGetLastError());
 }
 
+// ---- Krylov basis in double-float form (GB300: FP64 is 1/74 of the FP32 rate) ----------------------
+// A basis vector is stored as float2 (hi, lo) with value hi + lo (48 significant bits, same 8 bytes
+// as a double).  Products hi/lo x hi/lo are formed exactly with an FMA for hi*hi plus the two
+// cross terms, and sums are carried as unevaluated float pairs (TwoSum + renormalisation), so the
+// Gram-Schmidt dot products and updates run on the FP32 pipes at ~48-bit accuracy.
+__device__ __forceinline__ float2 df_split(double a) {
+  const float h = (float)a;
+  return make_float2(h, (float)(a - (double)h));
+}
+__device__ __forceinline__ double df_join(float2 v) { return (double)v.x + (double)v.y; }
+// acc += a * b
+__device__ __forceinline__ void df_fma(float2& acc, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float s = acc.x + p;
+  const float bb = s - acc.x;
+  const float err = (acc.x - (s - bb)) + (p - bb);
+  const float lo = acc.y + err + e;
+  const float hi = s + lo;
+  acc.y = lo - (hi - s);
+  acc.x = hi;
+}
+
+template <int KB>
+__global__ void __launch_bounds__(256, 3)
+    k_dots_partial_df(const float2* __restrict__ V, long long ldv, int k, const double* __restrict__ w,
+                      long long n, double* __restrict__ part, int self_dot) {
+  __shared__ double sh[KB + 1][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int i0 = 0; i0 < k; i0 += KB) {
+    const int kb = min(KB, k - i0);
+    const bool self = self_dot && i0 == 0;
+    float2 acc[KB];
+    double accw = 0.0;
+#pragma unroll
+    for (int i = 0; i < KB; ++i) acc[i] = make_float2(0.f, 0.f);
+    const float2* Vb = V + i0 * ldv;
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // two elements per iteration, every load issued before the double-float arithmetic
+    for (; e + stride < n; e += 2 * stride) {
+      const double wd0 = w[e], wd1 = w[e + stride];
+      float2 v0[KB], v1[KB];
+#pragma unroll
+      for (int i = 0; i < KB; ++i) {
+        v0[i] = i < kb ? Vb[i * ldv + e] : make_float2(0.f, 0.f);
+        v1[i] = i < kb ? Vb[i * ldv + e + stride] : make_float2(0.f, 0.f);
+      }
+      if (self) accw += wd0 * wd0 + wd1 * wd1;
+      const float2 we0 = df_split(wd0), we1 = df_split(wd1);
+#pragma unroll
+      for (int i = 0; i < KB; ++i) {
+        df_fma(acc[i], v0[i], we0);
+        df_fma(acc[i], v1[i], we1);
+      }
+    }
+    if (e < n) {
+      const double wd = w[e];
+      if (self) accw += wd * wd;
+      const float2 we = df_split(wd);
+#pragma unroll
+      for (int i = 0; i < KB; ++i)
+        if (i < kb) df_fma(acc[i], Vb[i * ldv + e], we);
+    }
+#pragma unroll
+    for (int i = 0; i <= KB; ++i) {
+      double v = i < KB ? df_join(acc[i]) : accw;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[i][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kb) {
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += sh[threadIdx.x][q];
+      part[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
+    if (self && threadIdx.x == 32) {
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += sh[KB][q];
+      part[(long long)k * gridDim.x + blockIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+cudaError_t launch_dots_partial_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
+                                   int G, int self_dot, cudaStream_t st) {
+  k_dots_partial_df<8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, self_dot);
+  return launched(cudaGetLastError());
+}
+
+// w <- w + sign * sum_i coef[i] V[i] (sum carried in double-float), partial sums of the new |w|^2
+__global__ void k_multi_axpy_norm_df(const float2* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
+                                     double sign, double* __restrict__ w, long long n, double* __restrict__ part) {
+  extern __shared__ float2 cs2[];
+  __shared__ double sh[32];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cs2[i] = df_split(sign * coef[i]);
+  __syncthreads();
+  double s = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double we = w[e];
+    float2 acc = make_float2(0.f, 0.f);
+    int i = 0;
+    for (; i + 8 <= k; i += 8) {  // eight basis loads in flight per thread
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V[(i + u) * ldv + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) df_fma(acc, cs2[i + u], v[u]);
+    }
+    for (; i < k; ++i) df_fma(acc, cs2[i], V[i * ldv + e]);
+    const double r = we + df_join(acc);
+    w[e] = r;
+    s += r * r;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+    part[blockIdx.x] = t;
+  }
+}
+cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
+                                      long long n, double* part, int G, cudaStream_t st) {
+  k_multi_axpy_norm_df<<<G, TPB, sizeof(float2) * (k > 0 ? k : 1), st>>>(V, ldv, k, coef, sign, w, n, part);
+  return launched(cudaGetLastError());
+}
+
+// v_df <- w / sqrt(nrm2) in double-float form, and the same vector as double in vd
+__global__ void k_scale_by_rnorm_df(const double* __restrict__ w, const double* __restrict__ nrm2,
+                                    float2* __restrict__ v, double* __restrict__ vd, long long n) {
+  const double sc = 1.0 / sqrt(nrm2[0]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = w[i] * sc;
+    v[i] = df_split(x);
+    vd[i] = x;
+  }
+}
+cudaError_t launch_scale_by_rnorm_df(const double* w, const double* nrm2, float2* v, double* vd, long long n,
+                                     cudaStream_t st) {
+  unsigned g = nblk(n);
+  if (g > 152u * 16u) g = 152u * 16u;
+  k_scale_by_rnorm_df<<<g, TPB, 0, st>>>(w, nrm2, v, vd, n);
+  return launched(cudaGetLastError());
+}
+
 __global__ void k_reduce_partials(const double* __restrict__ part, int G, double* __restrict__ out) {
   __shared__ double sh[32];
   const int i = blockIdx.x;

@@ -102,6 +102,27 @@ cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf,
 template <typename T>
 cudaError_t launch_p_prolong_add(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* xc,
                                  T* xf, cudaStream_t st);
+// Tiled Q1 operators (gs_q1tile.cu): OP = Q1_PLAP (K_p, cell scalar 1) or Q1_PMASS (M_p(1/eta),
+// cell scalar pm / eta); cmask (may be NULL) marks identity rows / zero columns.
+enum Q1Op { Q1_PLAP = 0, Q1_PMASS = 1 };
+template <typename T>
+struct Q1Args {
+  Geom g;
+  T kc[3];
+  T pm;
+  const T* eta;
+  const uint8_t* cmask;
+  const T* x;
+  T* y;
+  const T* b;
+  T* d;
+  const T* dinv;
+  T* xout;
+  T c1, c2;
+  int use_d;
+};
+template <typename T>
+cudaError_t launch_q1tile(int op, int mode, const Q1Args<T>& a, cudaStream_t st);
 // out[i] = mask[i] ? 0 : in[i]   (may run in place)
 template <typename T>
 cudaError_t launch_mask_copy(const T* in, const uint8_t* mask, T* out, long long n, cudaStream_t st);
@@ -135,6 +156,13 @@ cudaError_t launch_dots_norm_partial(const double* V, long long ldv, int k, cons
 // w <- w + sign * sum_i coef[i] V[i]; part[block] = partial sums of the new |w|^2 (G blocks)
 cudaError_t launch_multi_axpy_norm(const double* V, long long ldv, int k, const double* coef, double sign,
                                    double* w, long long n, double* part, int G, cudaStream_t st);
+// Krylov basis stored in double-float form (float2 hi + lo): the same operations on FP32 pipes
+cudaError_t launch_dots_partial_df(const float2* V, long long ldv, int k, const double* w, long long n,
+                                   double* part, int G, int self_dot, cudaStream_t st);
+cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, const double* coef, double sign,
+                                      double* w, long long n, double* part, int G, cudaStream_t st);
+cudaError_t launch_scale_by_rnorm_df(const double* w, const double* nrm2, float2* v, double* vd, long long n,
+                                     cudaStream_t st);
 // w <- w + sign * sum_i coef[i] V[i]   (coef on device)
 cudaError_t launch_multi_axpy(const double* V, long long ldv, int k, const double* coef, double sign,
                               double* w, long long n, cudaStream_t st);

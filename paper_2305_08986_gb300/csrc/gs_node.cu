@@ -271,6 +271,16 @@ __global__ void k_pdiag(const Geom g, const OpCoef<T> c, const T* __restrict__ e
 
 template <typename T>
 cudaError_t launch_pmass(int mode, PMassArgs<T> a, cudaStream_t st) {
+  if (!a.raw && !a.unit) {
+    Q1Args<T> q{};
+    q.g = a.g;
+    q.pm = a.c.pm;
+    q.eta = a.eta;
+    q.cmask = a.g.pmask;
+    q.x = a.x; q.y = a.y; q.b = a.b; q.d = a.d; q.dinv = a.dinv; q.xout = a.xout;
+    q.c1 = a.c1; q.c2 = a.c2; q.use_d = a.use_d;
+    return launch_q1tile<T>(Q1_PMASS, mode, q, st);
+  }
   const unsigned nb = nblk(a.g.Np);
   if (a.g.dim == 2) {
     if (mode == TILE_APPLY) k_pmass<T, 2, TILE_APPLY><<<nb, TPB, 0, st>>>(a);
@@ -305,63 +315,6 @@ INST(double)
 
 // ---- pressure Laplacian K_p (Cahouet-Chabard term of the Schur approximation) ----------------------
 namespace gs {
-
-template <typename T, int DIM, int MODE>
-__global__ void k_plap(const PLapArgs<T> A) {
-  const Geom& g = A.g;
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= g.Np) return;
-  int I, J, K;
-  unflat(q, g.npn, DIM, I, J, K);
-  const bool con = A.cmask[q] != 0;
-  T kx = T(0);
-  if (!con) {
-    const int idx[3] = {I, J, K};
-    int cl[3][2], cnt[3];
-    for (int ax = 0; ax < DIM; ++ax) {
-      cnt[ax] = 0;
-      if (idx[ax] - 1 >= 0) cl[ax][cnt[ax]++] = idx[ax] - 1;
-      if (idx[ax] < g.n[ax]) cl[ax][cnt[ax]++] = idx[ax];
-    }
-    const int c2n = DIM == 3 ? cnt[2] : 1;
-    for (int k = 0; k < c2n; ++k)
-      for (int j = 0; j < cnt[1]; ++j)
-        for (int i = 0; i < cnt[0]; ++i) {
-          const int c0 = cl[0][i], c1 = cl[1][j], c2 = DIM == 3 ? cl[2][k] : 0;
-          const long long cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
-          if (cell_void(g, cell)) continue;
-          const int la = I - c0, lb = J - c1, lc = DIM == 3 ? K - c2 : 0;
-          for (int rc = 0; rc < (DIM == 3 ? 2 : 1); ++rc)
-            for (int rb = 0; rb < 2; ++rb)
-              for (int ra = 0; ra < 2; ++ra) {
-                const long long r = (c0 + ra) + (long long)g.npn[0] * ((c1 + rb) + (long long)g.npn[1] * (c2 + rc));
-                if (A.cmask[r]) continue;
-                const T k1a = la == ra ? T(1) : T(-1), pa = la == ra ? T(2) : T(1);
-                const T k1b = lb == rb ? T(1) : T(-1), pb = lb == rb ? T(2) : T(1);
-                T w;
-                if (DIM == 2) {
-                  w = A.kc[0] * k1a * pb + A.kc[1] * pa * k1b;
-                } else {
-                  const T k1c = lc == rc ? T(1) : T(-1), pc = lc == rc ? T(2) : T(1);
-                  w = A.kc[0] * k1a * pb * pc + A.kc[1] * pa * k1b * pc + A.kc[2] * pa * pb * k1c;
-                }
-                kx += w * A.x[r];
-              }
-        }
-  }
-  const T kq = con ? A.x[q] : kx;
-  if (MODE == TILE_APPLY) {
-    A.y[q] = kq;
-  } else if (MODE == TILE_RESID) {
-    A.y[q] = A.b[q] - kq;
-  } else {
-    const T r = A.b[q] - kq;
-    T dn = A.c2 * A.dinv[q] * r;
-    if (A.use_d) dn += A.c1 * A.d[q];
-    A.d[q] = dn;
-    A.xout[q] = A.x[q] + dn;
-  }
-}
 
 template <typename T, int DIM>
 __global__ void k_plap_diag(const Geom g, const T k0, const T k1, const T k2, const uint8_t* __restrict__ cmask,
@@ -463,18 +416,15 @@ __global__ void k_cc_combine(const T* __restrict__ m, const T* __restrict__ v, c
 
 template <typename T>
 cudaError_t launch_plap(int mode, PLapArgs<T> a, cudaStream_t st) {
-  const unsigned nb = nblk(a.g.Np);
-  if (a.g.dim == 2) {
-    if (mode == TILE_APPLY) k_plap<T, 2, TILE_APPLY><<<nb, TPB, 0, st>>>(a);
-    else if (mode == TILE_RESID) k_plap<T, 2, TILE_RESID><<<nb, TPB, 0, st>>>(a);
-    else k_plap<T, 2, TILE_CHEB><<<nb, TPB, 0, st>>>(a);
-  } else {
-    if (mode == TILE_APPLY) k_plap<T, 3, TILE_APPLY><<<nb, TPB, 0, st>>>(a);
-    else if (mode == TILE_RESID) k_plap<T, 3, TILE_RESID><<<nb, TPB, 0, st>>>(a);
-    else k_plap<T, 3, TILE_CHEB><<<nb, TPB, 0, st>>>(a);
-  }
-  return launched(cudaGetLastError());
+  Q1Args<T> q{};
+  q.g = a.g;
+  for (int i = 0; i < 3; ++i) q.kc[i] = a.kc[i];
+  q.cmask = a.cmask;
+  q.x = a.x; q.y = a.y; q.b = a.b; q.d = a.d; q.dinv = a.dinv; q.xout = a.xout;
+  q.c1 = a.c1; q.c2 = a.c2; q.use_d = a.use_d;
+  return launch_q1tile<T>(Q1_PLAP, mode, q, st);
 }
+
 template <typename T>
 cudaError_t launch_plap_diag(const Geom& g, const T* kc, const uint8_t* cmask, T* dinv, cudaStream_t st) {
   if (g.dim == 2)

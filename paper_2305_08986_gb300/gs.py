@@ -36,7 +36,8 @@ class GsOptions(ctypes.Structure):
     _fields_ = [("cheb_degree", ctypes.c_int), ("smooth_steps", ctypes.c_int), ("restart", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("mg_precision", ctypes.c_int), ("schur_degree", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("seed", ctypes.c_int), ("coarse_mode", ctypes.c_int),
-                ("schur_kind", ctypes.c_int), ("orth", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("schur_kind", ctypes.c_int), ("orth", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("plap_degree", ctypes.c_int), ("krylov_fp64", ctypes.c_int)]
 
 
 class GsInfo(ctypes.Structure):

@@ -197,7 +197,7 @@ def test_pressure_laplacian_transfers_vcycle(case):
     from oracle.pressure import PressureHierarchy
     p, s, torch = _setup(case, mg_precision=64)
     m = mesh_from_problem(p)
-    H = PressureHierarchy(m, p.levels)
+    H = PressureHierarchy(m, p.levels, degree=2)
     inf = s.info()
     assert inf.schur_cc == 1
     L = p.levels - 1

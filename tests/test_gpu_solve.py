@@ -219,3 +219,21 @@ def test_graph_replay_matches_plain_launches(name):
         out.append((it, x.cpu()))
         s.close()
     assert out[0][0] == out[1][0] and torch.equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("krylov_fp64", [0, 1])
+def test_krylov_basis_arithmetic(krylov_fp64):
+    """Double-float (default) and IEEE FP64 Krylov bases both reach the oracle's solution."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS["channel_small"]()
+    m = mesh_from_problem(p)
+    o = StokesOracle(m, p.eta, p.alpha, p.levels)
+    b_ref = o.sys.lift_rhs(p.f, p.g)
+    xo, ito, _, _ = o.solve(b_ref, tol=1e-11)
+    s = gs.Solver.from_problem(p, mg_precision=64, krylov_fp64=krylov_fp64)
+    b = torch.tensor(b_ref, device="cuda")
+    x = torch.zeros_like(b)
+    it, rr, _ = s.solve(b, x, tol=1e-11)
+    assert rr <= 1e-11 and abs(it - ito) <= max(2, 0.05 * ito)
+    assert rel(normalize_pressure(m, o.sys, x.cpu().numpy()), normalize_pressure(m, o.sys, xo)) <= 1e-8
