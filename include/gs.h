@@ -65,7 +65,8 @@ typedef enum {
   GS_ECUDA = 3,
   GS_ENOCONV = 4,
   GS_EBREAKDOWN = 5,
-  GS_ETIMEOUT = 6
+  GS_ETIMEOUT = 6,
+  GS_EBUSY = 7 /* batching engine: every slot is occupied */
 } gs_status;
 
 /* Dirichlet face bits */
@@ -153,7 +154,10 @@ gs_status gs_lift_rhs(gs_ctx* ctx, const double* f, const double* g, double* rhs
 
 /* Solve `count` independent systems; ctxs[i] with rhs[i] -> x[i] (device pointers).
  * iterations / rel_residuals: host arrays of `count` entries or NULL.  Returns the first
- * non-OK status (all systems are still attempted). */
+ * non-OK status (all systems are still attempted).  When every context uses the default
+ * orthogonalisation (orth = 0) and no profiling, the systems run together through a batching
+ * engine on ctxs[0]'s stream (one launch per kernel per FGMRES iteration for all of them, see
+ * gs_engine_*).  Otherwise they run one after the other through gs_solve. */
 gs_status gs_batch_solve(gs_ctx* const* ctxs, int count, const double* const* rhs,
                          double* const* x, double tol, int* iterations, double* rel_residuals);
 
@@ -236,6 +240,57 @@ int gs_profile_read(gs_ctx* ctx, gs_kernel_stat* out, int max);
  * only, on the context's stream. */
 #define GS_NOALLOC_COARSE_MAX 16384
 gs_status gs_coarse_solve_noalloc(gs_ctx* ctx, const double* b, double* y);
+
+/* ---- Batching engine (many solves in lockstep; continuous batching) --------------------------
+ * The paper solves one system at a time; this engine runs many independent solves together on
+ * one GPU.  Each solve is a context of its own (hierarchy and Krylov state resident on the
+ * device).  gs_engine_step advances every solve in the engine by one FGMRES iteration (right
+ * preconditioned, restart m, classical Gram-Schmidt twice, Sec. 5): the launches all solves
+ * need for that iteration are merged so that each kernel runs once for all of them (a work
+ * list of (solve, block) pairs), the block preconditioners of all solves replay as one captured
+ * CUDA graph, and the host synchronises once per step.  Each solve runs the launches gs_solve
+ * issues for it (same kernel bodies, arguments and order) through the batched entry points: its
+ * result is bitwise the same whoever else is in the engine, and agrees with gs_solve's to
+ * rounding (the single-instance entry points are compiled separately, and the compiler may
+ * contract multiply-adds differently there).  Solves join with gs_engine_add and leave when they
+ * finish, between steps.
+ *
+ * gs_engine_create: max_slots solves at most at a time; max_restart >= the restart length of
+ * every context added (0: 50); stream: cudaStream_t or NULL; all engine work is enqueued there.
+ * The engine allocates its own staging buffers (device and pinned host memory, a few hundred
+ * bytes per slot plus the argument tables of one step).
+ * gs_engine_add: ctx must use orth = 0 and no profiling and must not be in the engine already;
+ * rhs, x: device, full length, x holds the initial guess and receives the solution; they and the
+ * context stay in use until the solve is reported by gs_engine_poll.  Synchronises ctx's stream.
+ * GS_EBUSY when every slot is taken.
+ * gs_engine_step: one iteration of every solve in the engine; *active (may be NULL) = solves
+ * still running afterwards.  A failing solve (GS_ENOCONV, GS_EBREAKDOWN) finishes with that
+ * status; the return value reports engine failures only (GS_ECUDA).
+ * gs_engine_poll: copies up to max finished solves (oldest first) and forgets them.
+ * t_added / t_done: host steady-clock seconds at gs_engine_add and at the end of the step that
+ * finished the solve. */
+typedef struct gs_engine gs_engine;
+typedef struct {
+  long long tag;
+  gs_status status;
+  int iterations;
+  double rel_residual;
+  double t_added, t_done;
+} gs_engine_result;
+typedef struct {
+  long long steps;
+  long long batched_launches; /* per-step merged launches (outside the plan graph) */
+  long long plan_builds;
+  long long plan_kernels;     /* kernels in the current plan graph */
+  long long completed;
+} gs_engine_stats;
+gs_status gs_engine_create(int max_slots, int max_restart, void* stream, gs_engine** out);
+gs_status gs_engine_add(gs_engine* eng, gs_ctx* ctx, const double* rhs, double* x, double tol, long long tag);
+gs_status gs_engine_step(gs_engine* eng, int* active);
+int gs_engine_poll(gs_engine* eng, gs_engine_result* out, int max);
+int gs_engine_active(const gs_engine* eng);
+gs_status gs_engine_get_stats(const gs_engine* eng, gs_engine_stats* out);
+void gs_engine_destroy(gs_engine* eng);
 
 /* Change the stream work is enqueued on. */
 gs_status gs_set_stream(gs_ctx* ctx, void* stream);

@@ -4,6 +4,7 @@
 //
 // Every device buffer is carved out of the caller's workspace (no device allocation here);
 // every launch goes to the context's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 
 #include "gs.h"
 #include "gs_kernels.h"
+#include "gs_slot.h"
 
 using namespace gs;
 
@@ -79,6 +81,27 @@ struct Level {
   double pkc[3] = {0, 0, 0};
 };
 
+// State of the resumable FGMRES that the batching engine drives (see gs_slot.h).
+struct KState {
+  enum Phase { NONE = 0, INIT, RESID, ITER, FINAL, DONE };
+  enum Pend { P_NONE = 0, P_SCALE, P_XUPDATE, P_ZERO_X };
+  int phase = NONE, pend = P_NONE;
+  const double* b = nullptr;
+  double* x = nullptr;
+  double tol = 0.0;
+  bool from_conv = false, from_max = false, project_final = true;
+  int it = 0, extra = 0, j = 0, kx = 0;
+  double bnorm = 0.0, rel = 0.0;
+  std::vector<double> H, cs, sn, g, y;
+  const double* ydev = nullptr;
+  gs_status result = GS_OK;
+  std::string err;
+  bool body_ok = false;
+  Recorder body;
+  const void* zu = nullptr;
+  const void* zp = nullptr;
+};
+
 }  // namespace
 
 struct gs_ctx {
@@ -129,6 +152,8 @@ struct gs_ctx {
   std::vector<cudaEvent_t> evs;
   size_t ev_used = 0;
   std::vector<std::pair<int, size_t>> recs;
+  // batching engine state
+  KState ks;
 };
 
 namespace {
@@ -1306,6 +1331,307 @@ gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, co
 
 }  // namespace
 
+// ---- resumable FGMRES for the batching engine (gs_slot.h) ---------------------------------------
+// Offsets in the context's scalar area dsc (4 (m + 4) doubles): h1 at 0, h2 at m + 4, the norm
+// at 2 (m + 4), the pressure-mean sum at 3 (m + 4), then |r|^2 and |b|^2.
+namespace gs {
+namespace {
+double* sl_nrm(gs_ctx* c) { return c->dsc + 2 * (c->opt.restart + 4); }
+double* sl_beta2(gs_ctx* c) { return c->dsc + 3 * (c->opt.restart + 4) + 1; }
+double* sl_bn2(gs_ctx* c) { return c->dsc + 3 * (c->opt.restart + 4) + 2; }
+
+gs_status sl_fail(gs_ctx* c, gs_status s, const std::string& why) {
+  c->ks.result = s;
+  c->ks.err = why;
+  c->ks.phase = KState::DONE;
+  return GS_OK;  // a failed solve is a finished slot, not an engine error
+}
+
+// |v|^2 into dst with the kernels of dot_host (k = 1)
+gs_status sl_norm2(gs_ctx* c, const double* v, double* dst) {
+  KL(K_DOTS, launch_dots_partial<double>(v, c->N, 1, v, c->N, c->part, c->G, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, 1, c->G, dst, c->st));
+  return GS_OK;
+}
+
+template <typename T>
+gs_status sl_cast_in(gs_ctx* c, const double* v) {
+  Level& F = c->lv[c->L - 1];
+  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)c->p_b, F.Np, (T)1, c->st));
+  KL(K_VEC, launch_cast<double, T>(v, (T*)F.d, F.nu, (T)1, c->st));
+  return GS_OK;
+}
+template <typename T>
+gs_status sl_cast_out(gs_ctx* c, const double* v, double* z) {
+  Level& F = c->lv[c->L - 1];
+  KL(K_VEC, launch_cast<T, double>((const T*)c->ks.zu, z, F.nu, 1.0, c->st));
+  KL(K_VEC, launch_cast<T, double>((const T*)c->ks.zp, z + c->nu, F.Np, 1.0, c->st));
+  KL(K_VEC, launch_copy_constrained(v, z, F.g, c->st));
+  CKS(project_pressure(c, z));
+  return GS_OK;
+}
+}  // namespace
+
+gs_status report(gs_status s, const std::string& why) { return fail(s, why); }
+
+gs_status slot_begin(gs_ctx* c, const double* b, double* x, double tol) {
+  if (!c || !b || !x) return fail(GS_EINVAL, "NULL argument");
+  if (!(tol > 0.0)) return fail(GS_EINVAL, "tol must be > 0");
+  if (c->opt.orth != 0) return fail(GS_EINVAL, "batched solves use classical Gram-Schmidt twice (orth = 0)");
+  if (c->prof) return fail(GS_EINVAL, "kernel profiling is on for this context");
+  KState& k = c->ks;
+  const int m = c->opt.restart;
+  k.phase = KState::INIT;
+  k.pend = KState::P_NONE;
+  k.b = b;
+  k.x = x;
+  k.tol = tol;
+  k.from_conv = k.from_max = false;
+  k.project_final = true;
+  k.it = k.extra = k.j = k.kx = 0;
+  k.bnorm = k.rel = 0.0;
+  k.H.assign((size_t)(m + 1) * m, 0.0);
+  k.cs.assign(m, 0.0);
+  k.sn.assign(m, 0.0);
+  k.g.assign(m + 1, 0.0);
+  k.y.assign(m, 0.0);
+  k.ydev = nullptr;
+  k.result = GS_OK;
+  k.err.clear();
+  c->last_it = 0;
+  c->last_rel = 0.0;
+  return GS_OK;
+}
+
+const Recorder* slot_body(gs_ctx* c, gs_status* st) {
+  KState& k = c->ks;
+  *st = GS_OK;
+  if (k.body_ok) return &k.body;
+  k.body.clear();
+  Recorder* prev = current_recorder();
+  current_recorder() = &k.body;
+  *st = c->fp32 ? precond_body<float>(c) : precond_body<double>(c);
+  current_recorder() = prev;
+  if (*st != GS_OK) return nullptr;
+  k.zu = c->lv[c->L - 1].xA;  // where the recorded launches leave z_u and z_p
+  k.zp = c->p_xB;
+  k.body_ok = true;
+  return &k.body;
+}
+
+bool slot_wants_body(const gs_ctx* c) { return c->ks.phase == KState::ITER; }
+
+gs_status slot_record_pre(gs_ctx* c) {
+  KState& k = c->ks;
+  const long long N = c->N;
+  const bool dfk = c->opt.krylov_fp64 == 0;
+  float2* Vdf = reinterpret_cast<float2*>(c->V);
+  switch (k.pend) {
+    case KState::P_SCALE:  // v_{j+1} = w / |w|
+      if (dfk)
+        KL(K_AXPY, launch_scale_by_rnorm_df(c->w, sl_nrm(c), Vdf + (long long)k.j * N, c->vcur, N, c->st));
+      else
+        KL(K_AXPY, launch_scale_by_rnorm(c->w, sl_nrm(c), c->V + (long long)k.j * N, N, c->st));
+      break;
+    case KState::P_XUPDATE:  // x += Z y
+      KL(K_AXPY, launch_multi_axpy(c->Z, N, k.kx, k.ydev, 1.0, k.x, N, c->st));
+      break;
+    case KState::P_ZERO_X:
+      KL(K_VEC, launch_fill_zero<double>(k.x, N, c->st));
+      break;
+    default:
+      break;
+  }
+  k.pend = KState::P_NONE;
+  switch (k.phase) {
+    case KState::INIT:
+      CKS(sl_norm2(c, k.b, sl_bn2(c)));
+      // fall through: the first residual
+    case KState::RESID:
+      CKS(saddle(c, TILE_RESID, k.x, c->r, k.b));
+      CKS(sl_norm2(c, c->r, sl_beta2(c)));
+      if (dfk)
+        KL(K_AXPY, launch_scale_by_rnorm_df(c->r, sl_beta2(c), Vdf, c->vcur, N, c->st));
+      else
+        KL(K_AXPY, launch_scale_by_rnorm(c->r, sl_beta2(c), c->V, N, c->st));
+      break;
+    case KState::ITER: {
+      const double* v = dfk ? c->vcur : c->V + (long long)k.j * N;
+      CKS(c->fp32 ? sl_cast_in<float>(c, v) : sl_cast_in<double>(c, v));
+      break;
+    }
+    case KState::FINAL:
+      if (k.project_final) CKS(project_pressure(c, k.x));
+      break;
+    default:
+      break;
+  }
+  return GS_OK;
+}
+
+gs_status slot_record_post(gs_ctx* c, double* gather_dev) {
+  KState& k = c->ks;
+  const long long N = c->N;
+  const int m = c->opt.restart;
+  const bool dfk = c->opt.krylov_fp64 == 0;
+  float2* Vdf = reinterpret_cast<float2*>(c->V);
+  switch (k.phase) {
+    case KState::INIT:
+      KL(K_VEC, launch_gather3(sl_bn2(c), 1, sl_beta2(c), 1, sl_beta2(c), 0, gather_dev, c->st));
+      break;
+    case KState::RESID:
+      KL(K_VEC, launch_gather3(sl_beta2(c), 1, sl_beta2(c), 0, sl_beta2(c), 0, gather_dev, c->st));
+      break;
+    case KState::ITER: {
+      const int j = k.j;
+      const double* v = dfk ? c->vcur : c->V + (long long)j * N;
+      double* Zj = c->Z + (long long)j * N;
+      double* h1 = c->dsc;
+      double* h2 = c->dsc + (m + 4);
+      double* nrm = sl_nrm(c);
+      CKS(c->fp32 ? sl_cast_out<float>(c, v, Zj) : sl_cast_out<double>(c, v, Zj));
+      CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
+      if (dfk)
+        KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 1, c->st));
+      else
+        KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, j + 2, c->G, h1, c->st));
+      if (dfk)
+        KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
+      else
+        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+      if (dfk)
+        KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
+      else
+        KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
+      if (dfk)
+        KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+      else
+        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+      KL(K_VEC, launch_gather3(h1, j + 1, h2, j + 1, nrm, 1, gather_dev, c->st));
+      break;
+    }
+    default:
+      break;
+  }
+  return GS_OK;
+}
+
+gs_status slot_update(gs_ctx* c, const double* gathered, double* y_host, const double* y_dev) {
+  KState& k = c->ks;
+  const int m = c->opt.restart;
+  auto Hc = [&](int i, int j) -> double& { return k.H[(size_t)i * m + j]; };
+  switch (k.phase) {
+    case KState::INIT:
+    case KState::RESID: {
+      double beta2;
+      if (k.phase == KState::INIT) {
+        k.bnorm = std::sqrt(gathered[0]);
+        if (!std::isfinite(k.bnorm)) return sl_fail(c, GS_EBREAKDOWN, "right-hand side is not finite");
+        if (k.bnorm == 0.0) {  // x = 0, no iterations
+          k.pend = KState::P_ZERO_X;
+          k.project_final = false;
+          k.rel = 0.0;
+          k.phase = KState::FINAL;
+          return GS_OK;
+        }
+        beta2 = gathered[1];
+      } else {
+        beta2 = gathered[0];
+      }
+      const double beta = std::sqrt(beta2);
+      if (!std::isfinite(beta)) return sl_fail(c, GS_EBREAKDOWN, "residual is not finite");
+      k.rel = beta / k.bnorm;
+      if (k.from_conv) {  // explicit check after a cycle that converged on the implicit estimate
+        k.from_conv = false;
+        if (k.rel <= k.tol) { k.phase = KState::FINAL; return GS_OK; }
+        if (k.extra >= 3) { k.result = GS_ENOCONV; k.phase = KState::FINAL; return GS_OK; }
+        k.extra++;
+      } else if (k.from_max) {
+        k.from_max = false;
+        k.result = k.rel <= k.tol ? GS_OK : GS_ENOCONV;
+        k.phase = KState::FINAL;
+        return GS_OK;
+      }
+      if (k.rel <= k.tol) { k.phase = KState::FINAL; return GS_OK; }
+      if (k.it >= c->opt.max_iter) { k.result = GS_ENOCONV; k.phase = KState::FINAL; return GS_OK; }
+      std::fill(k.g.begin(), k.g.end(), 0.0);
+      k.g[0] = beta;
+      k.j = 0;
+      k.phase = KState::ITER;
+      return GS_OK;
+    }
+    case KState::ITER: {
+      const int j = k.j;
+      for (int i = 0; i <= j; ++i) Hc(i, j) = gathered[i];
+      for (int i = 0; i <= j; ++i) Hc(i, j) += gathered[j + 1 + i];
+      const double hn = std::sqrt(gathered[2 * (j + 1)]);
+      if (!std::isfinite(hn)) return sl_fail(c, GS_EBREAKDOWN, "Arnoldi vector is not finite");
+      Hc(j + 1, j) = hn;
+      for (int i = 0; i < j; ++i) {
+        const double tmp = k.cs[i] * Hc(i, j) + k.sn[i] * Hc(i + 1, j);
+        Hc(i + 1, j) = -k.sn[i] * Hc(i, j) + k.cs[i] * Hc(i + 1, j);
+        Hc(i, j) = tmp;
+      }
+      const double rr = std::hypot(Hc(j, j), Hc(j + 1, j));
+      k.cs[j] = Hc(j, j) / rr;
+      k.sn[j] = Hc(j + 1, j) / rr;
+      Hc(j, j) = rr;
+      Hc(j + 1, j) = 0.0;
+      k.g[j + 1] = -k.sn[j] * k.g[j];
+      k.g[j] = k.cs[j] * k.g[j];
+      k.it++;
+      const bool converged = std::fabs(k.g[j + 1]) / k.bnorm <= k.tol || hn == 0.0;
+      if (converged || k.it >= c->opt.max_iter || j + 1 == m) {
+        const int kk = j + 1;
+        for (int i = kk - 1; i >= 0; --i) {
+          double s = k.g[i];
+          for (int q = i + 1; q < kk; ++q) s -= Hc(i, q) * k.y[q];
+          k.y[i] = s / Hc(i, i);
+        }
+        for (int i = 0; i < kk; ++i) y_host[i] = k.y[i];
+        k.ydev = y_dev;
+        k.kx = kk;
+        k.pend = KState::P_XUPDATE;
+        k.from_conv = converged;
+        k.from_max = !converged && k.it >= c->opt.max_iter;
+        k.phase = KState::RESID;
+      } else {
+        k.j = j + 1;
+        k.pend = KState::P_SCALE;
+      }
+      return GS_OK;
+    }
+    case KState::FINAL:
+      k.phase = KState::DONE;
+      c->last_it = k.it;
+      c->last_rel = k.rel;
+      if (k.result == GS_ENOCONV) k.err = "FGMRES did not reach the tolerance";
+      return GS_OK;
+    default:
+      return GS_OK;
+  }
+}
+
+bool slot_done(const gs_ctx* c, gs_status* status, int* iterations, double* rel_residual) {
+  const KState& k = c->ks;
+  if (k.phase != KState::DONE) return false;
+  if (status) *status = k.result;
+  if (iterations) *iterations = k.it;
+  if (rel_residual) *rel_residual = k.rel;
+  return true;
+}
+const char* slot_error(const gs_ctx* c) { return c->ks.err.c_str(); }
+int slot_restart(const gs_ctx* c) { return c->opt.restart; }
+cudaStream_t slot_stream(const gs_ctx* c) { return c->st; }
+
+}  // namespace gs
+
+
+
 // =====================================================================================
 extern "C" {
 
@@ -1424,6 +1750,32 @@ gs_status gs_batch_solve(gs_ctx* const* ctxs, int count, const double* const* rh
                          int* iterations, double* rel_residuals) {
   if (!ctxs || !rhs || !x || count < 0) return fail(GS_EINVAL, "NULL argument");
   gs_status first = GS_OK;
+  bool engine_ok = count > 1;
+  int max_restart = 1;
+  for (int i = 0; i < count && engine_ok; ++i) {
+    if (!ctxs[i] || ctxs[i]->opt.orth != 0 || ctxs[i]->prof) engine_ok = false;
+    for (int q = 0; q < i && engine_ok; ++q) engine_ok = ctxs[q] != ctxs[i];
+    if (engine_ok) max_restart = std::max(max_restart, ctxs[i]->opt.restart);
+  }
+  if (engine_ok) {  // all systems together, one launch per kernel per iteration
+    gs_engine* eng = nullptr;
+    CKS(gs_engine_create(count, max_restart, ctxs[0]->st, &eng));
+    gs_status st = GS_OK;
+    for (int i = 0; i < count && st == GS_OK; ++i) st = gs_engine_add(eng, ctxs[i], rhs[i], x[i], tol, i);
+    int active = count;
+    while (st == GS_OK && active > 0) st = gs_engine_step(eng, &active);
+    std::vector<gs_engine_result> res(count);
+    const int got = gs_engine_poll(eng, res.data(), count);
+    gs_engine_destroy(eng);
+    if (st != GS_OK) return st;
+    for (int r = 0; r < got; ++r) {
+      const int i = (int)res[r].tag;
+      if (iterations) iterations[i] = res[r].iterations;
+      if (rel_residuals) rel_residuals[i] = res[r].rel_residual;
+      if (res[r].status != GS_OK && first == GS_OK) first = res[r].status;
+    }
+    return first;
+  }
   for (int i = 0; i < count; ++i) {
     int it = 0;
     double rr = 0.0;
@@ -1576,6 +1928,7 @@ const char* gs_strerror(gs_status s) {
     case GS_ENOCONV: return "no convergence";
     case GS_EBREAKDOWN: return "breakdown (non-finite values)";
     case GS_ETIMEOUT: return "timeout";
+    case GS_EBUSY: return "busy (no free slot)";
   }
   return "unknown status";
 }

@@ -1,0 +1,104 @@
+// Launch layer shared by single-instance and batched execution.
+//
+// Every kernel of the solve path is written once as a block body `K::body(args, blk, nblk)`
+// (blk = the block's index in the instance's own grid, nblk = that grid's size) and reached
+// through two entry points:
+//   k_one<K>   one instance, args in the parameter space, grid = nblk blocks;
+//   k_many<K>  many instances in one launch: block b runs work[b] = (args row, blk, nblk, slot)
+//              with the args row read from a device table.  Blocks of a slot whose entry in
+//              `active` is 0 return at once (the slot left the batch).
+// submit<K>() launches k_one immediately, or, while a Recorder is installed on the calling
+// thread, appends (kernel, args, nblk, shared bytes) to it instead.  The batching engine records
+// the same host code for every instance and merges the recordings step by step into k_many
+// launches, so a batched instance runs exactly the arithmetic of its single-instance solve.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+namespace gs {
+
+cudaError_t launched(cudaError_t e, int kernels);
+
+struct WorkItem {
+  int arg;   // row of the argument table
+  int blk;   // block index within the instance's grid
+  int nblk;  // the instance's grid size
+  int slot;  // engine slot (-1: not maskable)
+};
+
+using BatchFn = cudaError_t (*)(const void* tab, const WorkItem* work, int nwork, const int* active, size_t smem,
+                                cudaStream_t st);
+
+struct RecOp {
+  BatchFn fn;
+  int nblk;
+  int arg_size;
+  size_t arg_off;  // offset of the argument bytes in Recorder::bytes
+  size_t smem;
+};
+
+struct Recorder {
+  std::vector<RecOp> ops;
+  std::vector<unsigned char> bytes;
+  void add(BatchFn fn, const void* args, int size, int nblk, size_t smem) {
+    const size_t off = (bytes.size() + 15) & ~size_t(15);
+    bytes.resize(off + size);
+    std::memcpy(bytes.data() + off, args, size);
+    ops.push_back(RecOp{fn, nblk, size, off, smem});
+  }
+  void clear() {
+    ops.clear();
+    bytes.clear();
+  }
+};
+
+// recorder installed on this thread (nullptr: launch immediately)
+Recorder*& current_recorder();
+
+template <class K>
+__global__ void __launch_bounds__(K::THREADS, K::MINB) k_one(const typename K::Args a) {
+  K::body(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::THREADS, K::MINB)
+    k_many(const typename K::Args* __restrict__ tab, const WorkItem* __restrict__ work, const int* __restrict__ active) {
+  const WorkItem w = work[blockIdx.x];
+  if (active != nullptr && w.slot >= 0 && active[w.slot] == 0) return;
+  K::body(tab[w.arg], w.blk, w.nblk);
+}
+
+template <class K>
+cudaError_t batch_launch(const void* tab, const WorkItem* work, int nwork, const int* active, size_t smem,
+                         cudaStream_t st) {
+  if (nwork <= 0) return cudaSuccess;
+  static size_t configured = 48 * 1024;  // per instantiation: largest dynamic size enabled so far
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_many<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k_many<K><<<(unsigned)nwork, K::THREADS, smem, st>>>((const typename K::Args*)tab, work, active);
+  return launched(cudaGetLastError(), 1);
+}
+
+template <class K>
+cudaError_t submit(const typename K::Args& a, long long nblk, size_t smem, cudaStream_t st) {
+  if (nblk < 1) nblk = 1;
+  if (Recorder* r = current_recorder()) {
+    r->add(&batch_launch<K>, &a, (int)sizeof(a), (int)nblk, smem);
+    return cudaSuccess;
+  }
+  static size_t configured = 48 * 1024;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_one<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  k_one<K><<<(unsigned)nblk, K::THREADS, smem, st>>>(a);
+  return launched(cudaGetLastError(), 1);
+}
+
+}  // namespace gs

@@ -8,6 +8,10 @@
 namespace gs {
 
 static std::atomic<long long> g_launches{0};
+Recorder*& current_recorder() {
+  static thread_local Recorder* r = nullptr;
+  return r;
+}
 cudaError_t launched(cudaError_t e, int kernels) {
   if (e == cudaSuccess) g_launches.fetch_add(kernels, std::memory_order_relaxed);
   return e;
@@ -43,30 +47,38 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 }  // namespace
 
+// grid-stride loop of one instance: element indices of block blk out of nblk
+#define GS_FOR(i, n) \
+  for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)nblk * blockDim.x)
+
 template <typename T>
-__global__ void k_cheb_init0(const T* __restrict__ b, const T* __restrict__ dinv, T inv_theta,
-                             T* __restrict__ d, T* __restrict__ x, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const T v = dinv[i] * b[i] * inv_theta;
-    d[i] = v;
-    x[i] = v;
+struct ChebInit0K {
+  struct Args { const T* b; const T* dinv; T inv_theta; T* d; T* x; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    GS_FOR(i, a.n) {
+      const T v = a.dinv[i] * a.b[i] * a.inv_theta;
+      a.d[i] = v;
+      a.x[i] = v;
+    }
   }
-}
+};
 template <typename T>
 cudaError_t launch_cheb_init0(const T* b, const T* dinv, T inv_theta, T* d, T* x, long long n, cudaStream_t st) {
-  k_cheb_init0<T><<<nblk(n), TPB, 0, st>>>(b, dinv, inv_theta, d, x, n);
-  return launched(cudaGetLastError());
+  return submit<ChebInit0K<T>>({b, dinv, inv_theta, d, x, n}, nblk(n), 0, st);
 }
 
 template <typename TI, typename TO>
-__global__ void k_cast(const TI* in, TO* out, long long n, TO scale) {  // may run in place
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = scale * (TO)in[i];
-}
+struct CastK {  // may run in place
+  struct Args { const TI* in; TO* out; long long n; TO scale; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    GS_FOR(i, a.n) a.out[i] = a.scale * (TO)a.in[i];
+  }
+};
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* in, TO* out, long long n, TO scale, cudaStream_t st) {
-  k_cast<TI, TO><<<nblk(n), TPB, 0, st>>>(in, out, n, scale);
-  return launched(cudaGetLastError());
+  return submit<CastK<TI, TO>>({in, out, n, scale}, nblk(n), 0, st);
 }
 
 template <typename T>
@@ -114,88 +126,96 @@ cudaError_t launch_lanczos_post(const T* dinv, const T* y, const T* vprev, T bet
 // and the block reduces KB sums at once (one barrier pair per KB vectors).  Deterministic: the
 // element-to-thread assignment and the reduction tree are fixed by the launch shape.
 template <typename T, int KB>
-__global__ void k_dots_partial(const T* __restrict__ V, long long ldv, int k, const T* __restrict__ w,
-                               long long n, double* __restrict__ part, int self_dot) {
-  __shared__ double sh[KB + 1][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i0 = 0; i0 < k || (i0 == 0 && self_dot); i0 += KB) {
-    const int kb = max(0, min(KB, k - i0));
-    const bool self = self_dot && i0 == 0;  // w . w rides along with the first block of vectors
-    double acc[KB], accw = 0.0;
+struct DotsK {
+  struct Args { const T* V; long long ldv; int k; const T* w; long long n; double* part; int self_dot; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ double sh[KB + 1][32];
+    const T* __restrict__ V = a.V;
+    const T* __restrict__ w = a.w;
+    const long long ldv = a.ldv, n = a.n;
+    const int k = a.k;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i0 = 0; i0 < k || (i0 == 0 && a.self_dot); i0 += KB) {
+      const int kb = max(0, min(KB, k - i0));
+      const bool self = a.self_dot && i0 == 0;  // w . w rides along with the first block of vectors
+      double acc[KB], accw = 0.0;
 #pragma unroll
-    for (int i = 0; i < KB; ++i) acc[i] = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-      const double we = (double)w[e];
-      if (self) accw += we * we;
+      for (int i = 0; i < KB; ++i) acc[i] = 0.0;
+      GS_FOR(e, n) {
+        const double we = (double)w[e];
+        if (self) accw += we * we;
 #pragma unroll
-      for (int i = 0; i < KB; ++i)
-        if (i < kb) acc[i] += (double)V[(i0 + i) * ldv + e] * we;
-    }
+        for (int i = 0; i < KB; ++i)
+          if (i < kb) acc[i] += (double)V[(i0 + i) * ldv + e] * we;
+      }
 #pragma unroll
-    for (int i = 0; i <= KB; ++i) {
-      double v = i < KB ? acc[i] : accw;
+      for (int i = 0; i <= KB; ++i) {
+        double v = i < KB ? acc[i] : accw;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) sh[i][wid] = v;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[i][wid] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < kb) {
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += sh[threadIdx.x][q];
+        a.part[(long long)(i0 + threadIdx.x) * nblk + blk] = t;
+      }
+      if (self && threadIdx.x == 32) {  // the row after the k dot products
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += sh[KB][q];
+        a.part[(long long)k * nblk + blk] = t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x < kb) {
-      double t = 0.0;
-      for (int q = 0; q < nw; ++q) t += sh[threadIdx.x][q];
-      part[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
-    }
-    if (self && threadIdx.x == 32) {  // the row after the k dot products
-      double t = 0.0;
-      for (int q = 0; q < nw; ++q) t += sh[KB][q];
-      part[(long long)k * gridDim.x + blockIdx.x] = t;
-    }
-    __syncthreads();
   }
-}
+};
 template <typename T>
 cudaError_t launch_dots_partial(const T* V, long long ldv, int k, const T* w, long long n, double* part, int G,
                                 cudaStream_t st) {
-  if (k <= 1)
-    k_dots_partial<T, 1><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, 0);
-  else
-    k_dots_partial<T, 8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, 0);
-  return launched(cudaGetLastError());
+  if (k <= 1) return submit<DotsK<T, 1>>({V, ldv, k, w, n, part, 0}, G, 0, st);
+  return submit<DotsK<T, 8>>({V, ldv, k, w, n, part, 0}, G, 0, st);
 }
 cudaError_t launch_dots_norm_partial(const double* V, long long ldv, int k, const double* w, long long n, double* part,
                                      int G, cudaStream_t st) {
-  k_dots_partial<double, 8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, 1);
-  return launched(cudaGetLastError());
+  return submit<DotsK<double, 8>>({V, ldv, k, w, n, part, 1}, G, 0, st);
 }
 
 // w <- w + sign * sum_i coef[i] V[i], and per-block partial sums of the new |w|^2
-__global__ void k_multi_axpy_norm(const double* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
-                                  double sign, double* __restrict__ w, long long n, double* __restrict__ part) {
-  extern __shared__ double cs[];
-  __shared__ double sh[32];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = sign * coef[i];
-  __syncthreads();
-  double s = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double acc = w[e];
-    for (int i = 0; i < k; ++i) acc += cs[i] * V[i * ldv + e];
-    w[e] = acc;
-    s += acc * acc;
-  }
+struct MultiAxpyNormK {
+  struct Args { const double* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    extern __shared__ double cs[];
+    __shared__ double sh[32];
+    const double* __restrict__ V = a.V;
+    double* __restrict__ w = a.w;
+    const int k = a.k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = a.sign * a.coef[i];
+    __syncthreads();
+    double s = 0.0;
+    GS_FOR(e, a.n) {
+      double acc = w[e];
+      for (int i = 0; i < k; ++i) acc += cs[i] * V[i * a.ldv + e];
+      w[e] = acc;
+      s += acc * acc;
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
-    part[blockIdx.x] = t;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+      a.part[blk] = t;
+    }
   }
-}
+};
 cudaError_t launch_multi_axpy_norm(const double* V, long long ldv, int k, const double* coef, double sign, double* w,
                                    long long n, double* part, int G, cudaStream_t st) {
-  k_multi_axpy_norm<<<G, TPB, sizeof(double) * (k > 0 ? k : 1), st>>>(V, ldv, k, coef, sign, w, n, part);
-  return launched(cudaGetLastError());
+  return submit<MultiAxpyNormK>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(double) * (k > 0 ? k : 1), st);
 }
 
 // ---- Krylov basis in double-float form (GB300: FP64 is 1/74 of the FP32 rate) ----------------------
@@ -224,175 +244,197 @@ __device__ __forceinline__ void df_fma(float2& acc, float2 a, float2 b) {
 }
 
 template <int KB>
-__global__ void __launch_bounds__(256, 3)
-    k_dots_partial_df(const float2* __restrict__ V, long long ldv, int k, const double* __restrict__ w,
-                      long long n, double* __restrict__ part, int self_dot) {
-  __shared__ double sh[KB + 1][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (int i0 = 0; i0 < k; i0 += KB) {
-    const int kb = min(KB, k - i0);
-    const bool self = self_dot && i0 == 0;
-    float2 acc[KB];
-    double accw = 0.0;
+struct DotsDfK {
+  struct Args { const float2* V; long long ldv; int k; const double* w; long long n; double* part; int self_dot; };
+  static constexpr int THREADS = TPB, MINB = 3;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ double sh[KB + 1][32];
+    const float2* __restrict__ V = a.V;
+    const double* __restrict__ w = a.w;
+    const long long ldv = a.ldv, n = a.n;
+    const int k = a.k;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long stride = (long long)nblk * blockDim.x;
+    for (int i0 = 0; i0 < k; i0 += KB) {
+      const int kb = min(KB, k - i0);
+      const bool self = a.self_dot && i0 == 0;
+      float2 acc[KB];
+      double accw = 0.0;
 #pragma unroll
-    for (int i = 0; i < KB; ++i) acc[i] = make_float2(0.f, 0.f);
-    const float2* Vb = V + i0 * ldv;
-    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    // two elements per iteration, every load issued before the double-float arithmetic
-    for (; e + stride < n; e += 2 * stride) {
-      const double wd0 = w[e], wd1 = w[e + stride];
-      float2 v0[KB], v1[KB];
+      for (int i = 0; i < KB; ++i) acc[i] = make_float2(0.f, 0.f);
+      const float2* Vb = V + i0 * ldv;
+      long long e = blk * (long long)blockDim.x + threadIdx.x;
+      // two elements per iteration, every load issued before the double-float arithmetic
+      for (; e + stride < n; e += 2 * stride) {
+        const double wd0 = w[e], wd1 = w[e + stride];
+        float2 v0[KB], v1[KB];
 #pragma unroll
-      for (int i = 0; i < KB; ++i) {
-        v0[i] = i < kb ? Vb[i * ldv + e] : make_float2(0.f, 0.f);
-        v1[i] = i < kb ? Vb[i * ldv + e + stride] : make_float2(0.f, 0.f);
+        for (int i = 0; i < KB; ++i) {
+          v0[i] = i < kb ? Vb[i * ldv + e] : make_float2(0.f, 0.f);
+          v1[i] = i < kb ? Vb[i * ldv + e + stride] : make_float2(0.f, 0.f);
+        }
+        if (self) accw += wd0 * wd0 + wd1 * wd1;
+        const float2 we0 = df_split(wd0), we1 = df_split(wd1);
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+          df_fma(acc[i], v0[i], we0);
+          df_fma(acc[i], v1[i], we1);
+        }
       }
-      if (self) accw += wd0 * wd0 + wd1 * wd1;
-      const float2 we0 = df_split(wd0), we1 = df_split(wd1);
+      if (e < n) {
+        const double wd = w[e];
+        if (self) accw += wd * wd;
+        const float2 we = df_split(wd);
 #pragma unroll
-      for (int i = 0; i < KB; ++i) {
-        df_fma(acc[i], v0[i], we0);
-        df_fma(acc[i], v1[i], we1);
+        for (int i = 0; i < KB; ++i)
+          if (i < kb) df_fma(acc[i], Vb[i * ldv + e], we);
       }
-    }
-    if (e < n) {
-      const double wd = w[e];
-      if (self) accw += wd * wd;
-      const float2 we = df_split(wd);
 #pragma unroll
-      for (int i = 0; i < KB; ++i)
-        if (i < kb) df_fma(acc[i], Vb[i * ldv + e], we);
-    }
+      for (int i = 0; i <= KB; ++i) {
+        double v = i < KB ? df_join(acc[i]) : accw;
 #pragma unroll
-    for (int i = 0; i <= KB; ++i) {
-      double v = i < KB ? df_join(acc[i]) : accw;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) sh[i][wid] = v;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[i][wid] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < kb) {
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += sh[threadIdx.x][q];
+        a.part[(long long)(i0 + threadIdx.x) * nblk + blk] = t;
+      }
+      if (self && threadIdx.x == 32) {
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += sh[KB][q];
+        a.part[(long long)k * nblk + blk] = t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x < kb) {
-      double t = 0.0;
-      for (int q = 0; q < nw; ++q) t += sh[threadIdx.x][q];
-      part[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
-    }
-    if (self && threadIdx.x == 32) {
-      double t = 0.0;
-      for (int q = 0; q < nw; ++q) t += sh[KB][q];
-      part[(long long)k * gridDim.x + blockIdx.x] = t;
-    }
-    __syncthreads();
   }
-}
+};
 cudaError_t launch_dots_partial_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
                                    int G, int self_dot, cudaStream_t st) {
-  k_dots_partial_df<8><<<G, TPB, 0, st>>>(V, ldv, k, w, n, part, self_dot);
-  return launched(cudaGetLastError());
+  return submit<DotsDfK<8>>({V, ldv, k, w, n, part, self_dot}, G, 0, st);
 }
 
 // w <- w + sign * sum_i coef[i] V[i] (sum carried in double-float), partial sums of the new |w|^2
-__global__ void k_multi_axpy_norm_df(const float2* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
-                                     double sign, double* __restrict__ w, long long n, double* __restrict__ part) {
-  extern __shared__ float2 cs2[];
-  __shared__ double sh[32];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) cs2[i] = df_split(sign * coef[i]);
-  __syncthreads();
-  double s = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const double we = w[e];
-    float2 acc = make_float2(0.f, 0.f);
-    int i = 0;
-    for (; i + 8 <= k; i += 8) {  // eight basis loads in flight per thread
-      float2 v[8];
+struct MultiAxpyNormDfK {
+  struct Args { const float2* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    extern __shared__ float2 cs2[];
+    __shared__ double sh[32];
+    const float2* __restrict__ V = a.V;
+    double* __restrict__ w = a.w;
+    const long long ldv = a.ldv;
+    const int k = a.k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs2[i] = df_split(a.sign * a.coef[i]);
+    __syncthreads();
+    double s = 0.0;
+    GS_FOR(e, a.n) {
+      const double we = w[e];
+      float2 acc = make_float2(0.f, 0.f);
+      int i = 0;
+      for (; i + 8 <= k; i += 8) {  // eight basis loads in flight per thread
+        float2 v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = V[(i + u) * ldv + e];
+        for (int u = 0; u < 8; ++u) v[u] = V[(i + u) * ldv + e];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) df_fma(acc, cs2[i + u], v[u]);
+        for (int u = 0; u < 8; ++u) df_fma(acc, cs2[i + u], v[u]);
+      }
+      for (; i < k; ++i) df_fma(acc, cs2[i], V[i * ldv + e]);
+      const double r = we + df_join(acc);
+      w[e] = r;
+      s += r * r;
     }
-    for (; i < k; ++i) df_fma(acc, cs2[i], V[i * ldv + e]);
-    const double r = we + df_join(acc);
-    w[e] = r;
-    s += r * r;
-  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) sh[wid] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
-    part[blockIdx.x] = t;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+      a.part[blk] = t;
+    }
   }
-}
+};
 cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
                                       long long n, double* part, int G, cudaStream_t st) {
-  k_multi_axpy_norm_df<<<G, TPB, sizeof(float2) * (k > 0 ? k : 1), st>>>(V, ldv, k, coef, sign, w, n, part);
-  return launched(cudaGetLastError());
+  return submit<MultiAxpyNormDfK>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(float2) * (k > 0 ? k : 1), st);
 }
 
 // v_df <- w / sqrt(nrm2) in double-float form, and the same vector as double in vd
-__global__ void k_scale_by_rnorm_df(const double* __restrict__ w, const double* __restrict__ nrm2,
-                                    float2* __restrict__ v, double* __restrict__ vd, long long n) {
-  const double sc = 1.0 / sqrt(nrm2[0]);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double x = w[i] * sc;
-    v[i] = df_split(x);
-    vd[i] = x;
+struct ScaleDfK {
+  struct Args { const double* w; const double* nrm2; float2* v; double* vd; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    const double sc = 1.0 / sqrt(a.nrm2[0]);
+    GS_FOR(i, a.n) {
+      const double x = a.w[i] * sc;
+      a.v[i] = df_split(x);
+      a.vd[i] = x;
+    }
   }
-}
+};
 cudaError_t launch_scale_by_rnorm_df(const double* w, const double* nrm2, float2* v, double* vd, long long n,
                                      cudaStream_t st) {
   unsigned g = nblk(n);
   if (g > 152u * 16u) g = 152u * 16u;
-  k_scale_by_rnorm_df<<<g, TPB, 0, st>>>(w, nrm2, v, vd, n);
-  return launched(cudaGetLastError());
+  return submit<ScaleDfK>({w, nrm2, v, vd, n}, g, 0, st);
 }
 
-__global__ void k_reduce_partials(const double* __restrict__ part, int G, double* __restrict__ out) {
-  __shared__ double sh[32];
-  const int i = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < G; b += blockDim.x) s += part[(long long)i * G + b];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) out[i] = s;
-}
-cudaError_t launch_reduce_partials(const double* part, int k, int G, double* out, cudaStream_t st) {
-  k_reduce_partials<<<k, TPB, 0, st>>>(part, G, out);
-  return launched(cudaGetLastError());
-}
-
-__global__ void k_multi_axpy(const double* __restrict__ V, long long ldv, int k, const double* __restrict__ coef,
-                             double sign, double* __restrict__ w, long long n) {
-  extern __shared__ double cs[];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = sign * coef[i];
-  __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double acc = w[e];
-    for (int i = 0; i < k; ++i) acc += cs[i] * V[i * ldv + e];
-    w[e] = acc;
+struct ReduceK {
+  struct Args { const double* part; int G; double* out; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    __shared__ double sh[32];
+    const int i = blk;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < a.G; b += blockDim.x) s += a.part[(long long)i * a.G + b];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) a.out[i] = s;
   }
+};
+cudaError_t launch_reduce_partials(const double* part, int k, int G, double* out, cudaStream_t st) {
+  return submit<ReduceK>({part, G, out}, k, 0, st);
 }
+
+struct MultiAxpyK {
+  struct Args { const double* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    extern __shared__ double cs[];
+    const double* __restrict__ V = a.V;
+    double* __restrict__ w = a.w;
+    const int k = a.k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = a.sign * a.coef[i];
+    __syncthreads();
+    GS_FOR(e, a.n) {
+      double acc = w[e];
+      for (int i = 0; i < k; ++i) acc += cs[i] * V[i * a.ldv + e];
+      w[e] = acc;
+    }
+  }
+};
 cudaError_t launch_multi_axpy(const double* V, long long ldv, int k, const double* coef, double sign, double* w,
                               long long n, cudaStream_t st) {
   unsigned g = nblk(n);
   if (g > 152u * 16u) g = 152u * 16u;
-  k_multi_axpy<<<g, TPB, sizeof(double) * (k > 0 ? k : 1), st>>>(V, ldv, k, coef, sign, w, n);
-  return launched(cudaGetLastError());
+  return submit<MultiAxpyK>({V, ldv, k, coef, sign, w, n}, g, sizeof(double) * (k > 0 ? k : 1), st);
 }
 
-__global__ void k_scale_by_rnorm(const double* __restrict__ w, const double* __restrict__ nrm2,
-                                 double* __restrict__ v, long long n) {
-  const double s = 1.0 / sqrt(nrm2[0]);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    v[i] = w[i] * s;
-}
+struct ScaleK {
+  struct Args { const double* w; const double* nrm2; double* v; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    const double s = 1.0 / sqrt(a.nrm2[0]);
+    GS_FOR(i, a.n) a.v[i] = a.w[i] * s;
+  }
+};
 cudaError_t launch_scale_by_rnorm(const double* w, const double* nrm2, double* v, long long n, cudaStream_t st) {
   unsigned g = nblk(n);
   if (g > 152u * 16u) g = 152u * 16u;
-  k_scale_by_rnorm<<<g, TPB, 0, st>>>(w, nrm2, v, n);
-  return launched(cudaGetLastError());
+  return submit<ScaleK>({w, nrm2, v, n}, g, 0, st);
 }
 
 __global__ void k_add_vec(double* a, const double* b, int k) {
@@ -404,62 +446,102 @@ cudaError_t launch_add_vec(double* a, const double* b, int k, cudaStream_t st) {
   return launched(cudaGetLastError());
 }
 
-__global__ void k_masked_sum_partial(const double* __restrict__ x, const uint8_t* __restrict__ mask, long long n,
-                                     double* __restrict__ part) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    if (!mask || !mask[e]) s += x[e];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
+struct MaskedSumK {
+  struct Args { const double* x; const uint8_t* mask; long long n; double* part; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    GS_FOR(e, a.n)
+      if (!a.mask || !a.mask[e]) s += a.x[e];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) a.part[blk] = s;
+  }
+};
 cudaError_t launch_masked_sum_partial(const double* x, const uint8_t* mask, long long n, double* part, int G,
                                       cudaStream_t st) {
-  k_masked_sum_partial<<<G, TPB, 0, st>>>(x, mask, n, part);
-  return launched(cudaGetLastError());
+  return submit<MaskedSumK>({x, mask, n, part}, G, 0, st);
 }
-__global__ void k_sub_scalar_masked(double* __restrict__ x, const uint8_t* __restrict__ mask, long long n,
-                                    const double* __restrict__ sum, double inv_count) {
-  const double m = sum[0] * inv_count;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    if (!mask || !mask[e]) x[e] -= m;
-}
+struct SubScalarK {
+  struct Args { double* x; const uint8_t* mask; long long n; const double* sum; double inv_count; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    const double m = a.sum[0] * a.inv_count;
+    GS_FOR(e, a.n)
+      if (!a.mask || !a.mask[e]) a.x[e] -= m;
+  }
+};
 cudaError_t launch_sub_scalar_masked(double* x, const uint8_t* mask, long long n, const double* sum,
                                      double inv_count, cudaStream_t st) {
-  k_sub_scalar_masked<<<nblk(n), TPB, 0, st>>>(x, mask, n, sum, inv_count);
-  return launched(cudaGetLastError());
+  return submit<SubScalarK>({x, mask, n, sum, inv_count}, nblk(n), 0, st);
 }
 
 // ---- dense coarse solve (explicit inverse of A_0 on its free unknowns) ------------------------------
 template <typename T>
-__global__ void k_coarse_gather(const T* __restrict__ b, const int* __restrict__ freeidx, int nf, double* __restrict__ tmp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nf) tmp[i] = (double)b[freeidx[i]];
-}
+struct CoarseGatherK {
+  struct Args { const T* b; const int* freeidx; int nf; double* tmp; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    const int i = blk * blockDim.x + threadIdx.x;
+    if (i < a.nf) a.tmp[i] = (double)a.b[a.freeidx[i]];
+  }
+};
 template <typename T>
-__global__ void k_coarse_gemv(const double* __restrict__ Ainv, const int* __restrict__ freeidx, int nf,
-                              const double* __restrict__ tmp, T* __restrict__ y) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= nf) return;
-  const double* row = Ainv + (long long)warp * nf;
-  double s = 0.0;
-  for (int j = lane; j < nf; j += 32) s += row[j] * tmp[j];
-  s = warp_sum(s);
-  if (lane == 0) y[freeidx[warp]] = (T)s;
-}
+struct CoarseGemvK {
+  struct Args { const double* Ainv; const int* freeidx; int nf; const double* tmp; T* y; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    const int warp = (blk * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= a.nf) return;
+    const double* row = a.Ainv + (long long)warp * a.nf;
+    double s = 0.0;
+    for (int j = lane; j < a.nf; j += 32) s += row[j] * a.tmp[j];
+    s = warp_sum(s);
+    if (lane == 0) a.y[a.freeidx[warp]] = (T)s;
+  }
+};
 template <typename T>
-__global__ void k_zero(T* y, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = T(0);
-}
+struct ZeroK {
+  struct Args { T* y; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    GS_FOR(i, a.n) a.y[i] = T(0);
+  }
+};
 template <typename T>
 cudaError_t launch_coarse_solve(const double* Ainv, const int* freeidx, int nf, const T* b, T* y, long long n,
                                 double* tmp, cudaStream_t st) {
-  k_coarse_gather<T><<<(nf + TPB - 1) / TPB, TPB, 0, st>>>(b, freeidx, nf, tmp);
-  k_zero<T><<<nblk(n), TPB, 0, st>>>(y, n);
-  k_coarse_gemv<T><<<(unsigned)(((long long)nf * 32 + TPB - 1) / TPB), TPB, 0, st>>>(Ainv, freeidx, nf, tmp, y);
-  return launched(cudaGetLastError(), 3);
+  cudaError_t e = submit<CoarseGatherK<T>>({b, freeidx, nf, tmp}, (nf + TPB - 1) / TPB, 0, st);
+  if (e != cudaSuccess) return e;
+  e = submit<ZeroK<T>>({y, n}, nblk(n), 0, st);
+  if (e != cudaSuccess) return e;
+  return submit<CoarseGemvK<T>>({Ainv, freeidx, nf, tmp, y}, ((long long)nf * 32 + TPB - 1) / TPB, 0, st);
+}
+
+// y[0..n) = 0 (no read of y: safe on uninitialised memory)
+template <typename T>
+cudaError_t launch_fill_zero(T* y, long long n, cudaStream_t st) {
+  return submit<ZeroK<T>>({y, n}, nblk(n), 0, st);
+}
+template cudaError_t launch_fill_zero<double>(double*, long long, cudaStream_t);
+
+// dst = [s0[0..n0) | s1[0..n1) | s2[0..n2)]: the host-bound scalars of one instance in one place
+struct Gather3K {
+  struct Args { const double* s[3]; int n[3]; double* dst; };
+  static constexpr int THREADS = 64, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int, int) {
+    int off = 0;
+    for (int q = 0; q < 3; ++q) {
+      for (int i = threadIdx.x; i < a.n[q]; i += blockDim.x) a.dst[off + i] = a.s[q][i];
+      off += a.n[q];
+    }
+  }
+};
+cudaError_t launch_gather3(const double* s0, int n0, const double* s1, int n1, const double* s2, int n2, double* dst,
+                           cudaStream_t st) {
+  Gather3K::Args a{{s0, s1, s2}, {n0, n1, n2}, dst};
+  return submit<Gather3K>(a, 1, 0, st);
 }
 
 // Gauss-Jordan inversion of an SPD matrix (no pivoting), one pivot per pair of launches.
@@ -515,15 +597,18 @@ __device__ __forceinline__ bool full_constrained(const Geom& geo, long long i) {
   return geo.pmask ? geo.pmask[i - n_u] != 0 : false;
 }
 
-__global__ void k_copy_constrained(const double* __restrict__ v, double* __restrict__ z, const Geom geo) {
-  const long long N = geo.dim * geo.Nv + geo.Np;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    if (full_constrained(geo, i)) z[i] = v[i];
-}
+struct CopyConstrainedK {
+  struct Args { const double* v; double* z; Geom geo; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    const long long N = a.geo.dim * a.geo.Nv + a.geo.Np;
+    GS_FOR(i, N)
+      if (full_constrained(a.geo, i)) a.z[i] = a.v[i];
+  }
+};
 cudaError_t launch_copy_constrained(const double* v, double* z, const Geom& geo, cudaStream_t st) {
   const long long N = geo.dim * geo.Nv + geo.Np;
-  k_copy_constrained<<<nblk(N), TPB, 0, st>>>(v, z, geo);
-  return launched(cudaGetLastError());
+  return submit<CopyConstrainedK>({v, z, geo}, nblk(N), 0, st);
 }
 
 // rhs = Mf - Kg on free entries, g on constrained entries (velocity then pressure)

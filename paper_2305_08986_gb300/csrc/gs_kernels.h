@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "gs_batch.cuh"
 #include "gs_common.cuh"
 
 namespace gs {
@@ -182,6 +183,11 @@ cudaError_t launch_coarse_solve(const double* Ainv, const int* freeidx, int nf, 
 cudaError_t launch_gj_save(const double* A, int n, int k, double* row, double* col, cudaStream_t st);
 cudaError_t launch_gj_update(double* A, int n, int k, const double* row, const double* col,
                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill_zero(T* y, long long n, cudaStream_t st);
+// dst = [s0[0..n0) | s1[0..n1) | s2[0..n2)]  (one block)
+cudaError_t launch_gather3(const double* s0, int n0, const double* s1, int n1, const double* s2, int n2, double* dst,
+                           cudaStream_t st);
 template <typename T>
 cudaError_t launch_axpby(const T* x, T* y, T a, T b, long long n, cudaStream_t st);  // y = a x + b y
 // z[i] = v[i] on every constrained entry of a full vector [u | p] (finest level)

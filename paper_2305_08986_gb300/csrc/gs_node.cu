@@ -94,9 +94,17 @@ __device__ __forceinline__ int restrict_stencil(int C, int nvf, int* fi, double*
   return m;
 }
 
+template <typename T>
+struct XferArgs {
+  Geom gf, gc;
+  const T* in;
+  T* out;
+};
+
 template <typename T, int DIM>
-__global__ void k_restrict(const Geom gf, const Geom gc, const T* __restrict__ rf, T* __restrict__ rc) {
-  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, const T* __restrict__ rf,
+                                              T* __restrict__ rc, int blk) {
+  const long long node = blk * (long long)blockDim.x + threadIdx.x;
   if (node >= gc.Nv) return;
   int I, J, K;
   unflat(node, gc.nv, DIM, I, J, K);
@@ -142,8 +150,9 @@ __device__ __forceinline__ int prolong_stencil(int I, int* ci, double* w) {
 }
 
 template <typename T, int DIM>
-__global__ void k_prolong_add(const Geom gf, const Geom gc, const T* __restrict__ xc, T* __restrict__ xf) {
-  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void prolong_add_body(const Geom& gf, const Geom& gc, const T* __restrict__ xc,
+                                                 T* __restrict__ xf, int blk) {
+  const long long node = blk * (long long)blockDim.x + threadIdx.x;
   if (node >= gf.Nv) return;
   int I, J, K;
   unflat(node, gf.nv, DIM, I, J, K);
@@ -173,22 +182,35 @@ __global__ void k_prolong_add(const Geom gf, const Geom gc, const T* __restrict_
   for (int a = 0; a < DIM; ++a) xf[a * gf.Nv + node] += acc[a];
 }
 
+template <typename T, int DIM>
+struct RestrictK {
+  using Args = XferArgs<T>;
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    restrict_body<T, DIM>(a.gf, a.gc, a.in, a.out, blk);
+  }
+};
+template <typename T, int DIM>
+struct ProlongAddK {
+  using Args = XferArgs<T>;
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    prolong_add_body<T, DIM>(a.gf, a.gc, a.in, a.out, blk);
+  }
+};
+
 template <typename T>
 cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st) {
-  if (gf.dim == 2)
-    k_restrict<T, 2><<<nblk(gc.Nv), TPB, 0, st>>>(gf, gc, rf, rc);
-  else
-    k_restrict<T, 3><<<nblk(gc.Nv), TPB, 0, st>>>(gf, gc, rf, rc);
-  return launched(cudaGetLastError());
+  const XferArgs<T> a{gf, gc, rf, rc};
+  if (gf.dim == 2) return submit<RestrictK<T, 2>>(a, nblk(gc.Nv), 0, st);
+  return submit<RestrictK<T, 3>>(a, nblk(gc.Nv), 0, st);
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(const Geom& gf, const Geom& gc, const T* xc, T* xf, cudaStream_t st) {
-  if (gf.dim == 2)
-    k_prolong_add<T, 2><<<nblk(gf.Nv), TPB, 0, st>>>(gf, gc, xc, xf);
-  else
-    k_prolong_add<T, 3><<<nblk(gf.Nv), TPB, 0, st>>>(gf, gc, xc, xf);
-  return launched(cudaGetLastError());
+  const XferArgs<T> a{gf, gc, xc, xf};
+  if (gf.dim == 2) return submit<ProlongAddK<T, 2>>(a, nblk(gf.Nv), 0, st);
+  return submit<ProlongAddK<T, 3>>(a, nblk(gf.Nv), 0, st);
 }
 
 // ---- pressure mass M_p(1/eta): cell matrix (prod h / 6^d) eta_K^{-1} Pi x Pi (x Pi) ---------------
@@ -343,10 +365,20 @@ __global__ void k_plap_diag(const Geom g, const T k0, const T k1, const T k2, co
   dinv[q] = T(1) / (T(nact) * per_cell);
 }
 
+template <typename T>
+struct PXferArgs {
+  Geom gf, gc;
+  const uint8_t* mf;
+  const uint8_t* mc;
+  const T* in;
+  T* out;
+};
+
 template <typename T, int DIM>
-__global__ void k_p_restrict(const Geom gf, const Geom gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                             const T* __restrict__ rf, T* __restrict__ rc) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void p_restrict_body(const Geom& gf, const Geom& gc, const uint8_t* __restrict__ mf,
+                                                const uint8_t* __restrict__ mc, const T* __restrict__ rf,
+                                                T* __restrict__ rc, int blk) {
+  const long long q = blk * (long long)blockDim.x + threadIdx.x;
   if (q >= gc.Np) return;
   if (mc[q]) { rc[q] = T(0); return; }
   int I, J, K;
@@ -375,9 +407,10 @@ __global__ void k_p_restrict(const Geom gf, const Geom gc, const uint8_t* __rest
 }
 
 template <typename T, int DIM>
-__global__ void k_p_prolong_add(const Geom gf, const Geom gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                                const T* __restrict__ xc, T* __restrict__ xf) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void p_prolong_add_body(const Geom& gf, const Geom& gc, const uint8_t* __restrict__ mf,
+                                                   const uint8_t* __restrict__ mc, const T* __restrict__ xc,
+                                                   T* __restrict__ xf, int blk) {
+  const long long q = blk * (long long)blockDim.x + threadIdx.x;
   if (q >= gf.Np) return;
   if (mf[q]) return;
   int I, J, K;
@@ -402,17 +435,41 @@ __global__ void k_p_prolong_add(const Geom gf, const Geom gc, const uint8_t* __r
   xf[q] += acc;
 }
 
+template <typename T, int DIM>
+struct PRestrictK {
+  using Args = PXferArgs<T>;
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    p_restrict_body<T, DIM>(a.gf, a.gc, a.mf, a.mc, a.in, a.out, blk);
+  }
+};
+template <typename T, int DIM>
+struct PProlongAddK {
+  using Args = PXferArgs<T>;
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    p_prolong_add_body<T, DIM>(a.gf, a.gc, a.mf, a.mc, a.in, a.out, blk);
+  }
+};
+
 template <typename T>
-__global__ void k_mask_copy(const T* in, const uint8_t* __restrict__ mask, T* out, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = mask[i] ? T(0) : in[i];
-}
+struct MaskCopyK {  // may run in place
+  struct Args { const T* in; const uint8_t* mask; T* out; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)nblk * blockDim.x)
+      a.out[i] = a.mask[i] ? T(0) : a.in[i];
+  }
+};
 template <typename T>
-__global__ void k_cc_combine(const T* __restrict__ m, const T* __restrict__ v, const uint8_t* __restrict__ mask, T alpha,
-                             T* __restrict__ z, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    z[i] = -(m[i] + alpha * (mask[i] ? T(0) : v[i]));
-}
+struct CcCombineK {
+  struct Args { const T* m; const T* v; const uint8_t* mask; T alpha; T* z; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)nblk * blockDim.x)
+      a.z[i] = -(a.m[i] + a.alpha * (a.mask[i] ? T(0) : a.v[i]));
+  }
+};
 
 template <typename T>
 cudaError_t launch_plap(int mode, PLapArgs<T> a, cudaStream_t st) {
@@ -436,30 +493,24 @@ cudaError_t launch_plap_diag(const Geom& g, const T* kc, const uint8_t* cmask, T
 template <typename T>
 cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* rf, T* rc,
                               cudaStream_t st) {
-  if (gf.dim == 2)
-    k_p_restrict<T, 2><<<nblk(gc.Np), TPB, 0, st>>>(gf, gc, mf, mc, rf, rc);
-  else
-    k_p_restrict<T, 3><<<nblk(gc.Np), TPB, 0, st>>>(gf, gc, mf, mc, rf, rc);
-  return launched(cudaGetLastError());
+  const PXferArgs<T> a{gf, gc, mf, mc, rf, rc};
+  if (gf.dim == 2) return submit<PRestrictK<T, 2>>(a, nblk(gc.Np), 0, st);
+  return submit<PRestrictK<T, 3>>(a, nblk(gc.Np), 0, st);
 }
 template <typename T>
 cudaError_t launch_p_prolong_add(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* xc,
                                  T* xf, cudaStream_t st) {
-  if (gf.dim == 2)
-    k_p_prolong_add<T, 2><<<nblk(gf.Np), TPB, 0, st>>>(gf, gc, mf, mc, xc, xf);
-  else
-    k_p_prolong_add<T, 3><<<nblk(gf.Np), TPB, 0, st>>>(gf, gc, mf, mc, xc, xf);
-  return launched(cudaGetLastError());
+  const PXferArgs<T> a{gf, gc, mf, mc, xc, xf};
+  if (gf.dim == 2) return submit<PProlongAddK<T, 2>>(a, nblk(gf.Np), 0, st);
+  return submit<PProlongAddK<T, 3>>(a, nblk(gf.Np), 0, st);
 }
 template <typename T>
 cudaError_t launch_mask_copy(const T* in, const uint8_t* mask, T* out, long long n, cudaStream_t st) {
-  k_mask_copy<T><<<nblk(n), TPB, 0, st>>>(in, mask, out, n);
-  return launched(cudaGetLastError());
+  return submit<MaskCopyK<T>>({in, mask, out, n}, nblk(n), 0, st);
 }
 template <typename T>
 cudaError_t launch_cc_combine(const T* m, const T* v, const uint8_t* mask, T alpha, T* z, long long n, cudaStream_t st) {
-  k_cc_combine<T><<<nblk(n), TPB, 0, st>>>(m, v, mask, alpha, z, n);
-  return launched(cudaGetLastError());
+  return submit<CcCombineK<T>>({m, v, mask, alpha, z, n}, nblk(n), 0, st);
 }
 
 #define INSTP(T)                                                                                          \

@@ -33,7 +33,7 @@ __device__ __forceinline__ void cp_async_q1(T* smem, const T* gmem, bool load) {
 }  // namespace
 
 template <typename T, int DIM, int OP, int MODE>
-__global__ void __launch_bounds__(256) k_q1tile(const Q1Args<T> A) {
+__device__ __forceinline__ void q1tile_body(const Q1Args<T>& A, int bid) {
   using Bx = Q1Box<DIM>;
   constexpr int B0 = Bx::B0, B1 = Bx::B1, B2 = Bx::B2;
   constexpr int X0 = B0 + 2, X1 = B1 + 2, X2 = DIM == 3 ? B2 + 2 : 1;  // staged nodes
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_q1tile(const Q1Args<T> A) {
   __shared__ T sc[C0 * C1 * C2];
   const Geom& g = A.g;
   const int nb0 = (g.npn[0] + B0 - 1) / B0, nb1 = (g.npn[1] + B1 - 1) / B1;
-  int blk = blockIdx.x;
+  int blk = bid;
   const int b0 = blk % nb0;
   blk /= nb0;
   const int b1 = blk % nb1;
@@ -146,15 +146,21 @@ __global__ void __launch_bounds__(256) k_q1tile(const Q1Args<T> A) {
   }
 }
 
+template <typename T, int DIM, int OP, int MODE>
+struct Q1TileK {
+  using Args = Q1Args<T>;
+  static constexpr int THREADS = 256, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) { q1tile_body<T, DIM, OP, MODE>(a, blk); }
+};
+
 template <typename T, int DIM, int OP>
 static cudaError_t q1_dispatch_mode(int mode, const Q1Args<T>& a, cudaStream_t st) {
   using Bx = Q1Box<DIM>;
   const long long nblk = (long long)((a.g.npn[0] + Bx::B0 - 1) / Bx::B0) * ((a.g.npn[1] + Bx::B1 - 1) / Bx::B1) *
                          (DIM == 3 ? (a.g.npn[2] + Bx::B2 - 1) / Bx::B2 : 1);
-  if (mode == TILE_APPLY) k_q1tile<T, DIM, OP, TILE_APPLY><<<(unsigned)nblk, 256, 0, st>>>(a);
-  else if (mode == TILE_RESID) k_q1tile<T, DIM, OP, TILE_RESID><<<(unsigned)nblk, 256, 0, st>>>(a);
-  else k_q1tile<T, DIM, OP, TILE_CHEB><<<(unsigned)nblk, 256, 0, st>>>(a);
-  return launched(cudaGetLastError());
+  if (mode == TILE_APPLY) return submit<Q1TileK<T, DIM, OP, TILE_APPLY>>(a, nblk, 0, st);
+  if (mode == TILE_RESID) return submit<Q1TileK<T, DIM, OP, TILE_RESID>>(a, nblk, 0, st);
+  return submit<Q1TileK<T, DIM, OP, TILE_CHEB>>(a, nblk, 0, st);
 }
 
 template <typename T>

@@ -53,8 +53,7 @@ __device__ __forceinline__ int owned_p_ext(int cs, int TO, int n) {
 }
 
 template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
-__global__ void __launch_bounds__(TileDims<DIM>::THREADS)
-k_tile(const TileArgs<T> A) {
+__device__ __forceinline__ void tile_body(const TileArgs<T>& A, int bid) {
   using S = TileShape<DIM>;
   using D = TileDims<DIM>;
   constexpr int NN = DIM == 2 ? 9 : 27;  // Q2 nodes per cell
@@ -66,7 +65,7 @@ k_tile(const TileArgs<T> A) {
   const Geom& g = A.g;
   const OpCoef<T>& c = A.c;
 
-  int tile = blockIdx.x;
+  int tile = bid;
   const int t0 = tile % A.tiles[0];
   tile /= A.tiles[0];
   const int t1 = tile % A.tiles[1];
@@ -266,6 +265,15 @@ k_tile(const TileArgs<T> A) {
 }
 
 template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
+struct TileK {
+  using Args = TileArgs<T>;
+  static constexpr int THREADS = TileDims<DIM>::THREADS, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    tile_body<T, DIM, MODE, WA, WBT, WB>(a, blk);
+  }
+};
+
+template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
 static cudaError_t launch_one(TileArgs<T> a, cudaStream_t st) {
   using S = TileShape<DIM>;
   using D = TileDims<DIM>;
@@ -273,16 +281,8 @@ static cudaError_t launch_one(TileArgs<T> a, cudaStream_t st) {
   a.tiles[1] = (a.g.n[1] + S::TC1 - 2) / (S::TC1 - 1);
   a.tiles[2] = DIM == 3 ? (a.g.n[2] + S::TC2 - 2) / (S::TC2 - 1) : 1;
   const size_t smem = sizeof(T) * (((WA || WBT) ? DIM * D::VSZ : 0) + (WB ? D::PSZ : 0));
-  auto kern = k_tile<T, DIM, MODE, WA, WBT, WB>;
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   const long long nblocks = (long long)a.tiles[0] * a.tiles[1] * a.tiles[2];
-  kern<<<(unsigned)nblocks, D::THREADS, smem, st>>>(a);
-  return launched(cudaGetLastError());
+  return submit<TileK<T, DIM, MODE, WA, WBT, WB>>(a, nblocks, smem, st);
 }
 
 template <typename T, int DIM, int MODE>

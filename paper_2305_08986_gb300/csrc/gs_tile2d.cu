@@ -98,7 +98,7 @@ __device__ __forceinline__ void gather2(const T* ru, int i0, int i1, T& s0, T& s
 }  // namespace
 
 template <typename T, int MODE, bool WA, bool WBT, bool WB>
-__global__ void __launch_bounds__(NT, 2) k_tile2d(const TileArgs<T> A) {
+__device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
   constexpr bool NEED_U = WA || WB;
   constexpr bool WU = WA || WBT;
   using SM = Smem2<MODE, NEED_U, WBT, WU, WB>;
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(NT, 2) k_tile2d(const TileArgs<T> A) {
   const Geom& g = A.g;
   const OpCoef<T>& c = A.c;
   const bool raw = A.raw != 0;
-  const int t0 = blockIdx.x % A.tiles[0];
-  const int t1 = blockIdx.x / A.tiles[0];
+  const int t0 = bid % A.tiles[0];
+  const int t1 = bid / A.tiles[0];
   const int cs0 = t0 * TO0, cs1 = t1 * TO1;
   const long long Nv = g.Nv;
   const int tid = threadIdx.x;
@@ -348,21 +348,20 @@ __global__ void __launch_bounds__(NT, 2) k_tile2d(const TileArgs<T> A) {
 }
 
 template <typename T, int MODE, bool WA, bool WBT, bool WB>
+struct Tile2dK {
+  using Args = TileArgs<T>;
+  static constexpr int THREADS = NT, MINB = 2;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) { tile2d_body<T, MODE, WA, WBT, WB>(a, blk); }
+};
+
+template <typename T, int MODE, bool WA, bool WBT, bool WB>
 static cudaError_t launch2(TileArgs<T> a, cudaStream_t st) {
   using SM = Smem2<MODE, WA || WB, WBT, WA || WBT, WB>;
   a.tiles[0] = (a.g.n[0] + TO0 - 1) / TO0;
   a.tiles[1] = (a.g.n[1] + TO1 - 1) / TO1;
   a.tiles[2] = 1;
   const size_t smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
-  auto kern = k_tile2d<T, MODE, WA, WBT, WB>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  kern<<<(unsigned)(a.tiles[0] * a.tiles[1]), NT, smem, st>>>(a);
-  return launched(cudaGetLastError());
+  return submit<Tile2dK<T, MODE, WA, WBT, WB>>(a, (long long)a.tiles[0] * a.tiles[1], smem, st);
 }
 
 template <typename T, int MODE>

@@ -21,7 +21,7 @@ if not os.path.exists(LIB_PATH):
                       "(or __graft_entry__.build()); there is no fallback implementation")
 _lib = ctypes.CDLL(LIB_PATH)
 
-GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ENOCONV, GS_EBREAKDOWN, GS_ETIMEOUT = range(7)
+GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ENOCONV, GS_EBREAKDOWN, GS_ETIMEOUT, GS_EBUSY = range(8)
 (OP_A, OP_RESIDUAL_A, OP_DIAG_A, OP_SMOOTH, OP_RESTRICT, OP_PROLONGATE, OP_B, OP_BT,
  OP_SCHUR_MASS, OP_SCHUR_INV, OP_COARSE, OP_PRECOND, OP_A_RAW, OP_PLAP, OP_PLAP_INV, OP_PRESTRICT,
  OP_PPROLONGATE) = range(17)
@@ -93,9 +93,38 @@ _lib.gs_strerror.argtypes = [ctypes.c_int]
 _lib.gs_last_error.restype = ctypes.c_char_p
 _lib.gs_last_error.argtypes = []
 
+
+class GsEngineResult(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_longlong), ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("t_added", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class GsEngineStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("batched_launches", ctypes.c_longlong),
+                ("plan_builds", ctypes.c_longlong), ("plan_kernels", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong)]
+
+
+_lib.gs_engine_create.restype = ctypes.c_int
+_lib.gs_engine_create.argtypes = [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+_lib.gs_engine_add.restype = ctypes.c_int
+_lib.gs_engine_add.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_longlong]
+_lib.gs_engine_step.restype = ctypes.c_int
+_lib.gs_engine_step.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
+_lib.gs_engine_poll.restype = ctypes.c_int
+_lib.gs_engine_poll.argtypes = [_vp, ctypes.POINTER(GsEngineResult), ctypes.c_int]
+_lib.gs_engine_active.restype = ctypes.c_int
+_lib.gs_engine_active.argtypes = [_vp]
+_lib.gs_engine_get_stats.restype = ctypes.c_int
+_lib.gs_engine_get_stats.argtypes = [_vp, ctypes.POINTER(GsEngineStats)]
+_lib.gs_engine_destroy.restype = None
+_lib.gs_engine_destroy.argtypes = [_vp]
+
 EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_vmult", "gs_vmult_A", "gs_vcycle", "gs_solve", "gs_lift_rhs",
             "gs_batch_solve", "gs_apply_level", "gs_get_info", "gs_set_stream", "gs_destroy", "gs_strerror",
-            "gs_last_error", "gs_profile", "gs_profile_read", "gs_coarse_solve_noalloc"]
+            "gs_last_error", "gs_profile", "gs_profile_read", "gs_coarse_solve_noalloc", "gs_engine_create",
+            "gs_engine_add", "gs_engine_step", "gs_engine_poll", "gs_engine_active", "gs_engine_get_stats",
+            "gs_engine_destroy"]
 
 
 class GsError(RuntimeError):
@@ -269,3 +298,78 @@ def batch_solve(solvers, rhs_list, x_list, tol=1e-8):
     rels = (ctypes.c_double * n)()
     s = _lib.gs_batch_solve(ctxs, n, rp, xp, float(tol), its, rels)
     return s, list(its), list(rels)
+
+
+class Engine:
+    """Batching engine (gs_engine_*): many solves advanced together, one FGMRES iteration of each
+    per step, one launch per kernel per step for all of them."""
+
+    def __init__(self, max_slots, max_restart=0, stream=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.stream = st
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(_lib.gs_engine_create(int(max_slots), int(max_restart), ctypes.c_void_p(st.cuda_stream),
+                                         ctypes.byref(h)), "gs_engine_create")
+        self.h = h
+        self.max_slots = int(max_slots)
+        self._held = {}  # tag -> (solver, rhs, x): kept alive while the solve runs
+
+    def add(self, solver, rhs, x, tol=1e-8, tag=0):
+        """Queue a solve; returns False when every slot is taken."""
+        T = self.torch.float64
+        s = _lib.gs_engine_add(self.h, solver.ctx, _ptr(rhs, T, solver.n_total, "rhs"),
+                               _ptr(x, T, solver.n_total, "x"), float(tol), int(tag))
+        if s == GS_EBUSY:
+            return False
+        _check(s, "gs_engine_add")
+        self._held[int(tag)] = (solver, rhs, x)
+        return True
+
+    def step(self):
+        """One iteration of every solve in the engine; returns the number still running."""
+        n = ctypes.c_int()
+        _check(_lib.gs_engine_step(self.h, ctypes.byref(n)), "gs_engine_step")
+        return n.value
+
+    def poll(self, max_results=4096):
+        arr = (GsEngineResult * max_results)()
+        n = _lib.gs_engine_poll(self.h, arr, max_results)
+        out = []
+        for i in range(n):
+            r = arr[i]
+            out.append({"tag": r.tag, "status": r.status, "iterations": r.iterations,
+                        "rel_residual": r.rel_residual, "t_added": r.t_added, "t_done": r.t_done})
+            self._held.pop(int(r.tag), None)
+        return out
+
+    def active(self):
+        return int(_lib.gs_engine_active(self.h))
+
+    def stats(self):
+        st = GsEngineStats()
+        _check(_lib.gs_engine_get_stats(self.h, ctypes.byref(st)), "gs_engine_get_stats")
+        return {k: getattr(st, k) for k, _ in GsEngineStats._fields_}
+
+    def run(self):
+        """Step until every solve has finished; returns the finished solves."""
+        out = []
+        while self.active() > 0:
+            self.step()
+            out.extend(self.poll())
+        out.extend(self.poll())
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.gs_engine_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -52,3 +52,17 @@ def test_footprint_host_logic(lib_path):
     assert gs.footprint_bytes(2, (15, 16), (1.0, 1.0), 2) == 0      # not coarsenable
     assert gs.footprint_bytes(1, (16,), (1.0,), 1) == 0              # unsupported dimension
     assert gs.footprint_bytes(3, (8, 8, 8), (1.0, 1.0, 1.0), 20) == 0
+
+
+def test_engine_argument_checks(lib_path):
+    """Host-side validation of the batching engine entry points (no CUDA call is reached)."""
+    import ctypes
+    from paper_2305_08986_gb300 import gs
+    h = ctypes.c_void_p()
+    assert gs._lib.gs_engine_create(0, 0, None, ctypes.byref(h)) == gs.GS_EINVAL
+    assert gs._lib.gs_engine_create(70000, 0, None, ctypes.byref(h)) == gs.GS_EINVAL
+    assert gs._lib.gs_engine_add(None, None, None, None, 1e-8, 0) == gs.GS_EINVAL
+    assert gs._lib.gs_engine_step(None, None) == gs.GS_EINVAL
+    assert gs._lib.gs_engine_poll(None, None, 4) == 0
+    assert gs._lib.gs_engine_active(None) == 0
+    assert gs._lib.gs_strerror(gs.GS_EBUSY) == b"busy (no free slot)"
