@@ -363,6 +363,148 @@ def run_gpu(args, rank, world):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------------------------------------------
+# batched workload: many uneven instances through the batching engine vs one after the other
+# --------------------------------------------------------------------------------------------
+def run_batched(args):
+    import torch
+    from paper_2305_08986_gb300 import build as gsbuild
+    gsbuild.build(verbose=False)
+    from paper_2305_08986_gb300 import gs, inputs
+    dev = torch.device("cuda", 0)
+    probs = inputs.batch_instances(args.instances, seed=0)
+    t0 = time.perf_counter()
+    solvers, rhs, xs = [], [], []
+    for p in probs:
+        s = gs.Solver.from_problem(p, device=dev)
+        f = torch.tensor(p.f, device=dev)
+        g = torch.tensor(p.g, device=dev)
+        b = torch.empty_like(f)
+        s.lift_rhs(f, g, b)
+        solvers.append(s)
+        rhs.append(b)
+        xs.append(torch.zeros_like(b))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    unknowns = sum(s.n_total for s in solvers)
+    st = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        out = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def engine_run():
+        return gs.batch_solve(solvers, rhs, xs, tol=TOL)
+
+    def sequential_run():
+        its = []
+        for s, b, x in zip(solvers, rhs, xs):
+            it, rr, _ = s.solve(b, x, tol=TOL)
+            its.append(it)
+        return its
+
+    for _ in range(max(1, args.warmup)):
+        timed(engine_run)
+    eng_ms = []
+    for _ in range(args.steps):
+        ms, (status, its, rels) = timed(engine_run)
+        eng_ms.append(ms)
+    failed = [i for i, r in enumerate(rels) if not r <= TOL]
+    x_eng = [x.clone() for x in xs]
+    timed(sequential_run)
+    seq_ms = []
+    for _ in range(max(1, min(args.steps, 2))):
+        ms, its_seq = timed(sequential_run)
+        seq_ms.append(ms)
+    diff = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(x_eng, xs))
+    eng = gs.Engine(len(solvers))
+    for i, (s, b, x) in enumerate(zip(solvers, rhs, xs)):
+        x.zero_()
+        eng.add(s, b, x, TOL, tag=i)
+    eng.run()
+    stats = eng.stats()
+    eng.close()
+    n2 = sum(1 for p in probs if p.dim == 2)
+    line = {"workload": f"batched: {len(probs)} instances ({n2} 2D in 16^2..256^2, {len(probs) - n2} 3D in 8^3..32^3), "
+                        "box inclusion contrast U(1e2,1e6), alpha U(1,1e3), FP32 MG / FP64 FGMRES(50), rel-res 1e-8",
+            "metric": "solve throughput", "unit": "GDoF/s", "unknowns": unknowns,
+            "value": unknowns / (statistics.median(eng_ms) * 1e-3) / 1e9,
+            "engine_ms": {"p50": statistics.median(eng_ms), "max": max(eng_ms)},
+            "sequential_ms": statistics.median(seq_ms),
+            "speedup_vs_sequential": statistics.median(seq_ms) / statistics.median(eng_ms),
+            "iterations": {"mean": statistics.fmean(its), "max": max(its)},
+            "not_converged": [{"i": i, "dim": probs[i].dim, "n": probs[i].n[0], "levels": probs[i].levels,
+                               "alpha": probs[i].alpha, "its": its[i], "rel": rels[i]} for i in failed],
+            "solution_rel_diff_engine_vs_sequential": diff,
+            "setup_s": t_setup, "engine_stats": stats, "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------
+# serving: Poisson arrivals through the continuous-batching server vs sequential plain FP64
+# --------------------------------------------------------------------------------------------
+def run_serving(args):
+    import numpy as np
+    import torch
+    from paper_2305_08986_gb300 import build as gsbuild
+    gsbuild.build(verbose=False)
+    from paper_2305_08986_gb300 import gs, inputs, serving
+    dev = torch.device("cuda", 0)
+    rates = [float(r) for r in args.rates.split(",")]
+    base = inputs.serving_stream(1.0, args.requests, seed=1)
+    problems = [p for _, p in base]
+    # sequential plain FP64 baseline: service time of each request alone (setup + solve + copy back)
+    svc = []
+    for i, p in enumerate(problems):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = gs.Solver.from_problem(p, device=dev, mg_precision=64)
+        f = torch.tensor(p.f, device=dev)
+        g = torch.tensor(p.g, device=dev)
+        b = torch.empty_like(f)
+        s.lift_rhs(f, g, b)
+        x = torch.zeros_like(b)
+        s.solve(b, x, tol=TOL)
+        x.cpu()
+        s.close()
+        svc.append(time.perf_counter() - t0)
+    out = {"workload": f"serving: {args.requests} requests per rate, 3D 8^3..48^3 and 2D 32^2..512^2 log-uniform, "
+                       "random-inclusion contrast up to 1e6, rel-res 1e-8, HBM cap "
+                       f"{args.hbm_cap_gb:g} GB, continuous batching (FP32 MG / FP64 FGMRES)",
+           "unknowns_total": int(sum(len(p.f) for p in problems)), "rates": {}}
+    for rate in rates:
+        rng = np.random.default_rng(int(rate * 1000) + 7)
+        offs = np.cumsum(rng.exponential(1.0 / rate, size=len(problems)))
+        stream = [(float(o), serving.Request(i, p, tol=TOL)) for i, (o, p) in enumerate(zip(offs, problems))]
+        srv = serving.StokesServer(hbm_cap_bytes=args.hbm_cap_gb * 1e9, max_slots=256, setup_workers=4)
+        t0 = serving.run_stream(srv, stream)
+        summ = serving.summarize(srv.results, t0)
+        summ["peak_running"] = srv.peak_running
+        summ["peak_admitted_gb"] = srv.peak_used / 1e9
+        summ["engine_steps"] = srv.engine.stats()["steps"]
+        srv.close()
+        # same arrivals through one FIFO server with the measured FP64 service times
+        tfree, lat = 0.0, []
+        for o, d in zip(offs, svc):
+            start = max(o, tfree)
+            tfree = start + d
+            lat.append(tfree - o)
+        lat.sort()
+        q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
+        summ["sequential_fp64"] = {"p50_ms": 1e3 * q(0.5), "p99_ms": 1e3 * q(0.99),
+                                   "solves_per_s": len(lat) / (tfree - offs[0] + svc[0])}
+        out["rates"][f"{rate:g}"] = summ
+        print(json.dumps({"rate": rate, **summ}), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,9 +515,19 @@ def main():
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.01)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="channel", choices=["channel", "batched", "serving"],
+                    help="channel: the contract line; batched / serving: the engine workloads (extra lines)")
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--rates", default="10,30,100,300,1000")
+    ap.add_argument("--hbm-cap-gb", type=float, default=150.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "batched" and args.impl == "gs":
+        return run_batched(args)
+    if args.workload == "serving" and args.impl == "gs":
+        return run_serving(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -127,6 +127,7 @@ cudaError_t run(const std::vector<Launch>& ls, const char* dbase, const int* act
 
 struct Slot {
   gs_ctx* c = nullptr;
+  long long uid = 0;  // unique per gs_engine_add: a context address may be reused after gs_destroy
   long long tag = 0;
   double t_added = 0.0;
 };
@@ -144,7 +145,11 @@ struct gs_engine {
   size_t off_y = 0, off_active = 0, fixed_bytes = 0;
   Staged step;  // per-step argument tables and work lists
   // plan: merged preconditioner bodies of its members, captured as a graph
-  std::vector<gs_ctx*> plan_ctx;  // per slot: the context whose body is in the plan (or NULL)
+  // per slot: uid of the solve whose body is in the plan (0: none).  Membership is keyed by uid,
+  // not by context address, so a new context allocated where a destroyed one lived never runs
+  // the old one's recorded launches.
+  std::vector<long long> plan_uid;
+  long long next_uid = 1;
   int plan_members = 0;
   Staged plan_tabs;
   cudaGraphExec_t plan_exec = nullptr;
@@ -175,7 +180,7 @@ int* active_host(gs_engine* e) { return reinterpret_cast<int*>(e->fixed.h + e->o
 void drop_plan(gs_engine* e) {
   if (e->plan_exec) cudaGraphExecDestroy(e->plan_exec);
   e->plan_exec = nullptr;
-  std::fill(e->plan_ctx.begin(), e->plan_ctx.end(), nullptr);
+  std::fill(e->plan_uid.begin(), e->plan_uid.end(), 0);
   e->plan_members = 0;
   e->plan_kernels = 0;
 }
@@ -194,7 +199,7 @@ gs_status build_plan(gs_engine* e) {
     if (!r) return st;
     recs.push_back(r);
     slot_of.push_back(s);
-    e->plan_ctx[s] = c;
+    e->plan_uid[s] = e->slots[s].uid;
   }
   e->plan_members = (int)recs.size();
   if (recs.empty()) return GS_OK;
@@ -234,9 +239,10 @@ gs_status engine_step(gs_engine* e, int* n_active) {
   int stale = 0, occupied = 0;
   for (int s = 0; s < e->max_slots; ++s) {
     gs_ctx* c = e->slots[s].c;
+    const bool member = c && e->plan_uid[s] == e->slots[s].uid;
     if (c) occupied++;
-    if (e->plan_ctx[s] && e->plan_ctx[s] != c) stale++;
-    if (c && e->plan_ctx[s] != c && slot_wants_body(c)) rebuild = true;
+    if (e->plan_uid[s] != 0 && !member) stale++;
+    if (c && !member && slot_wants_body(c)) rebuild = true;
   }
   if (e->plan_members > 0 && 2 * stale > e->plan_members) rebuild = true;
   if (rebuild) {
@@ -254,7 +260,7 @@ gs_status engine_step(gs_engine* e, int* n_active) {
     *act = 0;
     if (!c) continue;
     const bool body = slot_wants_body(c);
-    if (body && e->plan_ctx[s] == c) *act = 1;
+    if (body && e->plan_uid[s] == e->slots[s].uid) *act = 1;
     any_body |= *act;
     Recorder& rp = e->rpre[s];
     Recorder& rq = e->rpost[s];
@@ -336,7 +342,7 @@ gs_status gs_engine_create(int max_slots, int max_restart, void* stream, gs_engi
   e->gstride = (size_t)((slot_gather_max(max_restart) + 3) & ~3);
   e->ystride = (size_t)((max_restart + 3) & ~3);
   e->slots.assign(max_slots, Slot());
-  e->plan_ctx.assign(max_slots, nullptr);
+  e->plan_uid.assign(max_slots, 0);
   e->rpre.resize(max_slots);
   e->rpost.resize(max_slots);
   e->off_y = sizeof(double) * e->gstride * max_slots;
@@ -369,6 +375,7 @@ gs_status gs_engine_add(gs_engine* e, gs_ctx* c, const double* rhs, double* x, d
   // the engine's stream does not wait on the context's stream: finish what is queued there
   ECK(cudaStreamSynchronize(slot_stream(c)));
   e->slots[free_slot].c = c;
+  e->slots[free_slot].uid = e->next_uid++;
   e->slots[free_slot].tag = tag;
   e->slots[free_slot].t_added = now_s();
   return GS_OK;

@@ -218,13 +218,24 @@ def config_spheres(n: int = 64, levels: int = 5, n_spheres: int = 64, eta_in: fl
 
 def config_box_inclusion(dim: int, n: Sequence[int], levels: int, contrast: float, alpha: float,
                          seed: int, length: Optional[Sequence[float]] = None,
-                         faces: Optional[int] = None) -> Problem:
-    """Random axis-aligned box inclusion with eta = contrast inside, 1 outside; random N(0,1) load."""
+                         faces: Optional[int] = None, align_coarse: bool = False) -> Problem:
+    """Random axis-aligned box inclusion with eta = contrast inside, 1 outside; random N(0,1) load.
+
+    align_coarse: snap the box to cell boundaries of the coarsest level (n / 2^(levels-1) cells per
+    axis), so that every level resolves the interface, as the coarse meshes of the paper's FSI
+    benchmarks do (Sec. 4: the coarsest mesh is aligned with the solid-fluid interface)."""
     nn = tuple(int(k) for k in n)
     L = tuple(length) if length is not None else (1.0,) * dim
     rng = np.random.default_rng(seed)
     corner = rng.uniform(0.0, 0.6, size=dim) * np.array(L)
     side = rng.uniform(0.1, 0.4, size=dim) * np.array(L)
+    if align_coarse:
+        for a in range(dim):
+            nc = nn[a] >> (levels - 1)
+            h0 = L[a] / nc
+            i0 = min(int(corner[a] / h0), nc - 1)
+            i1 = min(max(i0 + 1, int(round((corner[a] + side[a]) / h0))), nc)
+            corner[a], side[a] = i0 * h0, (i1 - i0) * h0
     c = cell_centroids(dim, nn, L)
     inside = np.all((c >= corner) & (c <= np.minimum(corner + side, L)), axis=1)
     eta = np.where(inside, contrast, 1.0)
@@ -259,7 +270,8 @@ def config_random_field(dim: int, n: Sequence[int], levels: int = 1, seed: int =
 
 def batch_instances(count: int = 256, seed: int = 0, max2d: int = 256, max3d: int = 32) -> List[Problem]:
     """Batched workload: sizes drawn from 2D {16..256}^2 and 3D {8..32}^3 (coarsest level at most
-    7 cells (2D) or 4 cells (3D) per axis), contrast U(1e2, 1e6) in a random box, alpha U(1, 1e3)."""
+    7 cells (2D) or 4 cells (3D) per axis), contrast U(1e2, 1e6) in a random box aligned with the
+    coarsest mesh, alpha U(1, 1e3)."""
     sizes2 = [s for s in (16, 24, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 192, 224, 256) if s <= max2d]
     sizes3 = [s for s in (8, 12, 16, 24, 32) if s <= max3d]
     rng = np.random.default_rng(seed)
@@ -270,7 +282,7 @@ def batch_instances(count: int = 256, seed: int = 0, max2d: int = 256, max3d: in
         contrast = float(rng.uniform(1e2, 1e6))
         alpha = float(rng.uniform(1.0, 1e3))
         out.append(config_box_inclusion(dim, (s,) * dim, levels_for(s, dim), contrast, alpha,
-                                        seed=int(rng.integers(1 << 31))))
+                                        seed=int(rng.integers(1 << 31)), align_coarse=True))
     return out
 
 
@@ -300,7 +312,7 @@ def serving_stream(rate: float, count: int, seed: int = 0, n2=(32, 512), n3=(8, 
         contrast = float(math.exp(rng.uniform(0.0, math.log(1e6))))
         alpha = float(rng.uniform(1.0, 1e3))
         p = config_box_inclusion(dim, (s,) * dim, levels_for(s, dim), contrast, alpha,
-                                 seed=int(rng.integers(1 << 31)))
+                                 seed=int(rng.integers(1 << 31)), align_coarse=True)
         reqs.append((t, p))
     return reqs
 

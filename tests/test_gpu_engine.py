@@ -185,3 +185,26 @@ def test_batch_solve_matches_engine_and_oracle():
     xg = normalize_pressure(m, o.sys, setups[0][2].cpu().numpy())
     xo = normalize_pressure(m, o.sys, xo)
     assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+def test_engine_recycled_contexts():
+    """Short solves come and go through one slot while a long one keeps the plan alive; a new
+    context may live at a destroyed one's address and must never run the old one's launches."""
+    from paper_2305_08986_gb300 import gs
+    probs = _problems()
+    long_p, short_p = probs[1], probs[0]
+    ref_short = _engine_alone(short_p)
+    sl, bl, xl = _setup(long_p)
+    eng = gs.Engine(2)
+    assert eng.add(sl, bl, xl, 1e-13, tag=100)  # runs past the short ones (stops at max_iter or 1e-13)
+    for k in range(4):
+        s, b, x = _setup(short_p)
+        assert eng.add(s, b, x, TOL, tag=k)
+        res = []
+        while not res:
+            eng.step()
+            res = [r for r in eng.poll() if r["tag"] == k]
+        _same(ref_short, x, res[0]["iterations"], res[0]["rel_residual"], res[0]["status"])
+        s.close()
+        del s, b, x
+    eng.run()
