@@ -163,6 +163,12 @@ def run_reference(args, rank, world):
 # --------------------------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------------------------
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernels
+# at the 1280 x 224 workload, from one ncu --set full capture of the kernel as built now (cold,
+# standalone launch): the fused FP32 Chebyshev step and the FP64 saddle operator.
+NCU_TRAFFIC_BYTES = {"cheb_step": 39.430656e6 + 5.12e3, "saddle_fp64": 24.775168e6 + 256.0}
+
+
 def algorithmic_cost(kind, dim, n_cells, n_u, n_p, elem_bytes):
     """Algorithmic bytes / flops per launch of the dominant kernel classes."""
     if kind == "saddle_fp64":
@@ -256,14 +262,15 @@ def run_gpu(args, rank, world):
             peak = args.fp64_peak_tflops
             ach = cost["flops"] / avg_s / 1e12
             roof = {"bound": "alu", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom[1][0],
-                    "peak_source": "FP64 FMA microbenchmark on this GB300 (profiles/fp64_fp32_alu_peaks.md)"}
+                    "frac": ach / peak, "traffic": NCU_TRAFFIC_BYTES.get(dom[0]), "avg_launch_us": avg_s * 1e6,
+                    "launches": dom[1][0],
+                    "peak_source": "FP64 FMA microbenchmark on this GB300 (profiles/alu_peaks_gb300.md)"}
         elif cost is not None:
             ach = cost["bytes"] / avg_s / 1e9
             peak = peaks.get("hbm_gbs", 6800.0)
             roof = {"bound": "hbm", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": None, "avg_launch_us": avg_s * 1e6, "launches": dom[1][0],
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+                    "frac": ach / peak, "traffic": NCU_TRAFFIC_BYTES.get(dom[0]), "avg_launch_us": avg_s * 1e6,
+                    "launches": dom[1][0], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
 
     # ---- A x throughput (FP64 / FP32), L2 flushed between launches ----
     def time_apply(dtype, reps=30):
