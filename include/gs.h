@@ -112,6 +112,11 @@ typedef struct {            /* zero-initialised = defaults */
   int krylov_fp64;          /* 0: FGMRES basis V stored as double-float pairs (hi + lo, 48-bit),
                                   Gram-Schmidt products on the FP32 pipes (default);
                                1: basis and Gram-Schmidt in IEEE FP64 */
+  int tile_autotune;        /* 2D meshes: 0 -> at gs_create, time each compiled tile height of the
+                                  cell kernel (32 x 16, 32 x 17, 32 x 8 evaluated cells) on every
+                                  level and keep the fastest (default); 1 / 2 / 3 -> always
+                                  32 x 16 / 32 x 17 / 32 x 8 (the FP64 saddle operator uses 32 x 16
+                                  with 3).  The results do not depend on the choice. */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */
@@ -205,6 +210,8 @@ typedef struct {
   int schur_cc;            /* 1 if the Cahouet-Chabard term is active */
   int pressure_coarse_free;/* unknowns of the dense coarse pressure-Laplacian solve */
   double plambda_max[16];  /* Chebyshev upper bound of the pressure Laplacian per level */
+  int tile_rows[16];       /* 2D: evaluated cell rows per tile chosen for each level's multigrid kernels */
+  int saddle_tile_rows;    /* 2D: the same for the FP64 saddle operator (0 in 3D) */
 } gs_info;
 gs_status gs_get_info(const gs_ctx* ctx, gs_info* out);
 

@@ -79,6 +79,7 @@ struct Level {
   void *pxA = nullptr, *pxB = nullptr, *pb = nullptr, *pd = nullptr, *pdinv = nullptr;
   double plam_hi = 0.0;
   double pkc[3] = {0, 0, 0};
+  int shape = 0;  // 2D tile height variant of this level's multigrid kernels (TileArgs::shape)
 };
 
 // State of the resumable FGMRES that the batching engine drives (see gs_slot.h).
@@ -132,6 +133,7 @@ struct gs_ctx {
   // Krylov (FP64)
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
   double* vcur = nullptr;  // current basis vector as double (input of the preconditioner)
+  int saddle_shape = 0;    // 2D tile height variant of the FP64 saddle operator
   double* part = nullptr;
   int G = 1;   // blocks of the multi-dot partial sums
   int GA = 1;  // blocks of the fused axpy + norm (G * (m + 2) >= GA partial sums)
@@ -204,6 +206,7 @@ gs_options normalize_opts(const gs_options* o) {
   r.graphs = r.graphs == 1 ? 1 : 0;
   r.plap_degree = opt_or(r.plap_degree, 2);
   r.krylov_fp64 = r.krylov_fp64 == 1 ? 1 : 0;
+  r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 3) ? r.tile_autotune : 0;
   return r;
 }
 
@@ -534,6 +537,7 @@ TileArgs<T> tile_args(const Level& lv) {
   a.g = lv.g;
   a.c = coef<T>(lv);
   a.eta = etap<T>(lv);
+  a.shape = lv.shape;
   return a;
 }
 
@@ -794,6 +798,67 @@ void assemble_coarse_plap(gs_ctx* c, std::vector<double>& A) {
     for (size_t q = 0; q < A.size(); ++q) A[q] += 1.0 / nf;
 }
 
+// FP64 saddle operator on the finest level: y = K x (APPLY) or y = b - K x (RESID)
+gs_status saddle(gs_ctx* c, int mode, const double* x, double* y, const double* b, int raw = 0);
+
+// ---- tile-height autotuner (2D): a launch-shape choice, the results do not depend on it -------------
+// Time `reps` launches of one kernel configuration (after one warm-up launch); microseconds each.
+template <typename F>
+gs_status time_launches(gs_ctx* c, F&& launch, int reps, double* us) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(e);
+  *us = 1e3 * ms / reps;
+  return GS_OK;
+}
+
+// Per level, time the fused Chebyshev step with each compiled tile height on the level's own
+// (scratch) vectors and keep the fastest; then the same for the FP64 saddle operator on the
+// finest level.  A height must beat the current choice by 2 % to replace it.
+template <typename T>
+gs_status autotune(gs_ctx* c) {
+  for (int l = 0; l < c->L; ++l) {
+    Level& lv = c->lv[l];
+    CK(cudaMemsetAsync(lv.xA, 0, sizeof(T) * lv.nu, c->st));
+    CK(cudaMemsetAsync(lv.b, 0, sizeof(T) * lv.nu, c->st));
+    CK(cudaMemsetAsync(lv.d, 0, sizeof(T) * lv.nu, c->st));
+    double best_us = 0.0;
+    int best = 0;
+    for (int s = 0; s < kTileShapes2D; ++s) {
+      TileArgs<T> a = tile_args<T>(lv);
+      a.shape = s;
+      a.xu = (const T*)lv.xA; a.bu = (const T*)lv.b; a.d = (T*)lv.d; a.dinv = (const T*)lv.dinv;
+      a.xout = (T*)lv.xB; a.c1 = (T)0.5; a.c2 = (T)1; a.use_d = 1;
+      double us;
+      CKS(time_launches(c, [&]() { return launch_tile<T>(2, TILE_CHEB, OPS_A, a, c->st); }, 4, &us));
+      if (s == 0 || us < 0.98 * best_us) { best_us = us; best = s; }
+    }
+    lv.shape = best;
+  }
+  CK(cudaMemsetAsync(c->r, 0, sizeof(double) * c->N, c->st));
+  double best_us = 0.0;
+  int best = 0;
+  for (int s = 0; s < 2; ++s) {  // heights compiled for the full saddle operator
+    c->saddle_shape = s;
+    double us;
+    CKS(time_launches(c, [&]() -> cudaError_t {
+      return saddle(c, TILE_APPLY, c->r, c->w, nullptr) == GS_OK ? cudaSuccess : cudaErrorUnknown; }, 3, &us));
+    if (s == 0 || us < 0.98 * best_us) { best_us = us; best = s; }
+  }
+  c->saddle_shape = best;
+  return GS_OK;
+}
+
 gs_status setup(gs_ctx* c) {
   // upload per-level data
   for (int l = 0; l < c->L; ++l) {
@@ -840,6 +905,12 @@ gs_status setup(gs_ctx* c) {
   }
   if (c->fp32) CKS(setup_T<float>(c)); else CKS(setup_T<double>(c));
   CK(cudaStreamSynchronize(c->st));
+  if (c->dim == 2 && c->opt.tile_autotune == 0) {
+    CKS(c->fp32 ? autotune<float>(c) : autotune<double>(c));
+  } else if (c->dim == 2) {
+    for (int l = 0; l < c->L; ++l) c->lv[l].shape = c->opt.tile_autotune - 1;
+    c->saddle_shape = c->opt.tile_autotune == 2 ? 1 : 0;
+  }
   return GS_OK;
 }
 
@@ -1081,9 +1152,10 @@ gs_status precond(gs_ctx* c, const double* v, double* z) {
 }
 
 // FP64 saddle operator on the finest level: y = K x (APPLY) or y = b - K x (RESID)
-gs_status saddle(gs_ctx* c, int mode, const double* x, double* y, const double* b, int raw = 0) {
+gs_status saddle(gs_ctx* c, int mode, const double* x, double* y, const double* b, int raw) {
   const Level& F = c->lv[c->L - 1];
   TileArgs<double> a = tile_args<double>(F);
+  a.shape = c->saddle_shape;
   a.xu = x; a.xp = x + c->nu; a.yu = y; a.yp = y + c->nu;
   a.bu = b; a.bp = b ? b + c->nu : nullptr; a.raw = raw;
   KL(K_SADDLE64, launch_tile<double>(c->dim, mode, OPS_A | OPS_BT | OPS_B, a, c->st));
@@ -1826,6 +1898,9 @@ gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
   out->schur_cc = c->cc ? 1 : 0;
   out->pressure_coarse_free = c->nfp;
   for (int l = 0; l < c->L && l < 16; ++l) out->plambda_max[l] = c->lv[l].plam_hi;
+  static const int rows[kTileShapes2D] = {16, 17, 8};
+  for (int l = 0; l < c->L && l < 16; ++l) out->tile_rows[l] = c->dim == 2 ? rows[c->lv[l].shape] : 0;
+  out->saddle_tile_rows = c->dim == 2 ? rows[c->saddle_shape] : 0;
   return GS_OK;
 }
 

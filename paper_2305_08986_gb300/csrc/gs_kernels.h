@@ -33,7 +33,9 @@ struct TileArgs {
   int use_d;
   int raw;        // 1: no constraint elimination (operator of the unconstrained forms)
   int tiles[3];
+  int shape;      // 2D tile height variant (0: 16, 1: 17, 2: 8 rows of evaluated cells)
 };
+constexpr int kTileShapes2D = 3;
 
 // Which blocks of the saddle operator a launch computes.
 enum TileOps { OPS_A = 1, OPS_BT = 2, OPS_B = 4 };

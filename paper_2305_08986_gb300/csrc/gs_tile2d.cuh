@@ -16,29 +16,50 @@
 // Threads form a 32 x 8 grid.  In phases 1 and 3 thread (tx, ty) handles node columns 2 tx and
 // 2 tx + 1 and node rows ty + 8 r, so the parity of its nodes is fixed (no per-node index
 // arithmetic, uniform branches within a warp) and it consumes the epilogue operands it staged.
+#pragma once
 #include "gs_cell.cuh"
 #include "gs_kernels.h"
 
 namespace gs {
 
-namespace {
-constexpr int E0 = 32, E1 = 16;                    // evaluated cells per tile
-constexpr int TO0 = E0 - 1, TO1 = E1 - 1;          // owned cells per tile
-constexpr int NCELL = E0 * E1;                     // 512
-constexpr int NT = 256;                            // threads per CTA: 32 x 8
-constexpr int TY = NT / 32;                        // 8
-constexpr int IN0 = 2 * E0 + 1, IN1 = 2 * E1 + 1;  // velocity input node tile (65 x 33)
-constexpr int NIN = IN0 * IN1;
-constexpr int PI0 = E0 + 1, PI1 = E1 + 1;          // pressure input node tile (33 x 17)
-constexpr int VP0 = 2 * TO0 + 1, VP1 = 2 * TO1 + 1;  // owned velocity node region (63 x 31)
-constexpr int OWN = VP0 * VP1;
-constexpr int PP0 = TO0 + 1, PP1 = TO1 + 1;          // owned pressure node region (32 x 16)
-constexpr int POWN = PP0 * PP1;
-constexpr int ROWS = (VP1 + TY - 1) / TY;            // owned node rows per thread (4)
-constexpr int IROWS = (IN1 + TY - 1) / TY;           // input tile rows per thread (5)
+namespace tile2d {
+constexpr int NT = 256;      // threads per CTA: 32 x 8
+constexpr int TY = NT / 32;  // 8
 
-template <int MODE, bool NEED_U, bool WBT, bool WU, bool WB>
+// Tile shape: 32 x EY evaluated cells (EY = 16 by default; the per-level autotuner may pick
+// another compiled height, see launch_tile2d).
+template <int EY>
+struct Shape2 {
+  static constexpr int E0 = 32, E1 = EY;                  // evaluated cells per tile
+  static constexpr int TO0 = E0 - 1, TO1 = E1 - 1;        // owned cells per tile
+  static constexpr int NCELL = E0 * E1;
+  static constexpr int IN0 = 2 * E0 + 1, IN1 = 2 * E1 + 1;  // velocity input node tile
+  static constexpr int NIN = IN0 * IN1;
+  static constexpr int PI0 = E0 + 1, PI1 = E1 + 1;        // pressure input node tile
+  static constexpr int VP0 = 2 * TO0 + 1, VP1 = 2 * TO1 + 1;  // owned velocity node region
+  static constexpr int OWN = VP0 * VP1;
+  static constexpr int PP0 = TO0 + 1, PP1 = TO1 + 1;      // owned pressure node region
+  static constexpr int POWN = PP0 * PP1;
+  static constexpr int ROWS = (VP1 + TY - 1) / TY;        // owned node rows per thread
+  static constexpr int IROWS = (IN1 + TY - 1) / TY;       // input tile rows per thread
+  static constexpr int CROWS = (E1 + TY - 1) / TY;        // evaluated cell rows per thread
+};
+
+#define GS_SHAPE2_NAMES(EY)                                                                    \
+  using S2__ = Shape2<EY>;                                                                     \
+  constexpr int E0 = S2__::E0, E1 = S2__::E1, TO0 = S2__::TO0, TO1 = S2__::TO1;               \
+  constexpr int NCELL = S2__::NCELL, IN0 = S2__::IN0, IN1 = S2__::IN1, NIN = S2__::NIN;        \
+  constexpr int PI0 = S2__::PI0, PI1 = S2__::PI1, VP0 = S2__::VP0, VP1 = S2__::VP1;           \
+  constexpr int OWN = S2__::OWN, PP0 = S2__::PP0, PP1 = S2__::PP1, POWN = S2__::POWN;         \
+  constexpr int ROWS = S2__::ROWS, IROWS = S2__::IROWS, CROWS = S2__::CROWS;                  \
+  (void)E0; (void)E1; (void)TO0; (void)TO1; (void)NCELL; (void)IN0; (void)IN1; (void)NIN;      \
+  (void)PI0; (void)PI1; (void)VP0; (void)VP1; (void)OWN; (void)PP0; (void)PP1; (void)POWN;    \
+  (void)ROWS; (void)IROWS; (void)CROWS
+
+template <int EY, int MODE, bool NEED_U, bool WBT, bool WU, bool WB>
 struct Smem2 {
+  static constexpr int NIN = Shape2<EY>::NIN, PI0 = Shape2<EY>::PI0, PI1 = Shape2<EY>::PI1;
+  static constexpr int NCELL = Shape2<EY>::NCELL, OWN = Shape2<EY>::OWN, POWN = Shape2<EY>::POWN;
   static constexpr int SX = NEED_U ? 2 * NIN : 0;
   static constexpr int SP = WBT ? PI0 * PI1 : 0;
   static constexpr int RU = WU ? 18 * NCELL : 0;
@@ -72,8 +93,9 @@ __device__ __forceinline__ int owned_ext(int cs, int TO, int n, int mult) {
 // Sum of the cell results touching owned node (i0, i1), with the node's local positions fixed by
 // its parities (even: local 0 in the next cell and local 2 in the previous one; odd: local 1).
 // Evaluated cell index = cell + 1 - cs; indices beyond the evaluated range lie outside the mesh.
-template <typename T, bool XODD, bool YODD>
+template <typename T, int EY, bool XODD, bool YODD>
 __device__ __forceinline__ void gather2(const T* ru, int i0, int i1, T& s0, T& s1) {
+  GS_SHAPE2_NAMES(EY);
   s0 = T(0);
   s1 = T(0);
   const int ey0 = YODD ? (i1 + 1) >> 1 : (i1 >> 1) + 1;
@@ -95,13 +117,12 @@ __device__ __forceinline__ void gather2(const T* ru, int i0, int i1, T& s0, T& s
     }
   }
 }
-}  // namespace
-
-template <typename T, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB>
 __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
+  GS_SHAPE2_NAMES(EY);
   constexpr bool NEED_U = WA || WB;
   constexpr bool WU = WA || WBT;
-  using SM = Smem2<MODE, NEED_U, WBT, WU, WB>;
+  using SM = Smem2<EY, MODE, NEED_U, WBT, WU, WB>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sx = reinterpret_cast<T*>(smem_raw);
   T* sp = sx + SM::SX;
@@ -222,8 +243,9 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
 
   // ---- phase 2: evaluate cells; thread (tx, ty) -> cells (tx, ty) and (tx, ty + 8) ----
 #pragma unroll 1
-  for (int k = 0; k < NCELL / NT; ++k) {
+  for (int k = 0; k < CROWS; ++k) {
     const int e0 = tx, e1 = ty + TY * k;
+    if (e1 >= E1) continue;
     const int e = e0 + E0 * e1;
     const int c0 = cs0 - 1 + e0, c1 = cs1 - 1 + e1;
     bool active = c0 >= 0 && c0 < g.n[0] && c1 >= 0 && c1 < g.n[1];
@@ -291,11 +313,11 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
         if (i0 >= ve0) continue;
         T s0, s1;
         if (ty & 1) {
-          if (q) gather2<T, true, true>(ru, i0, i1, s0, s1);
-          else gather2<T, false, true>(ru, i0, i1, s0, s1);
+          if (q) gather2<T, EY, true, true>(ru, i0, i1, s0, s1);
+          else gather2<T, EY, false, true>(ru, i0, i1, s0, s1);
         } else {
-          if (q) gather2<T, true, false>(ru, i0, i1, s0, s1);
-          else gather2<T, false, false>(ru, i0, i1, s0, s1);
+          if (q) gather2<T, EY, true, false>(ru, i0, i1, s0, s1);
+          else gather2<T, EY, false, false>(ru, i0, i1, s0, s1);
         }
         const long long node = (2 * cs0 + i0) + (long long)g.nv[0] * (2 * cs1 + i1);
         const int sidx = (i0 + 2) + IN0 * (i1 + 2);  // the node in the staged input tile
@@ -347,43 +369,60 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
   }
 }
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB>
 struct Tile2dK {
   using Args = TileArgs<T>;
   static constexpr int THREADS = NT, MINB = 2;
-  static __device__ __forceinline__ void body(const Args& a, int blk, int) { tile2d_body<T, MODE, WA, WBT, WB>(a, blk); }
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) {
+    tile2d_body<T, EY, MODE, WA, WBT, WB>(a, blk);
+  }
 };
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB>
-static cudaError_t launch2(TileArgs<T> a, cudaStream_t st) {
-  using SM = Smem2<MODE, WA || WB, WBT, WA || WBT, WB>;
-  a.tiles[0] = (a.g.n[0] + TO0 - 1) / TO0;
-  a.tiles[1] = (a.g.n[1] + TO1 - 1) / TO1;
+template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB>
+cudaError_t launch2(TileArgs<T> a, cudaStream_t st) {
+  using S2 = Shape2<EY>;
+  using SM = Smem2<EY, MODE, WA || WB, WBT, WA || WBT, WB>;
+  a.tiles[0] = (a.g.n[0] + S2::TO0 - 1) / S2::TO0;
+  a.tiles[1] = (a.g.n[1] + S2::TO1 - 1) / S2::TO1;
   a.tiles[2] = 1;
   const size_t smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
-  return submit<Tile2dK<T, MODE, WA, WBT, WB>>(a, (long long)a.tiles[0] * a.tiles[1], smem, st);
+  return submit<Tile2dK<T, EY, MODE, WA, WBT, WB>>(a, (long long)a.tiles[0] * a.tiles[1], smem, st);
 }
 
-template <typename T, int MODE>
-static cudaError_t dispatch2(int ops, TileArgs<T> a, cudaStream_t st) {
-  switch (ops) {
-    case OPS_A: return launch2<T, MODE, true, false, false>(a, st);
-    case OPS_BT: return launch2<T, MODE, false, true, false>(a, st);
-    case OPS_B: return launch2<T, MODE, false, false, true>(a, st);
-    case OPS_A | OPS_BT | OPS_B: return launch2<T, MODE, true, true, true>(a, st);
-    default: return cudaErrorInvalidValue;
+// Launch one tile height.  FULL: every mode / operator combination is compiled; otherwise only
+// the velocity-block modes the multigrid uses on every level (apply, residual, Chebyshev).
+template <typename T, int EY, bool FULL>
+cudaError_t launch_shape(int mode, int ops, const TileArgs<T>& a, cudaStream_t st) {
+  if (ops == OPS_A) {
+    if (mode == TILE_APPLY) return launch2<T, EY, TILE_APPLY, true, false, false>(a, st);
+    if (mode == TILE_RESID) return launch2<T, EY, TILE_RESID, true, false, false>(a, st);
+    return launch2<T, EY, TILE_CHEB, true, false, false>(a, st);
   }
+  if constexpr (FULL) {
+    if (mode == TILE_CHEB) return cudaErrorInvalidValue;
+    const bool ap = mode == TILE_APPLY;
+    switch (ops) {
+      case OPS_BT:
+        return ap ? launch2<T, EY, TILE_APPLY, false, true, false>(a, st) : launch2<T, EY, TILE_RESID, false, true, false>(a, st);
+      case OPS_B:
+        return ap ? launch2<T, EY, TILE_APPLY, false, false, true>(a, st) : launch2<T, EY, TILE_RESID, false, false, true>(a, st);
+      case OPS_A | OPS_BT | OPS_B:
+        return ap ? launch2<T, EY, TILE_APPLY, true, true, true>(a, st) : launch2<T, EY, TILE_RESID, true, true, true>(a, st);
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
+  return cudaErrorNotSupported;
 }
 
+}  // namespace tile2d
+
+// per-height launchers (one translation unit each, compiled in parallel)
 template <typename T>
-cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st) {
-  if (mode == TILE_APPLY) return dispatch2<T, TILE_APPLY>(ops, a, st);
-  if (mode == TILE_RESID) return dispatch2<T, TILE_RESID>(ops, a, st);
-  if (ops != OPS_A) return cudaErrorInvalidValue;
-  return launch2<T, TILE_CHEB, true, false, false>(a, st);
-}
-
-template cudaError_t launch_tile2d<float>(int, int, TileArgs<float>, cudaStream_t);
-template cudaError_t launch_tile2d<double>(int, int, TileArgs<double>, cudaStream_t);
+cudaError_t launch_tile2d_e16(int mode, int ops, const TileArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tile2d_e17(int mode, int ops, const TileArgs<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tile2d_e8(int mode, int ops, const TileArgs<T>& a, cudaStream_t st);
 
 }  // namespace gs

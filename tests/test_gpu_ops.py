@@ -218,3 +218,36 @@ def test_pressure_laplacian_transfers_vcycle(case):
     assert rel(xf.cpu().numpy(), x + P @ xc) <= 1e-14
     s.apply_level(L, 14, torch.tensor(x, device="cuda"), y)
     assert rel(y.cpu().numpy(), H.apply_inverse(x)) <= 1e-10
+
+
+TILE_HEIGHT_CASES = {
+    "channel_small": lambda: inputs.config_channel(nx=160, ny=28, levels=3),
+    "box_ragged": lambda: inputs.config_box_inclusion(2, (100, 52), 3, 1e4, 30.0, seed=4, align_coarse=True),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TILE_HEIGHT_CASES))
+def test_tile_heights_give_identical_solves(name):
+    """The 2D cell kernel's tile height (32 x 16, 32 x 17, 32 x 8 evaluated cells, forced or
+    autotuned) changes only the launch shape: every node sums its cell contributions in a fixed
+    order, so the solve is bitwise the same."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = TILE_HEIGHT_CASES[name]()
+    outs = []
+    for mode in (1, 2, 3, 0):
+        s = gs.Solver.from_problem(p, tile_autotune=mode)
+        inf = s.info()
+        rows = [inf.tile_rows[l] for l in range(p.levels)]
+        assert all(r in (8, 16, 17) for r in rows) and inf.saddle_tile_rows in (16, 17)
+        if mode:
+            assert rows == [(16, 17, 8)[mode - 1]] * p.levels
+        f = torch.tensor(p.f, device="cuda")
+        g = torch.tensor(p.g, device="cuda")
+        b = torch.empty_like(f)
+        s.lift_rhs(f, g, b)
+        x = torch.zeros_like(b)
+        it, rr, _ = s.solve(b, x, tol=1e-9)
+        outs.append((x.cpu(), it, rr))
+    for x, it, rr in outs[1:]:
+        assert (it, rr) == outs[0][1:] and torch.equal(x, outs[0][0])
