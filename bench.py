@@ -354,6 +354,8 @@ def run_gpu(args, rank, world):
                        "parallelism": f"replicas x{world}"},
             "time_to_solve_ms": {"p50": statistics.median(ts), "p99": ts[min(len(ts) - 1, int(math.ceil(0.99 * len(ts))) - 1)]},
             "iterations": statistics.median(its), "rel_residual": max(rels),
+            "tile_rows": {"levels": [solver.info().tile_rows[l] for l in range(p.levels)],
+                          "saddle": solver.info().saddle_tile_rows},
             "ax_gdofs": {"fp64": ax64, "fp32": ax32},
             "fp64_multigrid": fp64,
             "roofline": roof,

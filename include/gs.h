@@ -115,8 +115,8 @@ typedef struct {            /* zero-initialised = defaults */
   int tile_autotune;        /* 2D meshes: 0 -> at gs_create, time each compiled tile height of the
                                   cell kernel (32 x 16, 32 x 17, 32 x 8 evaluated cells) on every
                                   level and keep the fastest (default); 1 / 2 / 3 -> always
-                                  32 x 16 / 32 x 17 / 32 x 8 (the FP64 saddle operator uses 32 x 16
-                                  with 3).  The results do not depend on the choice. */
+                                  32 x 16 / 32 x 17 / 32 x 8.  The results do not depend on the
+                                  choice. */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */

@@ -848,7 +848,7 @@ gs_status autotune(gs_ctx* c) {
   CK(cudaMemsetAsync(c->r, 0, sizeof(double) * c->N, c->st));
   double best_us = 0.0;
   int best = 0;
-  for (int s = 0; s < 2; ++s) {  // heights compiled for the full saddle operator
+  for (int s = 0; s < kTileShapes2D; ++s) {
     c->saddle_shape = s;
     double us;
     CKS(time_launches(c, [&]() -> cudaError_t {
@@ -909,7 +909,7 @@ gs_status setup(gs_ctx* c) {
     CKS(c->fp32 ? autotune<float>(c) : autotune<double>(c));
   } else if (c->dim == 2) {
     for (int l = 0; l < c->L; ++l) c->lv[l].shape = c->opt.tile_autotune - 1;
-    c->saddle_shape = c->opt.tile_autotune == 2 ? 1 : 0;
+    c->saddle_shape = c->opt.tile_autotune - 1;
   }
   return GS_OK;
 }

@@ -14,14 +14,14 @@ template cudaError_t launch_tile2d_e16<double>(int, int, const TileArgs<double>&
 
 namespace gs {
 
-// Tile height per launch: TileArgs::shape 0 -> 16 rows of evaluated cells (every mode), 1 -> 17
-// (every mode), 2 -> 8 (velocity-block modes; other operators fall back to 16).  The result does
-// not depend on the height: every node sums its cell contributions in a fixed order.
+// Tile height per launch: TileArgs::shape 0 -> 16 rows of evaluated cells, 1 -> 17, 2 -> 8 (every
+// mode and operator).  The result does not depend on the height: every node sums its cell
+// contributions in a fixed order.
 template <typename T>
 cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st) {
   if (mode == TILE_CHEB && ops != OPS_A) return cudaErrorInvalidValue;
   if (a.shape == 1) return launch_tile2d_e17<T>(mode, ops, a, st);
-  if (a.shape == 2 && ops == OPS_A) return launch_tile2d_e8<T>(mode, ops, a, st);
+  if (a.shape == 2) return launch_tile2d_e8<T>(mode, ops, a, st);
   return launch_tile2d_e16<T>(mode, ops, a, st);
 }
 template cudaError_t launch_tile2d<float>(int, int, TileArgs<float>, cudaStream_t);

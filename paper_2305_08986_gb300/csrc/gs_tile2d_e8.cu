@@ -5,7 +5,7 @@ namespace gs {
 
 template <typename T>
 cudaError_t launch_tile2d_e8(int mode, int ops, const TileArgs<T>& a, cudaStream_t st) {
-  return tile2d::launch_shape<T, 8, false>(mode, ops, a, st);
+  return tile2d::launch_shape<T, 8, true>(mode, ops, a, st);
 }
 template cudaError_t launch_tile2d_e8<float>(int, int, const TileArgs<float>&, cudaStream_t);
 template cudaError_t launch_tile2d_e8<double>(int, int, const TileArgs<double>&, cudaStream_t);

@@ -239,7 +239,7 @@ def test_tile_heights_give_identical_solves(name):
         s = gs.Solver.from_problem(p, tile_autotune=mode)
         inf = s.info()
         rows = [inf.tile_rows[l] for l in range(p.levels)]
-        assert all(r in (8, 16, 17) for r in rows) and inf.saddle_tile_rows in (16, 17)
+        assert all(r in (8, 16, 17) for r in rows) and inf.saddle_tile_rows in (8, 16, 17)
         if mode:
             assert rows == [(16, 17, 8)[mode - 1]] * p.levels
         f = torch.tensor(p.f, device="cuda")
