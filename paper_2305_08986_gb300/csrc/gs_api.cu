@@ -137,6 +137,7 @@ struct gs_ctx {
   double* part = nullptr;
   int G = 1;   // blocks of the multi-dot partial sums
   int GA = 1;  // blocks of the fused axpy + norm (G * (m + 2) >= GA partial sums)
+  int GF = 1;  // blocks of the fused CGS2 update + dots (one wave, 2 CTAs per SM; GF <= G)
   double* dsc = nullptr;
   double* hpin = nullptr;
   int last_it = 0;
@@ -481,6 +482,7 @@ void layout(gs_ctx* c, Arena& ar) {
   if (GA > (long long)c->G * (m + 2)) GA = (long long)c->G * (m + 2);
   if (GA < 1) GA = 1;
   c->GA = (int)GA;
+  c->GF = (int)std::min<long long>(G, 2 * 152);
   c->part = ar.take<double>((long long)c->G * (m + 2));
   c->dsc = ar.take<double>(4 * (m + 4));
   c->footprint = ar.off + 256;
@@ -1166,6 +1168,20 @@ gs_status norm2_host(gs_ctx* c, const double* x, double* out) {
   return dot_host<double>(c, x, c->N, 1, x, c->N, out);
 }
 
+// CGS2 with the double-float basis (orth = 0): h1 = V^T w; w -= V h1 fused with h2 = V^T w (one
+// pass over V); w -= V h2 with the new |w|^2.  h1, h2: j + 1 entries each, nrm: |w|^2 (device).
+const int kFusedGsMax = 64;
+gs_status cgs2_fused(gs_ctx* c, const float2* Vdf, int j, double* h1, double* h2, double* nrm) {
+  const long long N = c->N;
+  KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h1, c->st));
+  KL(K_AXPY, launch_multi_axpy_dots_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GF, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->GF, h2, c->st));
+  KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+  return GS_OK;
+}
+
 gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, double* relres) {
   const long long N = c->N;
   const int m = c->opt.restart;
@@ -1218,38 +1234,51 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       // classical Gram-Schmidt: h = V^T w (with |w|^2 in the same pass), w -= V h (with the new
       // |w|^2 in the same pass); a second pass when |w| fell below 1/sqrt(2) of its value
       // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, orth = 0)
-      if (dfk)
-        KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 1, c->st));
-      else
-        KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, j + 2, c->G, h1, c->st));
-      if (dfk)
-        KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
-      else
-        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
-      CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->st));
-      CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
-      CK(cudaStreamSynchronize(c->st));
-      for (int i = 0; i <= j; ++i) Hc(i, j) = c->hpin[i];
-      const double wn0 = std::sqrt(c->hpin[j + 1]);
-      double hn = std::sqrt(c->hpin[m + 1]);
-      if (c->opt.orth == 0 || hn < kReorthKappa * wn0) {
+      double hn;
+      if (c->opt.orth == 0 && dfk && j + 1 <= kFusedGsMax) {
+        // CGS2 with the first update fused into the second pass's dots: three passes over V
+        CKS(cgs2_fused(c, Vdf, j, h1, h2, nrm));
+        CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->hpin + (j + 1), h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->hpin + 2 * (j + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int i = 0; i <= j; ++i) Hc(i, j) = c->hpin[i];
+        for (int i = 0; i <= j; ++i) Hc(i, j) += c->hpin[j + 1 + i];
+        hn = std::sqrt(c->hpin[2 * (j + 1)]);
+      } else {
         if (dfk)
-          KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
+          KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 1, c->st));
         else
-          KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
-        KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
+          KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+        KL(K_DOTS, launch_reduce_partials(c->part, j + 2, c->G, h1, c->st));
         if (dfk)
-          KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+          KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
         else
-          KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+          KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
         KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
-        CK(cudaMemcpyAsync(c->hpin, h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
-        for (int i = 0; i <= j; ++i) Hc(i, j) += c->hpin[i];
+        for (int i = 0; i <= j; ++i) Hc(i, j) = c->hpin[i];
+        const double wn0 = std::sqrt(c->hpin[j + 1]);
         hn = std::sqrt(c->hpin[m + 1]);
+        if (c->opt.orth == 0 || hn < kReorthKappa * wn0) {
+          if (dfk)
+            KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
+          else
+            KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+          KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
+          if (dfk)
+            KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+          else
+            KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+          KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+          CK(cudaMemcpyAsync(c->hpin, h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+          CK(cudaMemcpyAsync(c->hpin + (m + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+          CK(cudaStreamSynchronize(c->st));
+          for (int i = 0; i <= j; ++i) Hc(i, j) += c->hpin[i];
+          hn = std::sqrt(c->hpin[m + 1]);
+        }
       }
       if (!std::isfinite(hn)) return fail(GS_EBREAKDOWN, "Arnoldi vector is not finite");
       Hc(j + 1, j) = hn;
@@ -1563,26 +1592,30 @@ gs_status slot_record_post(gs_ctx* c, double* gather_dev) {
       double* nrm = sl_nrm(c);
       CKS(c->fp32 ? sl_cast_out<float>(c, v, Zj) : sl_cast_out<double>(c, v, Zj));
       CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
-      if (dfk)
-        KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 1, c->st));
-      else
-        KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, j + 2, c->G, h1, c->st));
-      if (dfk)
-        KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
-      else
-        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
-      if (dfk)
-        KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
-      else
-        KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
-      if (dfk)
-        KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
-      else
-        KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
-      KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+      if (dfk && j + 1 <= kFusedGsMax) {
+        CKS(cgs2_fused(c, Vdf, j, h1, h2, nrm));
+      } else {
+        if (dfk)
+          KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 1, c->st));
+        else
+          KL(K_DOTS, launch_dots_norm_partial(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+        KL(K_DOTS, launch_reduce_partials(c->part, j + 2, c->G, h1, c->st));
+        if (dfk)
+          KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
+        else
+          KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GA, c->st));
+        KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+        if (dfk)
+          KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
+        else
+          KL(K_DOTS, launch_dots_partial<double>(c->V, N, j + 1, c->w, N, c->part, c->G, c->st));
+        KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h2, c->st));
+        if (dfk)
+          KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+        else
+          KL(K_AXPY, launch_multi_axpy_norm(c->V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+        KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+      }
       KL(K_VEC, launch_gather3(h1, j + 1, h2, j + 1, nrm, 1, gather_dev, c->st));
       break;
     }
@@ -1746,7 +1779,7 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
   layout(c, ar);
   c->cc = c->cc_alloc && (c->opt.schur_kind == 2 || alpha > 0.0);
   set_geom(c, mesh);
-  cudaError_t e = cudaMallocHost(&c->hpin, sizeof(double) * (c->opt.restart + 8));
+  cudaError_t e = cudaMallocHost(&c->hpin, sizeof(double) * (2 * c->opt.restart + 8));
   if (e != cudaSuccess) { delete c; return fail(GS_ECUDA, std::string("pinned buffer: ") + cudaGetErrorString(e)); }
   if (c->opt.graphs == 0 && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess)
     c->cap_st = nullptr;  // graphs stay off

@@ -363,6 +363,85 @@ cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, con
   return submit<MultiAxpyNormDfK>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(float2) * (k > 0 ? k : 1), st);
 }
 
+// First CGS2 update fused with the second pass's dot products (double-float basis):
+//   w <- w + sign * sum_i coef[i] V[i]            (double-float sum, FP64 result)
+//   part[i * nblk + blk] = sum over the block's elements of V[i] . w_new
+// The block walks its elements in rounds of 256: every thread updates one element and keeps the
+// new value (double-float) in shared memory, then warp q accumulates the dot products of basis
+// vectors q, q + 8, q + 16, ... over the round's 256 elements (coalesced rows; the rows were just
+// read by the update, so they come from L1/L2).  One pass over V from HBM instead of two.
+struct MultiAxpyDotsDfK {
+  static constexpr int KW = 8;  // basis vectors per warp (k <= 64)
+  struct Args { const float2* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
+  static constexpr int THREADS = TPB, MINB = 2;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    extern __shared__ float2 cs2[];
+    __shared__ float2 wt[TPB];
+    const float2* __restrict__ V = a.V;
+    double* __restrict__ w = a.w;
+    const long long ldv = a.ldv, n = a.n;
+    const int k = a.k;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < k; i += blockDim.x) cs2[i] = df_split(a.sign * a.coef[i]);
+    float2 acc[KW];
+#pragma unroll
+    for (int q = 0; q < KW; ++q) acc[q] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (long long base = (long long)blk * TPB; base < n; base += (long long)nblk * TPB) {
+      const long long e = base + tid;
+      float2 wdf = make_float2(0.f, 0.f);
+      if (e < n) {
+        float2 s = make_float2(0.f, 0.f);
+        int i = 0;
+        for (; i + 8 <= k; i += 8) {
+          float2 v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = V[(i + u) * ldv + e];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) df_fma(s, cs2[i + u], v[u]);
+        }
+        for (; i < k; ++i) df_fma(s, cs2[i], V[i * ldv + e]);
+        const double r = w[e] + df_join(s);
+        w[e] = r;
+        wdf = df_split(r);
+      }
+      wt[tid] = wdf;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < KW; ++q) {
+        const int i = wid + 8 * q;
+        if (i < k) {
+          const float2* Vi = V + i * ldv + base;
+          float2 v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int el = lane + 32 * t;
+            v[t] = base + el < n ? Vi[el] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int t = 0; t < 8; ++t) df_fma(acc[q], v[t], wt[lane + 32 * t]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+      const int i = wid + 8 * q;
+      if (i < k) {
+        double v = df_join(acc[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) a.part[(long long)i * nblk + blk] = v;
+      }
+    }
+  }
+};
+cudaError_t launch_multi_axpy_dots_df(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
+                                      long long n, double* part, int G, cudaStream_t st) {
+  if (k > 8 * MultiAxpyDotsDfK::KW) return cudaErrorInvalidValue;
+  return submit<MultiAxpyDotsDfK>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(float2) * (k > 0 ? k : 1), st);
+}
+
 // v_df <- w / sqrt(nrm2) in double-float form, and the same vector as double in vd
 struct ScaleDfK {
   struct Args { const double* w; const double* nrm2; float2* v; double* vd; long long n; };

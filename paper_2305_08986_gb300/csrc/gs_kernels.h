@@ -164,6 +164,10 @@ cudaError_t launch_dots_partial_df(const float2* V, long long ldv, int k, const 
                                    double* part, int G, int self_dot, cudaStream_t st);
 cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, const double* coef, double sign,
                                       double* w, long long n, double* part, int G, cudaStream_t st);
+// w <- w + sign * sum_i coef[i] V[i], then part[i * G + block] = partial sums of V[i] . w_new
+// (first CGS2 update fused with the second pass's dots; k <= 64)
+cudaError_t launch_multi_axpy_dots_df(const float2* V, long long ldv, int k, const double* coef, double sign,
+                                      double* w, long long n, double* part, int G, cudaStream_t st);
 cudaError_t launch_scale_by_rnorm_df(const double* w, const double* nrm2, float2* v, double* vd, long long n,
                                      cudaStream_t st);
 // w <- w + sign * sum_i coef[i] V[i]   (coef on device)
