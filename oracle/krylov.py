@@ -124,14 +124,14 @@ class StokesOracle:
     """FP64 reference solver for one problem: assembled system + velocity hierarchy."""
 
     def __init__(self, mesh: Mesh, eta, alpha, levels, degree=4, seed=0, restart=50, schur="auto",
-                 coarse="cholesky", orth="cgs2", pdegree=2):
+                 coarse="cholesky", orth="cgs2", pdegree=2, deflate=False):
         self.mesh = mesh
         self.alpha = float(alpha)
         self.sys = System(mesh, eta, alpha)
         self.levels = levels
         self.restart = restart
         self.orth = orth
-        self.mg = Hierarchy(mesh, eta, alpha, levels, degree=degree, seed=seed, coarse=coarse)
+        self.mg = Hierarchy(mesh, eta, alpha, levels, degree=degree, seed=seed, coarse=coarse, deflate=deflate)
         # Schur approximation: "mass" = M_p(1/eta) only; "cc" = Cahouet-Chabard
         # M_p(1/eta)^{-1} + alpha K_p^{-1}; "auto" = cc when alpha > 0
         self.schur = ("cc" if self.alpha > 0 else "mass") if schur == "auto" else schur

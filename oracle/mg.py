@@ -154,7 +154,7 @@ class Hierarchy:
     """Velocity multigrid hierarchy, levels[0] = coarsest."""
 
     def __init__(self, fine: Mesh, eta_fine, alpha, nlevels, degree=4, seed=0,
-                 lanczos_steps=12, safety=1.2, ratio=15.0, coarse="cholesky"):
+                 lanczos_steps=12, safety=1.2, ratio=15.0, coarse="cholesky", deflate=False):
         meshes = [fine]
         etas = [np.asarray(eta_fine, dtype=float)]
         for _ in range(nlevels - 1):
@@ -175,6 +175,12 @@ class Hierarchy:
         if coarse == "cholesky":
             A0 = self.levels[0].A.toarray()
             self.levels[0].chol = sla.cho_factor(A0, lower=True)
+        # rigid-body deflation of stiff inclusions on the finest level (deflation.py)
+        self.defl = None
+        if deflate:
+            from .deflation import Deflation
+            fl = self.levels[-1]
+            self.defl = Deflation(fl.mesh, fl.eta, fl.A)
 
     def vcycle(self, b, level=None):
         """Velocity V-cycle V(l, b) (Sec. 4): pre-smooth from 0, residual, restrict, recurse,
@@ -192,6 +198,8 @@ class Hierarchy:
         r = b - lv.A @ x
         rc = lv.P.T @ r
         x = x + lv.P @ self.vcycle(rc, level - 1)
+        if self.defl is not None and level == len(self.levels) - 1:
+            x = x + self.defl.correction(r)
         x = chebyshev(lv.A, Dinv, b, x, self.degree, lo, hi)
         return x
 

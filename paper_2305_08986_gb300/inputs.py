@@ -212,6 +212,28 @@ def config_spheres(n: int = 64, levels: int = 5, n_spheres: int = 64, eta_in: fl
     return Problem(f"spheres{n}", dim, nn, L, levels, eta, alpha, all_faces(dim), None, f, g)
 
 
+def config_discs(n: int = 64, levels: int = 4, n_discs: int = 8, eta_in: float = 1e6, alpha: float = 100.0,
+                 seed: int = 0, rmin: float = 0.015, rmax: float = 0.04) -> Problem:
+    """2D analog of the spheres workload: unit square, n^2 cells, eta = eta_in on cells whose
+    centroid lies in one of the seeded discs (centres U(0,1)^2, radius U(rmin, rmax)), 1 outside;
+    nodal load N(0, 1); no-slip."""
+    dim = 2
+    nn = (n, n)
+    L = (1.0, 1.0)
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.0, 1.0, size=(n_discs, 2))
+    radii = rng.uniform(rmin, rmax, size=n_discs)
+    c = cell_centroids(dim, nn, L)
+    inside = np.zeros(len(c), dtype=bool)
+    for k in range(n_discs):
+        inside |= ((c - centres[k]) ** 2).sum(axis=1) <= radii[k] ** 2
+    eta = np.where(inside, eta_in, 1.0)
+    nv = (2 * n + 1) ** 2
+    f = _full(dim, nn, rng.standard_normal(size=(nv, dim)))
+    g = _full(dim, nn)
+    return Problem(f"discs{n}_s{seed}", dim, nn, L, levels, eta, float(alpha), all_faces(dim), None, f, g)
+
+
 # --------------------------------------------------------------------------
 # generic random instances (tests, batching, serving)
 # --------------------------------------------------------------------------
