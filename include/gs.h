@@ -117,6 +117,14 @@ typedef struct {            /* zero-initialised = defaults */
                                   level and keep the fastest (default); 1 / 2 / 3 -> always
                                   32 x 16 / 32 x 17 / 32 x 8.  The results do not depend on the
                                   choice. */
+  int deflate;              /* 1: rigid-body deflation of stiff inclusions in the V-cycle's finest
+                                  level (not part of the paper's method; for stiff inclusions
+                                  smaller than a coarse cell, whose near-rigid motions no coarse
+                                  level represents): inclusions = node-connected components of
+                                  cells with eta >= sqrt(eta_min eta_max) when eta_max >= 1e3
+                                  eta_min, at most 256; Z = their rigid motions on their cells'
+                                  nodes; the finest level adds Z (Z^T A Z)^-1 Z^T r to its coarse
+                                  correction.  0: off (default). */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */
@@ -212,6 +220,8 @@ typedef struct {
   double plambda_max[16];  /* Chebyshev upper bound of the pressure Laplacian per level */
   int tile_rows[16];       /* 2D: evaluated cell rows per tile chosen for each level's multigrid kernels */
   int saddle_tile_rows;    /* 2D: the same for the FP64 saddle operator (0 in 3D) */
+  int deflation_inclusions;/* stiff inclusions in the deflation space (option deflate) */
+  int deflation_modes;     /* rigid modes kept (modes vanishing on unconstrained nodes dropped) */
 } gs_info;
 gs_status gs_get_info(const gs_ctx* ctx, gs_info* out);
 

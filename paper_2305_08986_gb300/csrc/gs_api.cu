@@ -134,6 +134,14 @@ struct gs_ctx {
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
   double* vcur = nullptr;  // current basis vector as double (input of the preconditioner)
   int saddle_shape = 0;    // 2D tile height variant of the FP64 saddle operator
+  // rigid-body deflation of stiff inclusions on the finest level (option deflate = 1)
+  int defl_ninc = 0, defl_M = 0, defl_m = 0;  // inclusions, modes (ninc x nt), modes kept
+  std::vector<int> hd_nodes, hd_off;
+  std::vector<double> hd_cen;
+  std::vector<uint8_t> hd_keep;
+  int *d_nodes = nullptr, *d_off = nullptr;
+  double *d_cen = nullptr, *d_Einv = nullptr, *d_c = nullptr, *d_y = nullptr;
+  DeflArgs defl{};
   double* part = nullptr;
   int G = 1;   // blocks of the multi-dot partial sums
   int GA = 1;  // blocks of the fused axpy + norm (G * (m + 2) >= GA partial sums)
@@ -208,6 +216,7 @@ gs_options normalize_opts(const gs_options* o) {
   r.plap_degree = opt_or(r.plap_degree, 2);
   r.krylov_fp64 = r.krylov_fp64 == 1 ? 1 : 0;
   r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 3) ? r.tile_autotune : 0;
+  r.deflate = r.deflate == 1 ? 1 : 0;
   return r;
 }
 
@@ -242,6 +251,10 @@ OpCoef<T> make_coef(int dim, const double* h, double alpha) {
   c.eta_scale = (T)1;
   return c;
 }
+
+// inclusions whose rigid motions the deflation space can hold (workspace capacity)
+const int kDeflMaxInclusions = 256;
+gs_status plan_deflation(gs_ctx* c, const gs_mesh* m);
 
 // ---- host planning: level sizes, obstacle flags, constraint masks, coarse eta -----------------
 gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
@@ -417,6 +430,110 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
     c->nfp = (int)c->hpfree.size();
     if ((long long)c->nfp * c->nfp > (1LL << 31)) return fail(GS_EINVAL, "coarsest pressure level too large");
   }
+  CKS(plan_deflation(c, m));
+  return GS_OK;
+}
+
+// ---- rigid-body deflation of stiff inclusions (finest level; kernels in gs_defl.cu) --------------
+// Stiff cells: active cells with eta >= sqrt(eta_min eta_max), only when eta_max >= 1e3 eta_min;
+// inclusions: connected components of stiff cells sharing a velocity node, numbered in the order
+// of their first cell; per inclusion the sorted unconstrained nodes of its cells, the centroid of
+// all its cells' nodes, and which of its rigid modes do not vanish on the unconstrained nodes.
+gs_status plan_deflation(gs_ctx* c, const gs_mesh* m) {
+  c->hd_nodes.clear();
+  c->hd_off.assign(1, 0);
+  c->hd_cen.clear();
+  c->hd_keep.clear();
+  c->defl_ninc = c->defl_M = c->defl_m = 0;
+  if (c->opt.deflate != 1) return GS_OK;
+  const Level& F = c->lv[c->L - 1];
+  const int dim = c->dim, nt = dim == 2 ? 3 : 6;
+  if (F.Nv >= (1LL << 31)) return fail(GS_EINVAL, "deflation: mesh too large for 32-bit node lists");
+  if (F.heta.empty()) return GS_OK;
+  double lo = INFINITY, hi = 0.0;
+  for (long long i = 0; i < F.Nc; ++i)
+    if (!F.hvoid[i]) { lo = std::fmin(lo, F.heta[i]); hi = std::fmax(hi, F.heta[i]); }
+  if (!(hi >= 1e3 * lo)) return GS_OK;
+  const double thr = std::sqrt(lo * hi);
+  auto stiff = [&](long long i) { return !F.hvoid[i] && F.heta[i] >= thr; };
+  const int n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
+  std::vector<int> lab(F.Nc, 0);
+  std::vector<std::vector<long long>> cells;
+  std::vector<long long> stack;
+  for (long long c0 = 0; c0 < F.Nc; ++c0) {
+    if (!stiff(c0) || lab[c0]) continue;
+    cells.emplace_back();
+    const int id = (int)cells.size();
+    lab[c0] = id;
+    stack.assign(1, c0);
+    while (!stack.empty()) {
+      const long long cc = stack.back();
+      stack.pop_back();
+      cells.back().push_back(cc);
+      const int i = (int)(cc % n0), j = (int)((cc / n0) % n1), k = (int)(cc / ((long long)n0 * n1));
+      for (int dk = (dim == 3 ? -1 : 0); dk <= (dim == 3 ? 1 : 0); ++dk)
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di) {
+            const int a = i + di, b = j + dj, e = k + dk;
+            if (a < 0 || a >= n0 || b < 0 || b >= n1 || e < 0 || e >= n2) continue;
+            const long long cn = a + (long long)n0 * (b + (long long)n1 * e);
+            if (stiff(cn) && !lab[cn]) { lab[cn] = id; stack.push_back(cn); }
+          }
+    }
+  }
+  const int nv0 = 2 * n0 + 1, nv1 = 2 * n1 + 1;
+  Geom gt{};
+  gt.dim = dim;
+  gt.faces = m->dirichlet_faces;
+  gt.nv[0] = nv0; gt.nv[1] = nv1; gt.nv[2] = dim == 3 ? 2 * n2 + 1 : 1;
+  std::vector<int> stamp(F.Nv, 0);
+  for (size_t q = 0; q < cells.size(); ++q) {
+    std::vector<int> nodes;
+    for (long long cc : cells[q]) {
+      const int i = (int)(cc % n0), j = (int)((cc / n0) % n1), k = (int)(cc / ((long long)n0 * n1));
+      for (int lc = 0; lc < (dim == 3 ? 3 : 1); ++lc)
+        for (int lb = 0; lb < 3; ++lb)
+          for (int la = 0; la < 3; ++la) {
+            const long long nd = (2 * i + la) + (long long)nv0 * ((2 * j + lb) + (long long)nv1 * (dim == 3 ? 2 * k + lc : 0));
+            if (stamp[nd] != (int)q + 1) { stamp[nd] = (int)q + 1; nodes.push_back((int)nd); }
+          }
+    }
+    std::sort(nodes.begin(), nodes.end());
+    double cen[3] = {0, 0, 0};
+    for (int nd : nodes) {
+      cen[0] += (nd % nv0) * (0.5 * F.h[0]);
+      cen[1] += ((nd / nv0) % nv1) * (0.5 * F.h[1]);
+      if (dim == 3) cen[2] += (nd / ((long long)nv0 * nv1)) * (0.5 * F.h[2]);
+    }
+    for (int a = 0; a < 3; ++a) cen[a] /= (double)nodes.size();
+    double norm2[6] = {0, 0, 0, 0, 0, 0};
+    for (int nd : nodes) {
+      const int I = nd % nv0, J = (nd / nv0) % nv1, K = dim == 3 ? (int)(nd / ((long long)nv0 * nv1)) : 0;
+      const bool con = F.has_void ? F.hvmask[nd] != 0 : face_constrained(gt, I, J, K);
+      if (con) continue;
+      c->hd_nodes.push_back(nd);
+      const double dx = I * (0.5 * F.h[0]) - cen[0], dy = J * (0.5 * F.h[1]) - cen[1];
+      const double dz = dim == 3 ? K * (0.5 * F.h[2]) - cen[2] : 0.0;
+      for (int a = 0; a < dim; ++a) norm2[a] += 1.0;
+      if (dim == 2) {
+        norm2[2] += dx * dx + dy * dy;
+      } else {
+        norm2[3] += dy * dy + dz * dz;
+        norm2[4] += dx * dx + dz * dz;
+        norm2[5] += dx * dx + dy * dy;
+      }
+    }
+    c->hd_off.push_back((int)c->hd_nodes.size());
+    for (int a = 0; a < 3; ++a) c->hd_cen.push_back(cen[a]);
+    for (int t = 0; t < nt; ++t) {
+      c->hd_keep.push_back(norm2[t] > 0.0 ? 1 : 0);
+      c->defl_m += norm2[t] > 0.0 ? 1 : 0;
+    }
+  }
+  c->defl_ninc = (int)cells.size();
+  c->defl_M = c->defl_ninc * nt;
+  if (c->defl_ninc > kDeflMaxInclusions)
+    return fail(GS_EINVAL, "deflation: more than " + std::to_string(kDeflMaxInclusions) + " stiff inclusions");
   return GS_OK;
 }
 
@@ -464,6 +581,15 @@ void layout(gs_ctx* c, Arena& ar) {
     c->PAinv = ar.take<double>((long long)c->nfp * c->nfp);
     c->pcfree = ar.take<int>(c->nfp);
     c->pctmp = ar.take<double>(c->nfp);
+  }
+  if (c->opt.deflate == 1) {  // capacity: every node, kDeflMaxInclusions inclusions
+    const int Mmax = kDeflMaxInclusions * (c->dim == 2 ? 3 : 6);
+    c->d_nodes = ar.take<int>(c->lv[c->L - 1].Nv);
+    c->d_off = ar.take<int>(kDeflMaxInclusions + 1);
+    c->d_cen = ar.take<double>(3LL * kDeflMaxInclusions);
+    c->d_Einv = ar.take<double>((long long)Mmax * Mmax);
+    c->d_c = ar.take<double>(Mmax);
+    c->d_y = ar.take<double>(Mmax);
   }
   const int m = c->opt.restart;
   c->V = ar.take<double>((long long)(m + 1) * c->N);
@@ -962,10 +1088,17 @@ gs_status vcycle(gs_ctx* c, int l) {
     a.xu = (const T*)lv.xA; a.bu = (const T*)lv.b; a.yu = (T*)lv.d;
     KL(K_RESID, launch_tile<T>(c->dim, TILE_RESID, OPS_A, a, c->st));
   }
+  // rigid-body deflation on the finest level: y = E^-1 Z^T r, added after the coarse correction
+  const bool defl = l == c->L - 1 && c->defl_ninc > 0;
+  if (defl) {
+    KL(K_VEC, launch_defl_dots<T>(c->defl, (const T*)lv.d, c->d_c, c->st));
+    KL(K_VEC, launch_defl_gemv(c->d_Einv, c->defl_M, c->d_c, c->d_y, c->st));
+  }
   Level& cl = c->lv[l - 1];
   KL(K_TRANSFER, launch_restrict<T>(lv.g, cl.g, (const T*)lv.d, (T*)cl.b, c->st));
   CKS(vcycle<T>(c, l - 1));
   KL(K_TRANSFER, launch_prolong_add<T>(lv.g, cl.g, (const T*)cl.xA, (T*)lv.xA, c->st));
+  if (defl) KL(K_VEC, launch_defl_add<T>(c->defl, c->d_y, (T*)lv.xA, c->st));
   for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, false));
   return GS_OK;
 }
@@ -1432,6 +1565,134 @@ gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, co
 
 }  // namespace
 
+// ---- deflation space: E = Z^T A Z from FP64 applies of colour-batched modes -------------------
+// Inclusions k and l interact when some cell has unconstrained nodes of both (then z_l^T A z_k
+// may be nonzero).  With a distance-2 colouring of that graph, applying A to the sum of mode t
+// over the inclusions of one colour gives, for every inclusion l, the entry of E in row (l, b)
+// and column (k, t) for the single inclusion k of that colour that interacts with l (or is l).
+gs_status setup_deflation(gs_ctx* c) {
+  if (c->opt.deflate != 1) return GS_OK;
+  const Level& F = c->lv[c->L - 1];
+  c->defl = DeflArgs{};
+  c->defl.g = F.g;
+  c->defl.nodes = c->d_nodes;
+  c->defl.off = c->d_off;
+  c->defl.cen = c->d_cen;
+  c->defl.ninc = c->defl_ninc;
+  if (c->defl_ninc == 0) return GS_OK;
+  const int dim = c->dim, nt = dim == 2 ? 3 : 6, ninc = c->defl_ninc, M = c->defl_M;
+  CK(cudaMemcpyAsync(c->d_nodes, c->hd_nodes.data(), sizeof(int) * c->hd_nodes.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->d_off, c->hd_off.data(), sizeof(int) * c->hd_off.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(c->d_cen, c->hd_cen.data(), sizeof(double) * c->hd_cen.size(), cudaMemcpyHostToDevice, c->st));
+  const int nv0 = F.g.nv[0], nv1 = F.g.nv[1];
+  std::vector<std::vector<int>> nb(ninc);
+  {
+    std::vector<std::pair<long long, int>> touch;  // (cell, inclusion) through unconstrained nodes
+    for (int k = 0; k < ninc; ++k)
+      for (int i = c->hd_off[k]; i < c->hd_off[k + 1]; ++i) {
+        const int nd = c->hd_nodes[i];
+        const int idx[3] = {nd % nv0, (nd / nv0) % nv1, dim == 3 ? nd / (nv0 * nv1) : 0};
+        int cl[3][2], cnt[3];
+        for (int a = 0; a < 3; ++a) {
+          cnt[a] = 0;
+          if (a >= dim) { cl[a][cnt[a]++] = 0; continue; }
+          const int v = idx[a];
+          if (v & 1) { cl[a][cnt[a]++] = v >> 1; continue; }
+          if ((v >> 1) - 1 >= 0) cl[a][cnt[a]++] = (v >> 1) - 1;
+          if ((v >> 1) < F.n[a]) cl[a][cnt[a]++] = v >> 1;
+        }
+        for (int z = 0; z < cnt[2]; ++z)
+          for (int y = 0; y < cnt[1]; ++y)
+            for (int x = 0; x < cnt[0]; ++x)
+              touch.push_back({cl[0][x] + (long long)F.n[0] * (cl[1][y] + (long long)F.n[1] * cl[2][z]), k});
+      }
+    std::sort(touch.begin(), touch.end());
+    touch.erase(std::unique(touch.begin(), touch.end()), touch.end());
+    for (size_t i = 0; i < touch.size();) {
+      size_t j = i;
+      while (j < touch.size() && touch[j].first == touch[i].first) ++j;
+      for (size_t a = i; a < j; ++a)
+        for (size_t b = i; b < j; ++b)
+          if (touch[a].second != touch[b].second) nb[touch[a].second].push_back(touch[b].second);
+      i = j;
+    }
+    for (auto& v : nb) {
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+  }
+  std::vector<int> color(ninc, -1);
+  int ncol = 0;
+  for (int k = 0; k < ninc; ++k) {
+    std::vector<char> used(ncol + 1, 0);
+    for (int a : nb[k]) {
+      if (color[a] >= 0) used[color[a]] = 1;
+      for (int b : nb[a])
+        if (b != k && color[b] >= 0) used[color[b]] = 1;
+    }
+    int col = 0;
+    while (used[col]) ++col;
+    color[k] = col;
+    ncol = std::max(ncol, col + 1);
+  }
+  std::vector<double> E((size_t)M * M, 0.0), yh(M), ch(M);
+  for (int col = 0; col < ncol; ++col)
+    for (int t = 0; t < nt; ++t) {
+      std::fill(yh.begin(), yh.end(), 0.0);
+      bool any = false;
+      for (int k = 0; k < ninc; ++k)
+        if (color[k] == col && c->hd_keep[k * nt + t]) { yh[k * nt + t] = 1.0; any = true; }
+      if (!any) continue;
+      CK(cudaMemcpyAsync(c->d_y, yh.data(), sizeof(double) * M, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemsetAsync(c->w, 0, sizeof(double) * c->nu, c->st));
+      CK(launch_defl_add<double>(c->defl, c->d_y, c->w, c->st));
+      CKS(apply_level_T<double>(c, c->L - 1, GS_OP_A, c->w, c->r, nullptr));
+      CK(launch_defl_dots<double>(c->defl, c->r, c->d_c, c->st));
+      CK(cudaMemcpyAsync(ch.data(), c->d_c, sizeof(double) * M, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      for (int l = 0; l < ninc; ++l) {
+        int src = color[l] == col ? l : -1;
+        for (int k : nb[l])
+          if (src < 0 && color[k] == col) src = k;
+        if (src < 0 || !c->hd_keep[src * nt + t]) continue;
+        for (int b = 0; b < nt; ++b)
+          if (c->hd_keep[l * nt + b]) E[(size_t)(l * nt + b) * M + (src * nt + t)] = ch[l * nt + b];
+      }
+    }
+  // invert E on the kept modes (Gauss-Jordan, partial pivoting), zero rows / columns elsewhere
+  std::vector<int> kept;
+  for (int q = 0; q < M; ++q)
+    if (c->hd_keep[q]) kept.push_back(q);
+  const int m = (int)kept.size();
+  std::vector<double> A((size_t)m * 2 * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j < m; ++j) A[(size_t)i * 2 * m + j] = E[(size_t)kept[i] * M + kept[j]];
+    A[(size_t)i * 2 * m + m + i] = 1.0;
+  }
+  for (int p = 0; p < m; ++p) {
+    int piv = p;
+    for (int i = p + 1; i < m; ++i)
+      if (std::fabs(A[(size_t)i * 2 * m + p]) > std::fabs(A[(size_t)piv * 2 * m + p])) piv = i;
+    if (!(std::fabs(A[(size_t)piv * 2 * m + p]) > 0.0)) return fail(GS_EINVAL, "deflation: singular Z^T A Z");
+    if (piv != p)
+      for (int j = 0; j < 2 * m; ++j) std::swap(A[(size_t)p * 2 * m + j], A[(size_t)piv * 2 * m + j]);
+    const double inv = 1.0 / A[(size_t)p * 2 * m + p];
+    for (int j = 0; j < 2 * m; ++j) A[(size_t)p * 2 * m + j] *= inv;
+    for (int i = 0; i < m; ++i) {
+      if (i == p) continue;
+      const double f = A[(size_t)i * 2 * m + p];
+      if (f == 0.0) continue;
+      for (int j = 0; j < 2 * m; ++j) A[(size_t)i * 2 * m + j] -= f * A[(size_t)p * 2 * m + j];
+    }
+  }
+  std::fill(E.begin(), E.end(), 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) E[(size_t)kept[i] * M + kept[j]] = A[(size_t)i * 2 * m + m + j];
+  CK(cudaMemcpyAsync(c->d_Einv, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return GS_OK;
+}
+
 // ---- resumable FGMRES for the batching engine (gs_slot.h) ---------------------------------------
 // Offsets in the context's scalar area dsc (4 (m + 4) doubles): h1 at 0, h2 at m + 4, the norm
 // at 2 (m + 4), the pressure-mean sum at 3 (m + 4), then |r|^2 and |b|^2.
@@ -1784,6 +2045,7 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
   if (c->opt.graphs == 0 && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) != cudaSuccess)
     c->cap_st = nullptr;  // graphs stay off
   s = setup(c);
+  if (s == GS_OK) s = setup_deflation(c);
   if (s != GS_OK) {
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
     cudaFreeHost(c->hpin);
@@ -1934,6 +2196,8 @@ gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
   static const int rows[kTileShapes2D] = {16, 17, 8};
   for (int l = 0; l < c->L && l < 16; ++l) out->tile_rows[l] = c->dim == 2 ? rows[c->lv[l].shape] : 0;
   out->saddle_tile_rows = c->dim == 2 ? rows[c->saddle_shape] : 0;
+  out->deflation_inclusions = c->defl_ninc;
+  out->deflation_modes = c->defl_m;
   return GS_OK;
 }
 

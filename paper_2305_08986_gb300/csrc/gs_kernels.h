@@ -202,4 +202,21 @@ cudaError_t launch_combine_lift(const double* Mf, const double* Kg, const double
                                 const uint8_t* vmask, const uint8_t* pmask, const Geom& geo,
                                 double* rhs, cudaStream_t st);
 
+// ---- rigid-body deflation of stiff inclusions (gs_defl.cu) ----
+struct DeflArgs {
+  Geom g;             // finest level
+  const int* nodes;   // unconstrained velocity nodes of every inclusion's cells, concatenated
+  const int* off;     // ninc + 1 offsets into nodes
+  const double* cen;  // per inclusion: centroid of all its cells' nodes (3 doubles)
+  int ninc;
+};
+// c[k * nt + t] = projection of r on mode t of inclusion k (nt = 3 in 2D, 6 in 3D)
+template <typename T>
+cudaError_t launch_defl_dots(const DeflArgs& d, const T* r, double* c, cudaStream_t st);
+// y = Einv c (M x M dense)
+cudaError_t launch_defl_gemv(const double* Einv, int M, const double* c, double* y, cudaStream_t st);
+// x += Z y
+template <typename T>
+cudaError_t launch_defl_add(const DeflArgs& d, const double* y, T* x, cudaStream_t st);
+
 }  // namespace gs

@@ -37,7 +37,8 @@ class GsOptions(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("mg_precision", ctypes.c_int), ("schur_degree", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("seed", ctypes.c_int), ("coarse_mode", ctypes.c_int),
                 ("schur_kind", ctypes.c_int), ("orth", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("plap_degree", ctypes.c_int), ("krylov_fp64", ctypes.c_int), ("tile_autotune", ctypes.c_int)]
+                ("plap_degree", ctypes.c_int), ("krylov_fp64", ctypes.c_int), ("tile_autotune", ctypes.c_int),
+                ("deflate", ctypes.c_int)]
 
 
 class GsInfo(ctypes.Structure):
@@ -48,7 +49,8 @@ class GsInfo(ctypes.Structure):
                 ("coarse_free", ctypes.c_int), ("footprint_bytes", ctypes.c_size_t),
                 ("kernel_launches", ctypes.c_longlong), ("schur_cc", ctypes.c_int),
                 ("pressure_coarse_free", ctypes.c_int), ("plambda_max", ctypes.c_double * 16),
-                ("tile_rows", ctypes.c_int * 16), ("saddle_tile_rows", ctypes.c_int)]
+                ("tile_rows", ctypes.c_int * 16), ("saddle_tile_rows", ctypes.c_int),
+                ("deflation_inclusions", ctypes.c_int), ("deflation_modes", ctypes.c_int)]
 
 
 class GsKernelStat(ctypes.Structure):
