@@ -514,6 +514,68 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------------------------------------------------
+# 3D spheres workload (64^3, 64 stiff spheres): deflated solve, FP32 vs FP64 multigrid, 3D A x
+# --------------------------------------------------------------------------------------------
+def run_spheres(args):
+    import torch
+    from paper_2305_08986_gb300 import build as gsbuild
+    gsbuild.build(verbose=False)
+    from paper_2305_08986_gb300 import gs, inputs
+    dev = torch.device("cuda", 0)
+    p = inputs.config_spheres(n=64, levels=5)
+    f = torch.tensor(p.f, device=dev)
+    g = torch.tensor(p.g, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    out = {"workload": "spheres 64^3 Q2-Q1 (6.71 M unknowns), 64 spheres eta 1e6 in 1, alpha 1e2, 5 MG levels, "
+                       "rigid-body deflation of the inclusions, FGMRES(200) FP64, rel-res 1e-8",
+           "l2": "flushed (256 MiB write) before every timed run"}
+    for prec in (32, 64):
+        s = gs.Solver.from_problem(p, device=dev, mg_precision=prec, deflate=1, restart=200, max_iter=2000)
+        b = torch.empty_like(f)
+        s.lift_rhs(f, g, b)
+        x = torch.zeros_like(b)
+        s.solve(b, x, tol=TOL, allow_noconv=True)  # warm-up (graph capture)
+        ts, its, rels = [], [], []
+        for _ in range(max(1, args.steps if prec == 32 else 1)):
+            x.zero_()
+            flush.fill_(1.0)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            it, rr, _ = s.solve(b, x, tol=TOL, allow_noconv=True)
+            e.record(st)
+            e.synchronize()
+            ts.append(a.elapsed_time(e))
+            its.append(it)
+            rels.append(rr)
+        inf = s.info()
+        key = "fp32_multigrid" if prec == 32 else "fp64_multigrid"
+        out[key] = {"time_to_solve_ms": statistics.median(ts), "iterations": its[-1], "rel_residual": max(rels),
+                    "unknowns": s.n_total, "deflation_inclusions": inf.deflation_inclusions,
+                    "deflation_modes": inf.deflation_modes}
+        if prec == 32:
+            for dt, name in ((torch.float32, "fp32"), (torch.float64, "fp64")):
+                xx = torch.randn(s.n_u, dtype=dt, device=dev)
+                yy = torch.empty_like(xx)
+                s.vmult_A(xx, yy)
+                tt = []
+                for _ in range(10):
+                    flush.fill_(2.0)
+                    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(st)
+                    s.vmult_A(xx, yy)
+                    e.record(st)
+                    e.synchronize()
+                    tt.append(a.elapsed_time(e))
+                t = statistics.median(tt) * 1e-3
+                out.setdefault("ax_gdofs", {})[name] = {"gdofs": s.n_u / t / 1e9, "us": t * 1e6}
+        s.close()
+        del s, b, x
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -524,8 +586,9 @@ def main():
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.01)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="channel", choices=["channel", "batched", "serving"],
-                    help="channel: the contract line; batched / serving: the engine workloads (extra lines)")
+    ap.add_argument("--workload", default="channel", choices=["channel", "batched", "serving", "spheres"],
+                    help="channel: the contract line; batched / serving: the engine workloads; spheres: the 3D "
+                         "64^3 inclusion workload (extra lines)")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=60)
     ap.add_argument("--rates", default="10,30,100,300,1000")
@@ -537,6 +600,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving" and args.impl == "gs":
         return run_serving(args)
+    if args.workload == "spheres" and args.impl == "gs":
+        return run_spheres(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
