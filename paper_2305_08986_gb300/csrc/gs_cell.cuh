@@ -215,6 +215,96 @@ __device__ __forceinline__ void cell_A3(const T (&x)[3][27], T (&y)[27], T eta, 
   }
 }
 
+// ---- 3D cell operators reading their input nodes from a shared-memory window ----------------------
+// x_a points to the cell's local node (0, 0, 0) of component a in a window with strides (1, s1, s2);
+// the first sweep over each input reads the window directly, so the inputs never sit in registers.
+template <class Op, int AX, typename T>
+__device__ __forceinline__ void sweep_w(const T* __restrict__ in, int s1, int s2, T* __restrict__ out) {
+  constexpr int O0 = AX == 0 ? Op::NOUT : 3;
+  constexpr int O1 = AX == 1 ? Op::NOUT : 3;
+  constexpr int L0 = AX == 0 ? 1 : 3;
+  constexpr int L1 = AX == 1 ? 1 : 3;
+  constexpr int L2 = AX == 2 ? 1 : 3;
+#pragma unroll
+  for (int k = 0; k < L2; ++k) {
+#pragma unroll
+    for (int j = 0; j < L1; ++j) {
+#pragma unroll
+      for (int i = 0; i < L0; ++i) {
+        T a[Op::NIN], o[Op::NOUT];
+#pragma unroll
+        for (int t = 0; t < Op::NIN; ++t) {
+          const int ii = AX == 0 ? t : i, jj = AX == 1 ? t : j, kk = AX == 2 ? t : k;
+          a[t] = in[ii + s1 * jj + s2 * kk];
+        }
+        Op::f(a, o);
+#pragma unroll
+        for (int t = 0; t < Op::NOUT; ++t) {
+          const int ii = AX == 0 ? t : i, jj = AX == 1 ? t : j, kk = AX == 2 ? t : k;
+          out[ii + O0 * (jj + O1 * kk)] = o[t];
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int COMP>
+__device__ __forceinline__ void cell_A3w(const T* x0, const T* x1, const T* x2, int s1, int s2, T (&y)[27], T eta,
+                                         const OpCoef<T>& c) {
+  const T* xc = COMP == 0 ? x0 : (COMP == 1 ? x1 : x2);
+  T a[27], k[27], b[27];
+  sweep_w<OpM, 2>(xc, s1, s2, a);
+  sweep_w<OpK, 2>(xc, s1, s2, k);
+  {
+    const T ckz = (COMP == 2 ? T(2) : T(1)) * eta * c.km[2];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) b[i] = c.mm * a[i] + ckz * k[i];
+  }
+  sweep<OpM, 1, 3, 3, 3, false>(b, k);
+  sweep<OpK, 1, 3, 3, 3, false>(a, b);
+  {
+    const T cky = (COMP == 1 ? T(2) : T(1)) * eta * c.km[1];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] += cky * b[i];
+  }
+  sweep<OpM, 1, 3, 3, 3, false>(a, b);
+  {
+    const T ckx = (COMP == 0 ? T(2) : T(1)) * eta * c.km[0];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) b[i] *= ckx;
+  }
+  sweep<OpM, 0, 3, 3, 3, false>(k, y);
+  sweep<OpK, 0, 3, 3, 3, true>(b, y);
+  if (COMP == 0) {
+    sweep_w<OpM, 2>(x1, s1, s2, a);
+    sweep<OpE, 1, 3, 3, 3, false>(a, k);
+    sweep_w<OpE, 2>(x2, s1, s2, a);
+    sweep<OpM, 1, 3, 3, 3, false>(a, b);
+    const T c1 = eta * c.ex[2], c2 = eta * c.ex[1];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
+    sweep<OpET, 0, 3, 3, 3, true>(k, y);
+  } else if (COMP == 1) {
+    sweep_w<OpM, 2>(x0, s1, s2, a);
+    sweep<OpE, 0, 3, 3, 3, false>(a, k);
+    sweep_w<OpE, 2>(x2, s1, s2, a);
+    sweep<OpM, 0, 3, 3, 3, false>(a, b);
+    const T c1 = eta * c.ex[2], c2 = eta * c.ex[0];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
+    sweep<OpET, 1, 3, 3, 3, true>(k, y);
+  } else {
+    sweep_w<OpM, 1>(x0, s1, s2, a);
+    sweep<OpE, 0, 3, 3, 3, false>(a, k);
+    sweep_w<OpE, 1>(x1, s1, s2, a);
+    sweep<OpM, 0, 3, 3, 3, false>(a, b);
+    const T c1 = eta * c.ex[1], c2 = eta * c.ex[0];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
+    sweep<OpET, 2, 3, 3, 3, true>(k, y);
+  }
+}
+
 // ---- divergence block B and its transpose -----------------------------------------------------
 // (B u)_q = - sum_b int psi_q d phi_j/dx_b u_jb :  -sum_b (G in direction b, N elsewhere) u_b
 template <typename T>
@@ -255,6 +345,26 @@ __device__ __forceinline__ void cell_B3(const T (&u)[3][27], T (&out)[8], const 
 #pragma unroll
   for (int i = 0; i < 12; ++i) s1[i] = c1 * s1[i] + c2 * s0[i];
   sweep<OpN, 0, 3, 2, 2, false>(s1, o);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) out[i] = -(c.bd[0] * out[i] + o[i]);
+}
+
+// (B u) of one 3D cell with the velocity read from a shared-memory window (sweeps of cell_B3)
+template <typename T>
+__device__ __forceinline__ void cell_B3w(const T* u0, const T* u1, const T* u2, int s1, int s2, T (&out)[8],
+                                         const OpCoef<T>& c) {
+  T t0[18], t1[18], s0[12], s1v[12], o[8];
+  sweep_w<OpN, 2>(u0, s1, s2, t0);        // (3,3,2)
+  sweep_w<OpN, 2>(u1, s1, s2, t1);
+  sweep<OpN, 1, 3, 3, 2, false>(t0, s0);  // (3,2,2)
+  sweep<OpG, 0, 3, 2, 2, false>(s0, out); // (2,2,2)
+  sweep<OpG, 1, 3, 3, 2, false>(t1, s1v);
+  sweep_w<OpG, 2>(u2, s1, s2, t0);
+  sweep<OpN, 1, 3, 3, 2, false>(t0, s0);
+  const T c1 = c.bd[1], c2 = c.bd[2];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) s1v[i] = c1 * s1v[i] + c2 * s0[i];
+  sweep<OpN, 0, 3, 2, 2, false>(s1v, o);
 #pragma unroll
   for (int i = 0; i < 8; ++i) out[i] = -(c.bd[0] * out[i] + o[i]);
 }

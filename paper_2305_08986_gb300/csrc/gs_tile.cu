@@ -264,12 +264,248 @@ __device__ __forceinline__ void tile_body(const TileArgs<T>& A, int bid) {
   }
 }
 
+// ---- 3D tile with a staged input window --------------------------------------------------------
+// The CTA copies the velocity nodes of all its evaluated cells (a W^3 window per component, W =
+// 2 TC0 + 1, with cp.async: zero fill outside the mesh and on constrained nodes) and, for B^T, the
+// pressure nodes (PW^3), then runs the parity-class phases of tile_body with every cell reading
+// its nodes from the window.  Outputs and epilogue as in tile_body.
+namespace {
+template <typename T>
+__device__ __forceinline__ void cp_async_3d(T* smem, const T* gmem, bool load) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(load ? 4 : 0));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(load ? 8 : 0));
+}
+}  // namespace
+
+template <int MODE, bool WA, bool WBT, bool WB>
+struct Smem3 {
+  using S = TileShape<3>;
+  using D = TileDims<3>;
+  static constexpr bool NEED_U = WA || WB, WU = WA || WBT;
+  static constexpr int W = 2 * S::TC0 + 1, WV = W * W * W;  // staged velocity window
+  static constexpr int PW = S::TC0 + 1, PWV = PW * PW * PW; // staged pressure window
+  static constexpr int SU = WU ? 3 * D::VSZ : 0;            // velocity outputs
+  static constexpr int SP = WB ? D::PSZ : 0;                // pressure outputs
+  static constexpr int SX = NEED_U ? 3 * WV : 0;
+  static constexpr int SPW = WBT ? PWV : 0;
+  static constexpr int TOTAL = SU + SP + SX + SPW;           // elements of T
+  static constexpr int FLAGS = NEED_U ? WV : 0;              // bytes
+};
+
+template <typename T, int MODE, bool WA, bool WBT, bool WB>
+__device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
+  using S = TileShape<3>;
+  using D = TileDims<3>;
+  using SM = Smem3<MODE, WA, WBT, WB>;
+  constexpr bool NEED_U = SM::NEED_U, WU = SM::WU;
+  constexpr int W = SM::W, WW = W * W, WV = SM::WV, PW = SM::PW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* sp = su + SM::SU;
+  T* sx = sp + SM::SP;
+  T* spw = sx + SM::SX;
+  uint8_t* sflag = reinterpret_cast<uint8_t*>(spw + SM::SPW);
+  const Geom& g = A.g;
+  const OpCoef<T>& c = A.c;
+  const bool raw = A.raw != 0;
+  const bool vmasked = !raw && g.vmask != nullptr;
+  const int tid = threadIdx.x;
+
+  int tile = bid;
+  const int t0 = tile % A.tiles[0];
+  tile /= A.tiles[0];
+  const int t1 = tile % A.tiles[1];
+  const int t2 = tile / A.tiles[1];
+  const int cs0 = t0 * (S::TC0 - 1), cs1 = t1 * (S::TC1 - 1), cs2 = t2 * (S::TC2 - 1);
+  const int ve0 = owned_v_ext(cs0, S::TC0 - 1, g.n[0]);
+  const int ve1 = owned_v_ext(cs1, S::TC1 - 1, g.n[1]);
+  const int ve2 = owned_v_ext(cs2, S::TC2 - 1, g.n[2]);
+  const int pe0 = owned_p_ext(cs0, S::TC0 - 1, g.n[0]);
+  const int pe1 = owned_p_ext(cs1, S::TC1 - 1, g.n[1]);
+  const int pe2 = owned_p_ext(cs2, S::TC2 - 1, g.n[2]);
+  const long long Nv = g.Nv;
+
+  // ---- stage the windows (all copies in flight together), zero the output tiles ----
+  if (NEED_U) {
+    const int I0 = 2 * (cs0 - 1), J0 = 2 * (cs1 - 1), K0 = 2 * (cs2 - 1);
+    for (int i = tid; i < WV; i += D::THREADS) {
+      const int a = i % W, b = (i / W) % W, k = i / WW;
+      const int I = I0 + a, J = J0 + b, K = K0 + k;
+      const bool inr = I >= 0 && I < g.nv[0] && J >= 0 && J < g.nv[1] && K >= 0 && K < g.nv[2];
+      const long long node = inr ? I + (long long)g.nv[0] * (J + (long long)g.nv[1] * K) : 0;
+      const bool fcon = !raw && inr && !vmasked && face_constrained(g, I, J, K);
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) cp_async_3d(sx + cc * WV + i, A.xu + cc * Nv + node, inr && !fcon);
+      sflag[i] = (vmasked && inr) ? g.vmask[node] : 0;
+    }
+  }
+  if (WBT) {
+    const int P0 = cs0 - 1, Q0 = cs1 - 1, R0 = cs2 - 1;
+    for (int i = tid; i < SM::PWV; i += D::THREADS) {
+      const int P = P0 + i % PW, Q = Q0 + (i / PW) % PW, R = R0 + i / (PW * PW);
+      const bool inr = P >= 0 && P < g.npn[0] && Q >= 0 && Q < g.npn[1] && R >= 0 && R < g.npn[2];
+      const long long q = inr ? P + (long long)g.npn[0] * (Q + (long long)g.npn[1] * R) : 0;
+      const bool con = inr && !raw && pnode_constrained(g, q);
+      cp_async_3d(spw + i, A.xp + q, inr && !con);
+    }
+  }
+  for (int i = tid; i < SM::SU + SM::SP; i += D::THREADS) su[i] = T(0);
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (NEED_U && vmasked) {
+    for (int i = tid; i < WV; i += D::THREADS)
+      if (sflag[i]) {
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) sx[cc * WV + i] = T(0);
+      }
+  }
+  __syncthreads();
+
+  const int comp = tid / D::NG;  // warp-uniform component
+  const int grp = tid % D::NG;
+  const int g0 = grp % S::G0;
+  const int g1 = (grp / S::G0) % S::G1;
+  const int g2 = grp / (S::G0 * S::G1);
+#pragma unroll 1
+  for (int ph = 0; ph < 8; ++ph) {
+    const int l0 = 2 * g0 + (ph & 1);
+    const int l1 = 2 * g1 + ((ph >> 1) & 1);
+    const int l2 = 2 * g2 + ((ph >> 2) & 1);
+    const int c0 = cs0 - 1 + l0, c1 = cs1 - 1 + l1, c2 = cs2 - 1 + l2;
+    bool active = c0 >= 0 && c0 < g.n[0] && c1 >= 0 && c1 < g.n[1] && c2 >= 0 && c2 < g.n[2];
+    long long cell = 0;
+    if (active) {
+      cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
+      if (cell_void(g, cell)) active = false;
+    }
+    if (active) {
+      const T eta = A.eta[cell] * c.eta_scale;
+      const T* x0 = sx + 2 * l0 + W * (2 * l1 + W * 2 * l2);
+      const T* x1 = x0 + WV;
+      const T* x2 = x0 + 2 * WV;
+      if (WU) {
+        T yl[27];
+        T pl[8];
+        if (WBT) {
+#pragma unroll
+          for (int lc = 0; lc < 2; ++lc)
+#pragma unroll
+            for (int lb = 0; lb < 2; ++lb)
+#pragma unroll
+              for (int la = 0; la < 2; ++la) pl[la + 2 * lb + 4 * lc] = spw[(l0 + la) + PW * ((l1 + lb) + PW * (l2 + lc))];
+        }
+        if (comp == 0) {
+          if (WA) cell_A3w<T, 0>(x0, x1, x2, W, WW, yl, eta, c);
+          if (WBT) cell_BT3<T, 0>(pl, yl, c, WA);
+        } else if (comp == 1) {
+          if (WA) cell_A3w<T, 1>(x0, x1, x2, W, WW, yl, eta, c);
+          if (WBT) cell_BT3<T, 1>(pl, yl, c, WA);
+        } else {
+          if (WA) cell_A3w<T, 2>(x0, x1, x2, W, WW, yl, eta, c);
+          if (WBT) cell_BT3<T, 2>(pl, yl, c, WA);
+        }
+        T* sc = su + comp * D::VSZ;
+#pragma unroll
+        for (int lc = 0; lc < 3; ++lc) {
+          const int i2 = 2 * (l2 - 1) + lc;
+          if (i2 < 0 || i2 >= ve2) continue;
+#pragma unroll
+          for (int lb = 0; lb < 3; ++lb) {
+            const int i1 = 2 * (l1 - 1) + lb;
+            if (i1 < 0 || i1 >= ve1) continue;
+#pragma unroll
+            for (int la = 0; la < 3; ++la) {
+              const int i0 = 2 * (l0 - 1) + la;
+              if (i0 < 0 || i0 >= ve0) continue;
+              sc[i0 + D::VE0 * (i1 + D::VE1 * i2)] += yl[la + 3 * lb + 9 * lc];
+            }
+          }
+        }
+      }
+      if (WB && comp == 0) {
+        T ob[8];
+        cell_B3w(x0, x1, x2, W, WW, ob, c);
+#pragma unroll
+        for (int lc = 0; lc < 2; ++lc) {
+          const int i2 = (l2 - 1) + lc;
+          if (i2 < 0 || i2 >= pe2) continue;
+#pragma unroll
+          for (int lb = 0; lb < 2; ++lb) {
+            const int i1 = (l1 - 1) + lb;
+            if (i1 < 0 || i1 >= pe1) continue;
+#pragma unroll
+            for (int la = 0; la < 2; ++la) {
+              const int i0 = (l0 - 1) + la;
+              if (i0 < 0 || i0 >= pe0) continue;
+              sp[i0 + D::PE0 * (i1 + D::PE1 * i2)] += ob[la + 2 * lb + 4 * lc];
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- owned velocity nodes: epilogue ----
+  if (WU) {
+    const int nown = ve0 * ve1 * ve2;
+    for (int i = tid; i < nown; i += D::THREADS) {
+      const int i0 = i % ve0;
+      const int i1 = (i / ve0) % ve1;
+      const int i2 = i / (ve0 * ve1);
+      const int I = 2 * cs0 + i0, J = 2 * cs1 + i1, K = 2 * cs2 + i2;
+      const long long node = I + (long long)g.nv[0] * (J + (long long)g.nv[1] * K);
+      const bool con = !raw && vnode_constrained(g, node, I, J, K);
+      const int s = i0 + D::VE0 * (i1 + D::VE1 * i2);
+      const int w = (i0 + 2) + W * ((i1 + 2) + W * (i2 + 2));  // the node in the staged window
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const long long gi = a * Nv + node;
+        const T ax = con ? (WA ? A.xu[gi] : T(0)) : su[a * D::VSZ + s];
+        if (MODE == TILE_APPLY) {
+          A.yu[gi] = ax;
+        } else if (MODE == TILE_RESID) {
+          A.yu[gi] = A.bu[gi] - ax;
+        } else {
+          const T r = A.bu[gi] - ax;
+          T dn = A.c2 * A.dinv[gi] * r;
+          if (A.use_d) dn += A.c1 * A.d[gi];
+          A.d[gi] = dn;
+          const T xin = (con || !NEED_U) ? A.xu[gi] : sx[a * WV + w];
+          A.xout[gi] = xin + dn;
+        }
+      }
+    }
+  }
+  if (WB) {
+    const int nown = pe0 * pe1 * pe2;
+    for (int i = tid; i < nown; i += D::THREADS) {
+      const int i0 = i % pe0;
+      const int i1 = (i / pe0) % pe1;
+      const int i2 = i / (pe0 * pe1);
+      const long long q = (cs0 + i0) + (long long)g.npn[0] * ((cs1 + i1) + (long long)g.npn[1] * (cs2 + i2));
+      const bool con = !raw && pnode_constrained(g, q);
+      const T bx = con ? (WBT ? A.xp[q] : T(0)) : sp[i0 + D::PE0 * (i1 + D::PE1 * i2)];
+      if (MODE == TILE_RESID)
+        A.yp[q] = A.bp[q] - bx;
+      else
+        A.yp[q] = bx;
+    }
+  }
+}
+
 template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
 struct TileK {
   using Args = TileArgs<T>;
   static constexpr int THREADS = TileDims<DIM>::THREADS, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int) {
-    tile_body<T, DIM, MODE, WA, WBT, WB>(a, blk);
+    if constexpr (DIM == 3)
+      tile3d_body<T, MODE, WA, WBT, WB>(a, blk);
+    else
+      tile_body<T, DIM, MODE, WA, WBT, WB>(a, blk);
   }
 };
 
@@ -280,7 +516,11 @@ static cudaError_t launch_one(TileArgs<T> a, cudaStream_t st) {
   a.tiles[0] = (a.g.n[0] + S::TC0 - 2) / (S::TC0 - 1);
   a.tiles[1] = (a.g.n[1] + S::TC1 - 2) / (S::TC1 - 1);
   a.tiles[2] = DIM == 3 ? (a.g.n[2] + S::TC2 - 2) / (S::TC2 - 1) : 1;
-  const size_t smem = sizeof(T) * (((WA || WBT) ? DIM * D::VSZ : 0) + (WB ? D::PSZ : 0));
+  size_t smem = sizeof(T) * (((WA || WBT) ? DIM * D::VSZ : 0) + (WB ? D::PSZ : 0));
+  if (DIM == 3) {
+    using SM = Smem3<MODE, WA, WBT, WB>;
+    smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
+  }
   const long long nblocks = (long long)a.tiles[0] * a.tiles[1] * a.tiles[2];
   return submit<TileK<T, DIM, MODE, WA, WBT, WB>>(a, nblocks, smem, st);
 }
