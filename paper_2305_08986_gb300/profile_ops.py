@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--coarse-mode", type=int, default=1)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--flush", type=int, default=1)
+    ap.add_argument("--tile-autotune", type=int, default=0,
+                    help="2D tile height: 0 autotuned, 1 / 2 / 3 forced 32 x 16 / 17 / 8 (gs_options.tile_autotune)")
     args = ap.parse_args()
 
     import torch
@@ -41,6 +43,7 @@ def main():
     for op in args.op.split(","):
         prec = 64 if op.endswith("64") else 32
         s = gs.Solver.from_problem(p, levels=args.levels, coarse_mode=args.coarse_mode, mg_precision=prec,
+                                   tile_autotune=args.tile_autotune,
                                    restart=2)
         dt = torch.float64 if prec == 64 else torch.float32
         nu = s.n_u
