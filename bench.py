@@ -100,7 +100,7 @@ class Clocks:
 # --------------------------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on a bounded sample
 # --------------------------------------------------------------------------------------------
-ORACLE_SAMPLE = dict(nx=160, ny=28, levels=3)
+ORACLE_SAMPLE = dict(nx=320, ny=56, levels=4)  # ~5 s of host work per solve
 
 
 def oracle_sample_run(steps: int, warmup: int):
@@ -341,7 +341,7 @@ def run_gpu(args, rank, world):
         cb = None
         if not args.skip_cpu_baseline and world == 1:
             try:
-                cb = cpu_baseline_entry(oracle_subprocess(1, 0))
+                cb = cpu_baseline_entry(oracle_subprocess(3, 0))
             except Exception as ex:  # the baseline must not break the GPU line
                 cb = {"value": None, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
         ts = sorted(times)
