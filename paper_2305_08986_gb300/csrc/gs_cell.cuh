@@ -216,10 +216,12 @@ __device__ __forceinline__ void cell_A3(const T (&x)[3][27], T (&y)[27], T eta, 
 }
 
 // ---- 3D cell operators reading their input nodes from a shared-memory window ----------------------
-// x_a points to the cell's local node (0, 0, 0) of component a in a window with strides (1, s1, s2);
-// the first sweep over each input reads the window directly, so the inputs never sit in registers.
+// x_a points to the cell's local node (0, 0, 0) of component a in the window; local node (i, j, k)
+// sits at x_a[i + ro[j] + po[k]] (row and plane offsets of the cell, which absorb any skew of the
+// window layout).  The first sweep over each input reads the window directly, so the inputs never
+// sit in registers.
 template <class Op, int AX, typename T>
-__device__ __forceinline__ void sweep_w(const T* __restrict__ in, int s1, int s2, T* __restrict__ out) {
+__device__ __forceinline__ void sweep_w(const T* __restrict__ in, const int* ro, const int* po, T* __restrict__ out) {
   constexpr int O0 = AX == 0 ? Op::NOUT : 3;
   constexpr int O1 = AX == 1 ? Op::NOUT : 3;
   constexpr int L0 = AX == 0 ? 1 : 3;
@@ -235,7 +237,7 @@ __device__ __forceinline__ void sweep_w(const T* __restrict__ in, int s1, int s2
 #pragma unroll
         for (int t = 0; t < Op::NIN; ++t) {
           const int ii = AX == 0 ? t : i, jj = AX == 1 ? t : j, kk = AX == 2 ? t : k;
-          a[t] = in[ii + s1 * jj + s2 * kk];
+          a[t] = in[ii + ro[jj] + po[kk]];
         }
         Op::f(a, o);
 #pragma unroll
@@ -249,12 +251,12 @@ __device__ __forceinline__ void sweep_w(const T* __restrict__ in, int s1, int s2
 }
 
 template <typename T, int COMP>
-__device__ __forceinline__ void cell_A3w(const T* x0, const T* x1, const T* x2, int s1, int s2, T (&y)[27], T eta,
-                                         const OpCoef<T>& c) {
+__device__ __forceinline__ void cell_A3w(const T* x0, const T* x1, const T* x2, const int* ro, const int* po,
+                                         T (&y)[27], T eta, const OpCoef<T>& c) {
   const T* xc = COMP == 0 ? x0 : (COMP == 1 ? x1 : x2);
   T a[27], k[27], b[27];
-  sweep_w<OpM, 2>(xc, s1, s2, a);
-  sweep_w<OpK, 2>(xc, s1, s2, k);
+  sweep_w<OpM, 2>(xc, ro, po, a);
+  sweep_w<OpK, 2>(xc, ro, po, k);
   {
     const T ckz = (COMP == 2 ? T(2) : T(1)) * eta * c.km[2];
 #pragma unroll
@@ -276,27 +278,27 @@ __device__ __forceinline__ void cell_A3w(const T* x0, const T* x1, const T* x2, 
   sweep<OpM, 0, 3, 3, 3, false>(k, y);
   sweep<OpK, 0, 3, 3, 3, true>(b, y);
   if (COMP == 0) {
-    sweep_w<OpM, 2>(x1, s1, s2, a);
+    sweep_w<OpM, 2>(x1, ro, po, a);
     sweep<OpE, 1, 3, 3, 3, false>(a, k);
-    sweep_w<OpE, 2>(x2, s1, s2, a);
+    sweep_w<OpE, 2>(x2, ro, po, a);
     sweep<OpM, 1, 3, 3, 3, false>(a, b);
     const T c1 = eta * c.ex[2], c2 = eta * c.ex[1];
 #pragma unroll
     for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
     sweep<OpET, 0, 3, 3, 3, true>(k, y);
   } else if (COMP == 1) {
-    sweep_w<OpM, 2>(x0, s1, s2, a);
+    sweep_w<OpM, 2>(x0, ro, po, a);
     sweep<OpE, 0, 3, 3, 3, false>(a, k);
-    sweep_w<OpE, 2>(x2, s1, s2, a);
+    sweep_w<OpE, 2>(x2, ro, po, a);
     sweep<OpM, 0, 3, 3, 3, false>(a, b);
     const T c1 = eta * c.ex[2], c2 = eta * c.ex[0];
 #pragma unroll
     for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
     sweep<OpET, 1, 3, 3, 3, true>(k, y);
   } else {
-    sweep_w<OpM, 1>(x0, s1, s2, a);
+    sweep_w<OpM, 1>(x0, ro, po, a);
     sweep<OpE, 0, 3, 3, 3, false>(a, k);
-    sweep_w<OpE, 1>(x1, s1, s2, a);
+    sweep_w<OpE, 1>(x1, ro, po, a);
     sweep<OpM, 0, 3, 3, 3, false>(a, b);
     const T c1 = eta * c.ex[1], c2 = eta * c.ex[0];
 #pragma unroll
@@ -349,17 +351,103 @@ __device__ __forceinline__ void cell_B3(const T (&u)[3][27], T (&out)[8], const 
   for (int i = 0; i < 8; ++i) out[i] = -(c.bd[0] * out[i] + o[i]);
 }
 
+// ---- 3D operator in a rotated frame: one code path for every output component ------------------
+// Local node (i, j, k) of the window sits at in[o0[i] + o1[j] + o2[k]]: the three offset tables map
+// the logical axes to any physical axes.  A thread computing output component a uses the frame
+// (a, a + 1, a + 2) (cyclic), rotated coefficients, and its own component as the logical x input,
+// so the component-0 expression of cell_A3w serves all three components (one instruction stream).
+template <class Op, int AX, typename T>
+__device__ __forceinline__ void sweep_p(const T* __restrict__ in, const int* o0, const int* o1, const int* o2,
+                                        T* __restrict__ out) {
+  constexpr int O0 = AX == 0 ? Op::NOUT : 3;
+  constexpr int O1 = AX == 1 ? Op::NOUT : 3;
+  constexpr int L0 = AX == 0 ? 1 : 3;
+  constexpr int L1 = AX == 1 ? 1 : 3;
+  constexpr int L2 = AX == 2 ? 1 : 3;
+#pragma unroll
+  for (int k = 0; k < L2; ++k) {
+#pragma unroll
+    for (int j = 0; j < L1; ++j) {
+#pragma unroll
+      for (int i = 0; i < L0; ++i) {
+        T a[Op::NIN], o[Op::NOUT];
+#pragma unroll
+        for (int t = 0; t < Op::NIN; ++t) {
+          const int ii = AX == 0 ? t : i, jj = AX == 1 ? t : j, kk = AX == 2 ? t : k;
+          a[t] = in[o0[ii] + o1[jj] + o2[kk]];
+        }
+        Op::f(a, o);
+#pragma unroll
+        for (int t = 0; t < Op::NOUT; ++t) {
+          const int ii = AX == 0 ? t : i, jj = AX == 1 ? t : j, kk = AX == 2 ? t : k;
+          out[ii + O0 * (jj + O1 * kk)] = o[t];
+        }
+      }
+    }
+  }
+}
+
+// y (logical layout, x fastest) = output component "logical x" of the cell operator; xc / x1 / x2:
+// the input components along logical x / y / z; km, ex: coefficients of the logical axes
+template <typename T>
+__device__ __forceinline__ void cell_A3p(const T* xc, const T* x1, const T* x2, const int* o0, const int* o1,
+                                         const int* o2, T (&y)[27], T eta, T mm, const T* km, const T* ex) {
+  T a[27], k[27], b[27];
+  sweep_p<OpM, 2>(xc, o0, o1, o2, a);
+  sweep_p<OpK, 2>(xc, o0, o1, o2, k);
+  {
+    const T ckz = eta * km[2];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) b[i] = mm * a[i] + ckz * k[i];
+  }
+  sweep<OpM, 1, 3, 3, 3, false>(b, k);
+  sweep<OpK, 1, 3, 3, 3, false>(a, b);
+  {
+    const T cky = eta * km[1];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) k[i] += cky * b[i];
+  }
+  sweep<OpM, 1, 3, 3, 3, false>(a, b);
+  {
+    const T ckx = T(2) * eta * km[0];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) b[i] *= ckx;
+  }
+  sweep<OpM, 0, 3, 3, 3, false>(k, y);
+  sweep<OpK, 0, 3, 3, 3, true>(b, y);
+  sweep_p<OpM, 2>(x1, o0, o1, o2, a);
+  sweep<OpE, 1, 3, 3, 3, false>(a, k);
+  sweep_p<OpE, 2>(x2, o0, o1, o2, a);
+  sweep<OpM, 1, 3, 3, 3, false>(a, b);
+  const T c1 = eta * ex[2], c2 = eta * ex[1];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
+  sweep<OpET, 0, 3, 3, 3, true>(k, y);
+}
+
+// B^T contribution to output component "logical x" in the rotated frame (cell_BT3<T, 0> with the
+// pressure nodes given in the logical frame and the output axis's coefficient bd_a)
+template <typename T>
+__device__ __forceinline__ void cell_BT3p(const T (&p)[8], T (&u)[27], T bd_a, bool acc) {
+  T a[12], b[18], v[27];
+  sweep<OpNT, 2, 2, 2, 2, false>(p, a);  // (2,2,3)
+  sweep<OpNT, 1, 2, 2, 3, false>(a, b);  // (2,3,3)
+  sweep<OpGT, 0, 2, 3, 3, false>(b, v);  // (3,3,3)
+#pragma unroll
+  for (int i = 0; i < 27; ++i) u[i] = (acc ? u[i] : T(0)) - bd_a * v[i];
+}
+
 // (B u) of one 3D cell with the velocity read from a shared-memory window (sweeps of cell_B3)
 template <typename T>
-__device__ __forceinline__ void cell_B3w(const T* u0, const T* u1, const T* u2, int s1, int s2, T (&out)[8],
-                                         const OpCoef<T>& c) {
+__device__ __forceinline__ void cell_B3w(const T* u0, const T* u1, const T* u2, const int* ro, const int* po,
+                                         T (&out)[8], const OpCoef<T>& c) {
   T t0[18], t1[18], s0[12], s1v[12], o[8];
-  sweep_w<OpN, 2>(u0, s1, s2, t0);        // (3,3,2)
-  sweep_w<OpN, 2>(u1, s1, s2, t1);
+  sweep_w<OpN, 2>(u0, ro, po, t0);        // (3,3,2)
+  sweep_w<OpN, 2>(u1, ro, po, t1);
   sweep<OpN, 1, 3, 3, 2, false>(t0, s0);  // (3,2,2)
   sweep<OpG, 0, 3, 2, 2, false>(s0, out); // (2,2,2)
   sweep<OpG, 1, 3, 3, 2, false>(t1, s1v);
-  sweep_w<OpG, 2>(u2, s1, s2, t0);
+  sweep_w<OpG, 2>(u2, ro, po, t0);
   sweep<OpN, 1, 3, 3, 2, false>(t0, s0);
   const T c1 = c.bd[1], c2 = c.bd[2];
 #pragma unroll

@@ -280,16 +280,33 @@ __device__ __forceinline__ void cp_async_3d(T* smem, const T* gmem, bool load) {
 }
 }  // namespace
 
-template <int MODE, bool WA, bool WBT, bool WB>
+// Skewed layouts of the window and of the output tile: node (i0, i1, i2) of a W- (or VE-) wide
+// box sits at i0 + W i1 + P i2 + A (i1 >> 2) + B (i2 >> 2), with the plane pitch P >= W^2 +
+// A ((W - 1) >> 2) so that planes never overlap.  In one parity phase the cells of a warp start 4
+// nodes apart along each axis, so in the plain layout all their accesses fall on 8 of the 32 banks
+// (7-way conflicts); these (A, B, P) make them conflict-free (FP64 output tile: at most 2-way),
+// found by enumerating every phase and local node over injective layouts.
+template <typename T>
+struct Skew3 {
+  static constexpr bool F = sizeof(T) == 4;
+  static constexpr int WA = 1, WB = 0, WP = F ? 300 : 294;       // window (W = 17)
+  static constexpr int OA = 1, OB = F ? 0 : 3, OP = F ? 236 : 229;  // output tile (VE = 15)
+};
+
+template <typename T, int MODE, bool WA, bool WBT, bool WB>
 struct Smem3 {
   using S = TileShape<3>;
   using D = TileDims<3>;
+  using K = Skew3<T>;
   static constexpr bool NEED_U = WA || WB, WU = WA || WBT;
   static constexpr int W = 2 * S::TC0 + 1, WV = W * W * W;  // staged velocity window
+  static constexpr int WVA = (W - 1) * (1 + W + K::WP) + (K::WA + K::WB) * ((W - 1) >> 2) + 1;  // skewed window
+  static constexpr int VSZA = (D::VE0 - 1) + (D::VE1 - 1) * D::VE0 + (D::VE2 - 1) * K::OP +
+                              K::OA * ((D::VE1 - 1) >> 2) + K::OB * ((D::VE2 - 1) >> 2) + 1;
   static constexpr int PW = S::TC0 + 1, PWV = PW * PW * PW; // staged pressure window
-  static constexpr int SU = WU ? 3 * D::VSZ : 0;            // velocity outputs
+  static constexpr int SU = WU ? 3 * VSZA : 0;              // velocity outputs
   static constexpr int SP = WB ? D::PSZ : 0;                // pressure outputs
-  static constexpr int SX = NEED_U ? 3 * WV : 0;
+  static constexpr int SX = NEED_U ? 3 * WVA : 0;
   static constexpr int SPW = WBT ? PWV : 0;
   static constexpr int TOTAL = SU + SP + SX + SPW;           // elements of T
   static constexpr int FLAGS = NEED_U ? WV : 0;              // bytes
@@ -299,9 +316,14 @@ template <typename T, int MODE, bool WA, bool WBT, bool WB>
 __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   using S = TileShape<3>;
   using D = TileDims<3>;
-  using SM = Smem3<MODE, WA, WBT, WB>;
+  using SM = Smem3<T, MODE, WA, WBT, WB>;
+  using K = Skew3<T>;
   constexpr bool NEED_U = SM::NEED_U, WU = SM::WU;
-  constexpr int W = SM::W, WW = W * W, WV = SM::WV, PW = SM::PW;
+  constexpr int W = SM::W, WW = W * W, WV = SM::WV, WVA = SM::WVA, VSZA = SM::VSZA, PW = SM::PW;
+  auto widx = [](int i0, int i1, int i2) { return i0 + W * i1 + K::WP * i2 + K::WA * (i1 >> 2) + K::WB * (i2 >> 2); };
+  auto oidx = [](int i0, int i1, int i2) {
+    return i0 + D::VE0 * i1 + K::OP * i2 + K::OA * (i1 >> 2) + K::OB * (i2 >> 2);
+  };
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);
   T* sp = su + SM::SU;
@@ -337,8 +359,9 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
       const bool inr = I >= 0 && I < g.nv[0] && J >= 0 && J < g.nv[1] && K >= 0 && K < g.nv[2];
       const long long node = inr ? I + (long long)g.nv[0] * (J + (long long)g.nv[1] * K) : 0;
       const bool fcon = !raw && inr && !vmasked && face_constrained(g, I, J, K);
+      const int wi = widx(a, b, k);
 #pragma unroll
-      for (int cc = 0; cc < 3; ++cc) cp_async_3d(sx + cc * WV + i, A.xu + cc * Nv + node, inr && !fcon);
+      for (int cc = 0; cc < 3; ++cc) cp_async_3d(sx + cc * WVA + wi, A.xu + cc * Nv + node, inr && !fcon);
       sflag[i] = (vmasked && inr) ? g.vmask[node] : 0;
     }
   }
@@ -358,8 +381,9 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   if (NEED_U && vmasked) {
     for (int i = tid; i < WV; i += D::THREADS)
       if (sflag[i]) {
+        const int wi = widx(i % W, (i / W) % W, i / WW);
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) sx[cc * WV + i] = T(0);
+        for (int cc = 0; cc < 3; ++cc) sx[cc * WVA + wi] = T(0);
       }
   }
   __syncthreads();
@@ -369,12 +393,26 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   const int g0 = grp % S::G0;
   const int g1 = (grp / S::G0) % S::G1;
   const int g2 = grp / (S::G0 * S::G1);
+  // rotated frame of this thread's output component: logical axes (x, y, z) = physical
+  // (comp, comp + 1, comp + 2) mod 3; coefficients and input components follow the rotation
+  const int pa[3] = {comp, comp == 2 ? 0 : comp + 1, comp == 0 ? 2 : comp - 1};
+  T km_l[3], ex_l[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    km_l[q] = c.km[pa[q]];
+    ex_l[q] = c.ex[pa[q]];
+  }
+  const T bd_a = c.bd[comp];
+  const int vext[3] = {ve0, ve1, ve2};
+  auto fw = [](int ax, int i) { return ax == 0 ? i : (ax == 1 ? W * i + K::WA * (i >> 2) : K::WP * i + K::WB * (i >> 2)); };
+  auto fo = [](int ax, int i) {
+    return ax == 0 ? i : (ax == 1 ? D::VE0 * i + K::OA * (i >> 2) : K::OP * i + K::OB * (i >> 2));
+  };
+  auto fp = [](int ax, int i) { return ax == 0 ? i : (ax == 1 ? PW * i : PW * PW * i); };
 #pragma unroll 1
   for (int ph = 0; ph < 8; ++ph) {
-    const int l0 = 2 * g0 + (ph & 1);
-    const int l1 = 2 * g1 + ((ph >> 1) & 1);
-    const int l2 = 2 * g2 + ((ph >> 2) & 1);
-    const int c0 = cs0 - 1 + l0, c1 = cs1 - 1 + l1, c2 = cs2 - 1 + l2;
+    const int lp[3] = {2 * g0 + (ph & 1), 2 * g1 + ((ph >> 1) & 1), 2 * g2 + ((ph >> 2) & 1)};
+    const int c0 = cs0 - 1 + lp[0], c1 = cs1 - 1 + lp[1], c2 = cs2 - 1 + lp[2];
     bool active = c0 >= 0 && c0 < g.n[0] && c1 >= 0 && c1 < g.n[1] && c2 >= 0 && c2 < g.n[2];
     long long cell = 0;
     if (active) {
@@ -383,62 +421,66 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
     }
     if (active) {
       const T eta = A.eta[cell] * c.eta_scale;
-      const T* x0 = sx + 2 * l0 + W * (2 * l1 + W * 2 * l2);
-      const T* x1 = x0 + WV;
-      const T* x2 = x0 + 2 * WV;
+      int o[3][3];  // window offsets of the cell's nodes along each logical axis
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) o[q][t] = fw(pa[q], 2 * lp[pa[q]] + t);
       if (WU) {
         T yl[27];
-        T pl[8];
+        if (WA)
+          cell_A3p(sx + pa[0] * WVA, sx + pa[1] * WVA, sx + pa[2] * WVA, o[0], o[1], o[2], yl, eta, c.mm, km_l, ex_l);
         if (WBT) {
+          T pl[8];  // the cell's pressure nodes in the logical frame
 #pragma unroll
           for (int lc = 0; lc < 2; ++lc)
 #pragma unroll
             for (int lb = 0; lb < 2; ++lb)
 #pragma unroll
-              for (int la = 0; la < 2; ++la) pl[la + 2 * lb + 4 * lc] = spw[(l0 + la) + PW * ((l1 + lb) + PW * (l2 + lc))];
+              for (int la = 0; la < 2; ++la)
+                pl[la + 2 * lb + 4 * lc] =
+                    spw[fp(pa[0], lp[pa[0]] + la) + fp(pa[1], lp[pa[1]] + lb) + fp(pa[2], lp[pa[2]] + lc)];
+          cell_BT3p(pl, yl, bd_a, WA);
         }
-        if (comp == 0) {
-          if (WA) cell_A3w<T, 0>(x0, x1, x2, W, WW, yl, eta, c);
-          if (WBT) cell_BT3<T, 0>(pl, yl, c, WA);
-        } else if (comp == 1) {
-          if (WA) cell_A3w<T, 1>(x0, x1, x2, W, WW, yl, eta, c);
-          if (WBT) cell_BT3<T, 1>(pl, yl, c, WA);
-        } else {
-          if (WA) cell_A3w<T, 2>(x0, x1, x2, W, WW, yl, eta, c);
-          if (WBT) cell_BT3<T, 2>(pl, yl, c, WA);
-        }
-        T* sc = su + comp * D::VSZ;
+        int oo[3][3];
+        bool ok[3][3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const int i = 2 * (lp[pa[q]] - 1) + t;
+            ok[q][t] = i >= 0 && i < vext[pa[q]];
+            oo[q][t] = fo(pa[q], i);
+          }
+        T* sc = su + comp * VSZA;
 #pragma unroll
         for (int lc = 0; lc < 3; ++lc) {
-          const int i2 = 2 * (l2 - 1) + lc;
-          if (i2 < 0 || i2 >= ve2) continue;
+          if (!ok[2][lc]) continue;
 #pragma unroll
           for (int lb = 0; lb < 3; ++lb) {
-            const int i1 = 2 * (l1 - 1) + lb;
-            if (i1 < 0 || i1 >= ve1) continue;
+            if (!ok[1][lb]) continue;
 #pragma unroll
             for (int la = 0; la < 3; ++la) {
-              const int i0 = 2 * (l0 - 1) + la;
-              if (i0 < 0 || i0 >= ve0) continue;
-              sc[i0 + D::VE0 * (i1 + D::VE1 * i2)] += yl[la + 3 * lb + 9 * lc];
+              if (!ok[0][la]) continue;
+              sc[oo[0][la] + oo[1][lb] + oo[2][lc]] += yl[la + 3 * lb + 9 * lc];
             }
           }
         }
       }
-      if (WB && comp == 0) {
+      if (WB && comp == 0) {  // comp 0: the rotated frame is the physical one
         T ob[8];
-        cell_B3w(x0, x1, x2, W, WW, ob, c);
+        cell_B3w(sx + 2 * lp[0], sx + WVA + 2 * lp[0], sx + 2 * WVA + 2 * lp[0], o[1], o[2], ob, c);
 #pragma unroll
         for (int lc = 0; lc < 2; ++lc) {
-          const int i2 = (l2 - 1) + lc;
+          const int i2 = (lp[2] - 1) + lc;
           if (i2 < 0 || i2 >= pe2) continue;
 #pragma unroll
           for (int lb = 0; lb < 2; ++lb) {
-            const int i1 = (l1 - 1) + lb;
+            const int i1 = (lp[1] - 1) + lb;
             if (i1 < 0 || i1 >= pe1) continue;
 #pragma unroll
             for (int la = 0; la < 2; ++la) {
-              const int i0 = (l0 - 1) + la;
+              const int i0 = (lp[0] - 1) + la;
               if (i0 < 0 || i0 >= pe0) continue;
               sp[i0 + D::PE0 * (i1 + D::PE1 * i2)] += ob[la + 2 * lb + 4 * lc];
             }
@@ -459,12 +501,12 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
       const int I = 2 * cs0 + i0, J = 2 * cs1 + i1, K = 2 * cs2 + i2;
       const long long node = I + (long long)g.nv[0] * (J + (long long)g.nv[1] * K);
       const bool con = !raw && vnode_constrained(g, node, I, J, K);
-      const int s = i0 + D::VE0 * (i1 + D::VE1 * i2);
-      const int w = (i0 + 2) + W * ((i1 + 2) + W * (i2 + 2));  // the node in the staged window
+      const int s = oidx(i0, i1, i2);
+      const int w = widx(i0 + 2, i1 + 2, i2 + 2);  // the node in the staged window
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const long long gi = a * Nv + node;
-        const T ax = con ? (WA ? A.xu[gi] : T(0)) : su[a * D::VSZ + s];
+        const T ax = con ? (WA ? A.xu[gi] : T(0)) : su[a * VSZA + s];
         if (MODE == TILE_APPLY) {
           A.yu[gi] = ax;
         } else if (MODE == TILE_RESID) {
@@ -474,7 +516,7 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
           T dn = A.c2 * A.dinv[gi] * r;
           if (A.use_d) dn += A.c1 * A.d[gi];
           A.d[gi] = dn;
-          const T xin = (con || !NEED_U) ? A.xu[gi] : sx[a * WV + w];
+          const T xin = (con || !NEED_U) ? A.xu[gi] : sx[a * WVA + w];
           A.xout[gi] = xin + dn;
         }
       }
@@ -518,7 +560,7 @@ static cudaError_t launch_one(TileArgs<T> a, cudaStream_t st) {
   a.tiles[2] = DIM == 3 ? (a.g.n[2] + S::TC2 - 2) / (S::TC2 - 1) : 1;
   size_t smem = sizeof(T) * (((WA || WBT) ? DIM * D::VSZ : 0) + (WB ? D::PSZ : 0));
   if (DIM == 3) {
-    using SM = Smem3<MODE, WA, WBT, WB>;
+    using SM = Smem3<T, MODE, WA, WBT, WB>;
     smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
   }
   const long long nblocks = (long long)a.tiles[0] * a.tiles[1] * a.tiles[2];
