@@ -18,6 +18,8 @@ Sec. 4; it stops on the Euclidean norm of the residual.  Readings taken here:
   iteration count of degree 4 on the channel workload);
 * preconditioner (block upper triangular):  z_p = -S^{-1} r_p,
   z_u = V-cycle(r_u - B^T z_p); on constrained entries (identity rows of K) z = r;
+  precond="monolithic": Sec. 4's own preconditioner, n V-cycles of saddle-point multigrid with
+  the block smoother K_j (monolithic.py), constrained entries and pressure mean as above;
 * pure-Dirichlet problems have the constant pressure in the kernel; the mean of
   the free pressure entries is subtracted from every preconditioned vector and
   from the final iterate.
@@ -124,13 +126,26 @@ class StokesOracle:
     """FP64 reference solver for one problem: assembled system + velocity hierarchy."""
 
     def __init__(self, mesh: Mesh, eta, alpha, levels, degree=4, seed=0, restart=50, schur="auto",
-                 coarse="cholesky", orth="cgs2", pdegree=2, deflate=False):
+                 coarse="cholesky", orth="cgs2", pdegree=2, deflate=False, precond="block", smooth=2, cycles=1):
         self.mesh = mesh
         self.alpha = float(alpha)
         self.sys = System(mesh, eta, alpha)
         self.levels = levels
         self.restart = restart
         self.orth = orth
+        # precond = "block": the block-triangular variant below; "monolithic": Sec. 4's saddle-point
+        # multigrid with the block smoother K_j (monolithic.py), m = smooth, n = cycles
+        self.mono = None
+        if precond == "monolithic":
+            from .monolithic import MonolithicHierarchy
+            self.mono = MonolithicHierarchy(mesh, eta, alpha, levels, degree=degree, smooth=smooth, cycles=cycles,
+                                            seed=seed, coarse="chebyshev" if coarse == "chebyshev" else "dense")
+            self.mg = self.mono.vel
+            self.schur = "mono"
+            self.pmg = None
+            self.nullspace = mesh.has_pressure_nullspace()
+            self.free_p = ~self.sys.p_constrained
+            return
         self.mg = Hierarchy(mesh, eta, alpha, levels, degree=degree, seed=seed, coarse=coarse, deflate=deflate)
         # Schur approximation: "mass" = M_p(1/eta) only; "cc" = Cahouet-Chabard
         # M_p(1/eta)^{-1} + alpha K_p^{-1}; "auto" = cc when alpha > 0
@@ -154,6 +169,10 @@ class StokesOracle:
         return self.sys.K @ x
 
     def precond(self, r):
+        if self.mono is not None:
+            z = self.mono.apply(r)
+            z[self.sys.constrained] = r[self.sys.constrained]
+            return self.project(z)
         n_u = self.mesh.n_u
         ru, rp = r[:n_u], r[n_u:]
         zp = -schur_apply_inv(self.sys.Mpw, rp, self.mesh.dim)
