@@ -125,6 +125,21 @@ typedef struct {            /* zero-initialised = defaults */
                                   eta_min, at most 256; Z = their rigid motions on their cells'
                                   nodes; the finest level adds Z (Z^T A Z)^-1 Z^T r to its coarse
                                   correction.  0: off (default). */
+  int precond_kind;         /* 0: block upper-triangular preconditioner (velocity V-cycle + Schur
+                                  approximation, the default);
+                               1: the preconditioner of Sec. 4 itself: mono_cycles V-cycles of
+                                  multigrid on the whole saddle matrix M_j = [A_j B_j^T; B_j 0] with
+                                  mono_smooth steps of the block smoother of Eq. "smoother",
+                                  K_j = [Ahat B^T; B B Ahat^{-1} B^T - Shat]^{-1}, before and after
+                                  the coarse correction; Ahat^{-1} = Cheb(A, diag A, cheb_degree);
+                                  Shat^{-1} = ChebMINRES(1, 1): one MINRES step on
+                                  S = B Ahat^{-1} B^T preconditioned by one Chebyshev step with
+                                  diag(B diag(A)^{-1} B^T) (n_S = k_S = 1, Table
+                                  NS-solver-parameters-1); dense saddle solve on level 0 (or, with
+                                  coarse_mode = 1, mono_smooth smoothing steps).  smooth_steps,
+                                  schur_*, plap_degree and deflate do not apply. */
+  int mono_smooth;          /* m of precond_kind 1; 0 -> 2 (Table NS-solver-parameters-1) */
+  int mono_cycles;          /* n of precond_kind 1; 0 -> 1 */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */
@@ -192,11 +207,20 @@ typedef enum {
   GS_OP_PLAP = 13,       /* y = K_p,l x          (pressure Laplacian of level l)     */
   GS_OP_PLAP_INV = 14,   /* y = V_p(x) ~ K_p^{-1} x (finest level, MG precision)    */
   GS_OP_PRESTRICT = 15,  /* y (level l-1) = P_p,l^T x (Q1 restriction)               */
-  GS_OP_PPROLONGATE = 16 /* y (level l) += P_p,l x (level l-1) (Q1 interpolation)    */
+  GS_OP_PPROLONGATE = 16,/* y (level l) += P_p,l x (level l-1) (Q1 interpolation)    */
+  /* precond_kind = 1 only; "level vector" = [u (d N_v,l) | p (N_p,l)] of level l, MG precision: */
+  GS_OP_SCHUR_DIAG = 17, /* y = diag(B_l diag(A_l)^{-1} B_l^T) (pressure, N_p,l; 0 on
+                            constrained nodes), the ChebMINRES preconditioner of Sec. 4 */
+  GS_OP_SADDLE_SMOOTH = 18, /* y = K_j x: one block-smoother application (Eq. "smoother") to
+                            the level vector x; level >= 1 (or level 0 with coarse_mode 1) */
+  GS_OP_SADDLE_VCYCLE = 19, /* y = V_l(x): one saddle-point V-cycle on level l, level vectors */
+  GS_OP_SADDLE_COARSE = 20  /* y = M_0^{-1} x: dense saddle solve of level 0 (FP64 level
+                            vectors, free unknowns; constrained entries of y are 0) */
 } gs_op;
 
 /* Apply one operator of level `level` (0 = coarsest).  prec = 64: x, y, aux are double*;
- * prec = 32: float* (GS_OP_COARSE and GS_OP_PRECOND take double* always).  Enqueue only. */
+ * prec = 32: float* (GS_OP_COARSE, GS_OP_SADDLE_COARSE and GS_OP_PRECOND take double* always;
+ * the saddle operators 17-19 need prec = the context's mg_precision).  Enqueue only. */
 gs_status gs_apply_level(gs_ctx* ctx, int level, gs_op op, int prec, const void* x, void* y,
                          const void* aux);
 
@@ -222,6 +246,8 @@ typedef struct {
   int saddle_tile_rows;    /* 2D: the same for the FP64 saddle operator (0 in 3D) */
   int deflation_inclusions;/* stiff inclusions in the deflation space (option deflate) */
   int deflation_modes;     /* rigid modes kept (modes vanishing on unconstrained nodes dropped) */
+  int precond_kind;        /* the preconditioner in use (gs_options.precond_kind) */
+  int saddle_coarse_free;  /* unknowns of the dense coarse saddle solve (precond_kind 1) */
 } gs_info;
 gs_status gs_get_info(const gs_ctx* ctx, gs_info* out);
 

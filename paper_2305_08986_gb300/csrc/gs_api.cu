@@ -41,10 +41,11 @@ gs_status fail(gs_status s, const std::string& why) {
   } while (0)
 
 // kernel classes reported by gs_profile_read
-enum KClass { K_SADDLE64 = 0, K_CHEB, K_RESID, K_BT, K_TRANSFER, K_COARSE, K_SCHUR, K_DOTS, K_AXPY, K_VEC, K_NCLASS };
+enum KClass { K_SADDLE64 = 0, K_CHEB, K_RESID, K_BT, K_TRANSFER, K_COARSE, K_SCHUR, K_DOTS, K_AXPY, K_VEC, K_MONO,
+              K_NCLASS };
 const char* const kclass_name[K_NCLASS] = {"saddle_fp64", "cheb_step", "residual_A", "gradient_BT", "transfer",
                                            "coarse_solve", "schur_step", "gram_schmidt_dots", "krylov_axpy",
-                                           "vector_misc"};
+                                           "vector_misc", "saddle_smoother"};
 
 struct Arena {
   char* base = nullptr;
@@ -80,6 +81,12 @@ struct Level {
   double plam_hi = 0.0;
   double pkc[3] = {0, 0, 0};
   int shape = 0;  // 2D tile height variant of this level's multigrid kernels (TileArgs::shape)
+  // saddle-point multigrid (precond_kind 1): level vectors [u | p] (iterate ms, right-hand side
+  // mr, residual mres), the first Ahat solve mwt, Schur work vectors mz / mq, the inverse Schur
+  // diagonal dsinv and the pressure constraint mask mpm (all zero without obstacle cells)
+  void *ms = nullptr, *mr = nullptr, *mres = nullptr, *mwt = nullptr, *mz = nullptr, *mq = nullptr;
+  void* dsinv = nullptr;
+  uint8_t* mpm = nullptr;
 };
 
 // State of the resumable FGMRES that the batching engine drives (see gs_slot.h).
@@ -130,6 +137,16 @@ struct gs_ctx {
   double* Ainv = nullptr;
   int* cfree = nullptr;
   double *ctmp = nullptr, *gjrow = nullptr, *gjcol = nullptr;
+  // saddle-point multigrid (precond_kind 1): dense coarse saddle inverse on its free unknowns
+  // (velocity free entries, then free pressure entries offset by d N_v of level 0), MINRES sums,
+  // finest-level right-hand side and cycle sum (mono_cycles > 1)
+  bool mono = false;
+  int nmf = 0;
+  std::vector<int> hmfree;
+  double* MAinv = nullptr;
+  int* mcfree = nullptr;
+  double *mctmp = nullptr, *msc = nullptr;
+  void *mb = nullptr, *mx = nullptr;
   // Krylov (FP64)
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
   double* vcur = nullptr;  // current basis vector as double (input of the preconditioner)
@@ -217,6 +234,9 @@ gs_options normalize_opts(const gs_options* o) {
   r.krylov_fp64 = r.krylov_fp64 == 1 ? 1 : 0;
   r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 3) ? r.tile_autotune : 0;
   r.deflate = r.deflate == 1 ? 1 : 0;
+  r.precond_kind = r.precond_kind == 1 ? 1 : 0;
+  r.mono_smooth = opt_or(r.mono_smooth, 2);
+  r.mono_cycles = opt_or(r.mono_cycles, 1);
   return r;
 }
 
@@ -349,7 +369,7 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
               for (int la = 0; la < 3; ++la)
                 lv.hvmask[(2 * i + la) + (long long)nv0 * ((2 * j + lb) + (long long)nv1 * (dim == 3 ? 2 * k + lc : 0))] = 1;
         }
-    if (l == L - 1) {
+    {
       const int np0 = lv.n[0] + 1, np1 = lv.n[1] + 1;
       lv.hpmask.assign(lv.Np, 1);
       for (int k = 0; k < lv.n[2]; ++k)
@@ -393,6 +413,17 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
     c->n_pfree = 0;
     for (auto v : Fl.hpmask) c->n_pfree += v ? 0 : 1;
   }
+  // saddle-point multigrid: free unknowns of the dense coarse saddle solve
+  c->mono = c->opt.precond_kind == 1;
+  c->hmfree.clear();
+  if (c->mono && c->opt.deflate == 1) return fail(GS_EINVAL, "deflation applies to the block-triangular preconditioner");
+  if (c->mono && c->opt.coarse_mode != 1) {
+    c->hmfree = c->hfree;
+    for (long long q = 0; q < C0.Np; ++q)
+      if (!(C0.has_void && C0.hpmask[q])) c->hmfree.push_back((int)(C0.nu + q));
+  }
+  c->nmf = (int)c->hmfree.size();
+  if ((long long)c->nmf * c->nmf > (1LL << 31)) return fail(GS_EINVAL, "coarsest level too large for the dense saddle solve");
   // pressure Laplacian of the Cahouet-Chabard term: p = 0 on pressure nodes touched by no active
   // cell and on faces without a velocity Dirichlet condition; pure Neumann if every face is
   // Dirichlet (then singular with the constant in its kernel)
@@ -548,7 +579,7 @@ void layout(gs_ctx* c, Arena& ar) {
     if (lv.has_void) {
       lv.cvoid = ar.take<uint8_t>(lv.Nc);
       lv.vmask = ar.take<uint8_t>(lv.Nv);
-      if (l == c->L - 1) lv.pmask = ar.take<uint8_t>(lv.Np);
+      lv.pmask = ar.take<uint8_t>(lv.Np);
     }
     lv.xA = takeT(lv.nu);
     lv.xB = takeT(lv.nu);
@@ -565,7 +596,7 @@ void layout(gs_ctx* c, Arena& ar) {
   c->Ainv = ar.take<double>((long long)c->nf * c->nf);
   c->cfree = ar.take<int>(c->nf);
   c->ctmp = ar.take<double>(c->nf);
-  const int gjn = c->nf > c->nfp ? c->nf : c->nfp;
+  const int gjn = std::max(c->nf, std::max(c->nfp, c->nmf));
   c->gjrow = ar.take<double>(gjn);
   c->gjcol = ar.take<double>(gjn);
   if (c->cc_alloc) {
@@ -581,6 +612,27 @@ void layout(gs_ctx* c, Arena& ar) {
     c->PAinv = ar.take<double>((long long)c->nfp * c->nfp);
     c->pcfree = ar.take<int>(c->nfp);
     c->pctmp = ar.take<double>(c->nfp);
+  }
+  if (c->mono) {
+    for (int l = 0; l < c->L; ++l) {
+      Level& lv = c->lv[l];
+      lv.ms = takeT(lv.nu + lv.Np);
+      lv.mr = takeT(lv.nu + lv.Np);
+      lv.mres = takeT(lv.nu + lv.Np);
+      lv.mwt = takeT(lv.nu);
+      lv.mz = takeT(lv.Np);
+      lv.mq = takeT(lv.Np);
+      lv.dsinv = takeT(lv.Np);
+      lv.mpm = ar.take<uint8_t>(lv.Np);
+    }
+    c->MAinv = ar.take<double>((long long)c->nmf * c->nmf);
+    c->mcfree = ar.take<int>(c->nmf);
+    c->mctmp = ar.take<double>(c->nmf);
+    c->msc = ar.take<double>(2);
+    if (c->opt.mono_cycles > 1) {
+      c->mb = takeT(F.nu + F.Np);
+      c->mx = takeT(F.nu + F.Np);
+    }
   }
   if (c->opt.deflate == 1) {  // capacity: every node, kDeflMaxInclusions inclusions
     const int Mmax = kDeflMaxInclusions * (c->dim == 2 ? 3 : 6);
@@ -874,6 +926,11 @@ gs_status setup_T(gs_ctx* c) {
   for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(lanczos<T>(c, l));
   const Level& F = c->lv[c->L - 1];
   CK(launch_pdiag<T>(F.g, coef<T>(F), etap<T>(F), (T*)c->p_dinv, c->st));
+  if (c->mono)
+    for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) {
+      Level& lv = c->lv[l];
+      CK(launch_schur_diag<T>(lv.g, lv.c64, (const T*)lv.dinv, (T*)lv.dsinv, 1, c->st));
+    }
   if (c->cc) {
     for (int l = 0; l < c->L; ++l) {
       Level& lv = c->lv[l];
@@ -924,6 +981,57 @@ void assemble_coarse_plap(gs_ctx* c, std::vector<double>& A) {
       }
   if (c->psingular)
     for (size_t q = 0; q < A.size(); ++q) A[q] += 1.0 / nf;
+}
+
+// host assembly of the dense coarse saddle matrix M_0 = [A_0 B_0^T; B_0 0] on its free unknowns
+// (the velocity block of assemble_coarse, then the free pressure nodes); B's cell entries are
+// -bd[a] (Gi in direction a) (Ni elsewhere) with Ni, Gi the 1D Q1 x Q2 integrals times 6.  With
+// every face Dirichlet the pressure block gets -1 1^T / n_p,free (the constant pressure is in
+// the kernel of M_0; mean-free solutions of consistent systems do not change).
+void assemble_coarse_saddle(gs_ctx* c, std::vector<double>& M) {
+  const Level& lv = c->lv[0];
+  const int dim = c->dim, nf = c->nf, n = c->nmf;
+  std::vector<double> A;
+  assemble_coarse(c, A);
+  M.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < nf; ++i)
+    for (int j = 0; j < nf; ++j) M[(size_t)i * n + j] = A[(size_t)i * nf + j];
+  std::vector<int> umap(lv.nu, -1), pmap(lv.Np, -1);
+  for (int i = 0; i < nf; ++i) umap[c->hfree[i]] = i;
+  for (int i = nf; i < n; ++i) pmap[c->hmfree[i] - lv.nu] = i;
+  static const int Ni[2][3] = {{1, 2, 0}, {0, 2, 1}};
+  static const int Gi[2][3] = {{-5, 4, 1}, {-1, -4, 5}};
+  const int nv0 = 2 * lv.n[0] + 1, nv1 = 2 * lv.n[1] + 1;
+  const int np0 = lv.n[0] + 1, np1 = lv.n[1] + 1;
+  const int nbp = dim == 2 ? 4 : 8, nbv = dim == 2 ? 9 : 27;
+  for (int k = 0; k < lv.n[2]; ++k)
+    for (int j = 0; j < lv.n[1]; ++j)
+      for (int i = 0; i < lv.n[0]; ++i) {
+        const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+        if (lv.has_void && lv.hvoid[cc]) continue;
+        for (int pq = 0; pq < nbp; ++pq) {
+          const int qi[3] = {pq & 1, (pq >> 1) & 1, pq >> 2};
+          const int row = pmap[(i + qi[0]) + (long long)np0 * ((j + qi[1]) + (long long)np1 * (dim == 3 ? k + qi[2] : 0))];
+          if (row < 0) continue;
+          for (int pv = 0; pv < nbv; ++pv) {
+            const int vi[3] = {pv % 3, (pv / 3) % 3, pv / 9};
+            const long long node =
+                (2 * i + vi[0]) + (long long)nv0 * ((2 * j + vi[1]) + (long long)nv1 * (dim == 3 ? 2 * k + vi[2] : 0));
+            for (int a = 0; a < dim; ++a) {
+              const int col = umap[a * lv.Nv + node];
+              if (col < 0) continue;
+              double prod = 1.0;
+              for (int b = 0; b < dim; ++b) prod *= (b == a) ? Gi[qi[b]][vi[b]] : Ni[qi[b]][vi[b]];
+              const double v = -lv.c64.bd[a] * prod;
+              M[(size_t)row * n + col] += v;
+              M[(size_t)col * n + row] += v;
+            }
+          }
+        }
+      }
+  if (c->nullspace && n > nf)
+    for (int r = nf; r < n; ++r)
+      for (int q = nf; q < n; ++q) M[(size_t)r * n + q] -= 1.0 / (n - nf);
 }
 
 // FP64 saddle operator on the finest level: y = K x (APPLY) or y = b - K x (RESID)
@@ -1018,6 +1126,28 @@ gs_status setup(gs_ctx* c) {
     for (int l = 0; l < c->L; ++l) {
       Level& lv = c->lv[l];
       CK(cudaMemcpyAsync(lv.pcmask, lv.hpc.data(), lv.Np, cudaMemcpyHostToDevice, c->st));
+    }
+  }
+  if (c->mono) {
+    for (int l = 0; l < c->L; ++l) {
+      Level& lv = c->lv[l];
+      if (lv.has_void)
+        CK(cudaMemcpyAsync(lv.mpm, lv.hpmask.data(), lv.Np, cudaMemcpyHostToDevice, c->st));
+      else
+        CK(cudaMemsetAsync(lv.mpm, 0, lv.Np, c->st));
+    }
+    if (c->nmf > 0) {
+      std::vector<double> M;
+      assemble_coarse_saddle(c, M);
+      CK(cudaMemcpyAsync(c->MAinv, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(c->mcfree, c->hmfree.data(), sizeof(int) * c->nmf, cudaMemcpyHostToDevice, c->st));
+      // Gauss-Jordan without pivoting: the velocity pivots are those of the SPD A_0, the pressure
+      // pivots those of the negative definite -(B_0 A_0^{-1} B_0^T (+ 1 1^T / n))
+      for (int k = 0; k < c->nmf; ++k) {
+        CK(launch_gj_save(c->MAinv, c->nmf, k, c->gjrow, c->gjcol, c->st));
+        CK(launch_gj_update(c->MAinv, c->nmf, k, c->gjrow, c->gjcol, c->st));
+      }
+      CK(cudaStreamSynchronize(c->st));
     }
   }
   if (c->cc && c->nfp > 0) {
@@ -1188,6 +1318,127 @@ gs_status plap_inverse(gs_ctx* c, const T* r) {
   return GS_OK;
 }
 
+// ---- saddle-point multigrid with the block smoother K_j (Sec. 4, Eq. "smoother") ---------------
+// Level l: iterate [u | p] in lv.ms, right-hand side in lv.mr (MG precision).  One smoothing step
+// x <- x + K_j (b - M_j x) applies K_j by its block factorisation
+//   w~ = Ahat^{-1} r_u,   w_p = Shat^{-1} (B w~ - r_p),   w_u = w~ - Ahat^{-1} B^T w_p,
+// Ahat^{-1} = Cheb(A, diag A, k_A) from zero, Shat^{-1} = one MINRES step on S = B Ahat^{-1} B^T
+// with preconditioner P = D_S^{-1} = diag(B diag(A)^{-1} B^T)^{-1}: w_p = a z, z = P (B w~ - r_p),
+// a = (z . S z) / ((S z) . P (S z)).  S z = B y with y = Ahat^{-1} B^T z, and Ahat^{-1} is linear,
+// so Ahat^{-1} B^T w_p = a y: the second Ahat solve of the smoother is the one inside S z.  The
+// kernels run on -z, -y and -S z (from r_p - B w~), which leaves a and the update unchanged.
+template <typename T>
+gs_status mono_smooth_step(gs_ctx* c, int l, bool zero) {
+  Level& lv = c->lv[l];
+  T* x = (T*)lv.ms;
+  const T* b = (const T*)lv.mr;
+  const T* ru = b;
+  const T* rp = b + lv.nu;
+  if (!zero) {  // r = b - M_j x
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = x; a.xp = x + lv.nu; a.bu = b; a.bp = b + lv.nu;
+    a.yu = (T*)lv.mres; a.yp = (T*)lv.mres + lv.nu;
+    KL(K_MONO, launch_tile<T>(c->dim, TILE_RESID, OPS_A | OPS_BT | OPS_B, a, c->st));
+    ru = (const T*)lv.mres;
+    rp = ru + lv.nu;
+  }
+  CKS(cheb<T>(c, l, ru, true));  // w~ = Ahat^{-1} r_u in lv.xA
+  std::swap(lv.xA, lv.mwt);
+  const T* wt = (const T*)lv.mwt;
+  T* q = (T*)lv.mq;
+  T* z = (T*)lv.mz;
+  {  // q = r_p - B w~
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = wt; a.bp = rp; a.yp = q;
+    KL(K_MONO, launch_tile<T>(c->dim, TILE_RESID, OPS_B, a, c->st));
+  }
+  KL(K_MONO, launch_mul<T>((const T*)lv.dsinv, q, z, lv.Np, c->st));  // z = P q
+  {  // lv.b = B^T z
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xp = z; a.yu = (T*)lv.b;
+    KL(K_MONO, launch_tile<T>(c->dim, TILE_APPLY, OPS_BT, a, c->st));
+  }
+  CKS(cheb<T>(c, l, (const T*)lv.b, true));  // y = Ahat^{-1} B^T z in lv.xA
+  {  // q = B y = S z
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = (const T*)lv.xA; a.yp = q;
+    KL(K_MONO, launch_tile<T>(c->dim, TILE_APPLY, OPS_B, a, c->st));
+  }
+  KL(K_MONO, launch_schur_dots<T>(z, q, (const T*)lv.dsinv, lv.Np, c->part, c->G, c->msc, c->st));
+  KL(K_MONO, launch_mono_update<T>(x, x + lv.nu, wt, (const T*)lv.xA, z, c->msc, lv.nu, lv.Np, zero ? 1 : 0, c->st));
+  return GS_OK;
+}
+
+// one saddle-point V-cycle on level l: right-hand side lv.mr -> iterate lv.ms.  m smoothing steps
+// (the first from zero), residual, Q2 / Q1 restriction, recursion, interpolation, m steps; level
+// 0: dense saddle solve (coarse_mode 0) or m smoothing steps from zero.
+template <typename T>
+gs_status mono_vcycle(gs_ctx* c, int l) {
+  Level& lv = c->lv[l];
+  if (l == 0 && c->opt.coarse_mode != 1) {
+    KL(K_COARSE, launch_coarse_solve<T>(c->MAinv, c->mcfree, c->nmf, (const T*)lv.mr, (T*)lv.ms, lv.nu + lv.Np,
+                                        c->mctmp, c->st));
+    return GS_OK;
+  }
+  const int m = c->opt.mono_smooth;
+  for (int s = 0; s < m; ++s) CKS(mono_smooth_step<T>(c, l, s == 0));
+  if (l == 0) return GS_OK;
+  T* res = (T*)lv.mres;
+  {
+    TileArgs<T> a = tile_args<T>(lv);
+    a.xu = (const T*)lv.ms; a.xp = (const T*)lv.ms + lv.nu; a.bu = (const T*)lv.mr; a.bp = (const T*)lv.mr + lv.nu;
+    a.yu = res; a.yp = res + lv.nu;
+    KL(K_MONO, launch_tile<T>(c->dim, TILE_RESID, OPS_A | OPS_BT | OPS_B, a, c->st));
+  }
+  Level& cl = c->lv[l - 1];
+  KL(K_TRANSFER, launch_restrict<T>(lv.g, cl.g, res, (T*)cl.mr, c->st));
+  KL(K_TRANSFER, launch_p_restrict<T>(lv.g, cl.g, lv.mpm, cl.mpm, res + lv.nu, (T*)cl.mr + cl.nu, c->st));
+  CKS(mono_vcycle<T>(c, l - 1));
+  KL(K_TRANSFER, launch_prolong_add<T>(lv.g, cl.g, (const T*)cl.ms, (T*)lv.ms, c->st));
+  KL(K_TRANSFER, launch_p_prolong_add<T>(lv.g, cl.g, lv.mpm, cl.mpm, (const T*)cl.ms + cl.nu, (T*)lv.ms + lv.nu,
+                                         c->st));
+  for (int s = 0; s < m; ++s) CKS(mono_smooth_step<T>(c, l, false));
+  return GS_OK;
+}
+
+// n cycles on the finest level from zero, x <- x + V(b - M x): input F.mr, output mono_out()
+template <typename T>
+gs_status mono_body(gs_ctx* c) {
+  Level& F = c->lv[c->L - 1];
+  const long long n = F.nu + F.Np;
+  const int cycles = c->opt.mono_cycles;
+  if (cycles > 1) KL(K_VEC, launch_cast<T, T>((const T*)F.mr, (T*)c->mb, n, (T)1, c->st));
+  CKS(mono_vcycle<T>(c, c->L - 1));
+  if (cycles > 1) {
+    KL(K_VEC, launch_cast<T, T>((const T*)F.ms, (T*)c->mx, n, (T)1, c->st));
+    for (int i = 1; i < cycles; ++i) {
+      TileArgs<T> a = tile_args<T>(F);
+      a.xu = (const T*)c->mx; a.xp = (const T*)c->mx + F.nu; a.bu = (const T*)c->mb; a.bp = (const T*)c->mb + F.nu;
+      a.yu = (T*)F.mr; a.yp = (T*)F.mr + F.nu;
+      KL(K_MONO, launch_tile<T>(c->dim, TILE_RESID, OPS_A | OPS_BT | OPS_B, a, c->st));
+      CKS(mono_vcycle<T>(c, c->L - 1));
+      KL(K_VEC, launch_add<T>((const T*)F.ms, (T*)c->mx, n, c->st));
+    }
+  }
+  return GS_OK;
+}
+
+// staging of the preconditioner body: where its input is cast to and its result is left
+void* body_in_u(gs_ctx* c) { return c->mono ? c->lv[c->L - 1].mr : c->lv[c->L - 1].d; }
+void* body_in_p(gs_ctx* c) {
+  const size_t S = c->fp32 ? 4 : 8;
+  return c->mono ? (void*)((char*)c->lv[c->L - 1].mr + S * c->nu) : c->p_b;
+}
+const void* body_out_u(gs_ctx* c) {
+  if (!c->mono) return c->lv[c->L - 1].xA;
+  return c->opt.mono_cycles > 1 ? c->mx : c->lv[c->L - 1].ms;
+}
+const void* body_out_p(gs_ctx* c) {
+  if (!c->mono) return c->p_xB;
+  const size_t S = c->fp32 ? 4 : 8;
+  return (const char*)body_out_u(c) + S * c->nu;
+}
+
 gs_status project_pressure(gs_ctx* c, double* x) {
   if (!c->nullspace) return GS_OK;
   const Level& F = c->lv[c->L - 1];
@@ -1205,6 +1456,7 @@ gs_status project_pressure(gs_ctx* c, double* x) {
 // once into a CUDA graph and replayed.
 template <typename T>
 gs_status precond_body(gs_ctx* c) {
+  if (c->mono) return mono_body<T>(c);
   Level& F = c->lv[c->L - 1];
   CKS(schur_inv<T>(c, (const T*)c->p_b));
   if (c->cc) {
@@ -1246,8 +1498,8 @@ gs_status capture_precond(gs_ctx* c) {
     return fail(GS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   // the graph leaves its results where the captured launches put them
-  c->g_zu = c->lv[c->L - 1].xA;
-  c->g_zp = c->p_xB;
+  c->g_zu = body_out_u(c);
+  c->g_zp = body_out_p(c);
   return GS_OK;
 }
 
@@ -1256,8 +1508,8 @@ gs_status capture_precond(gs_ctx* c) {
 template <typename T>
 gs_status precond_T(gs_ctx* c, const double* v, double* z) {
   Level& F = c->lv[c->L - 1];
-  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)c->p_b, F.Np, (T)1, c->st));
-  KL(K_VEC, launch_cast<double, T>(v, (T*)F.d, F.nu, (T)1, c->st));
+  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)body_in_p(c), F.Np, (T)1, c->st));
+  KL(K_VEC, launch_cast<double, T>(v, (T*)body_in_u(c), F.nu, (T)1, c->st));
   const void* zu;
   const void* zp;
   const bool use_graph = c->opt.graphs == 0 && !c->prof && c->cap_st != nullptr;
@@ -1271,8 +1523,8 @@ gs_status precond_T(gs_ctx* c, const double* v, double* z) {
     const long long before = launches_total();
     CKS(precond_body<T>(c));
     c->pgraph_kernels = (int)(launches_total() - before);
-    zu = F.xA;
-    zp = c->p_xB;
+    zu = body_out_u(c);
+    zp = body_out_p(c);
   }
   c->pcalls++;
   KL(K_VEC, launch_cast<T, double>((const T*)zu, z, F.nu, 1.0, c->st));
@@ -1552,6 +1804,25 @@ gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, co
         CK(launch_p_prolong_add<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, x, y, c->st));
       return GS_OK;
     }
+    case GS_OP_SCHUR_DIAG:
+    case GS_OP_SADDLE_SMOOTH:
+    case GS_OP_SADDLE_VCYCLE: {
+      if (!c->mono || !mgprec) return fail(GS_EINVAL, "saddle-point multigrid operators: precond_kind 1, MG precision");
+      if (op == GS_OP_SCHUR_DIAG) {
+        CK(launch_schur_diag<T>(lv.g, lv.c64, (const T*)lv.dinv, y, 0, c->st));
+        return GS_OK;
+      }
+      if (op == GS_OP_SADDLE_SMOOTH && l == 0 && c->opt.coarse_mode != 1)
+        return fail(GS_EINVAL, "block smoother: level >= 1 (or level 0 with coarse_mode 1)");
+      const long long n = lv.nu + lv.Np;
+      CK(launch_cast<T, T>(x, (T*)lv.mr, n, (T)1, c->st));
+      if (op == GS_OP_SADDLE_SMOOTH)
+        CKS(mono_smooth_step<T>(c, l, true));
+      else
+        CKS(mono_vcycle<T>(c, l));
+      CK(launch_cast<T, T>((const T*)lv.ms, y, n, (T)1, c->st));
+      return GS_OK;
+    }
     case GS_OP_SCHUR_INV: {
       if (!finest || !mgprec) return fail(GS_EINVAL, "Schur inverse: finest level, MG precision");
       CKS(schur_inv<T>(c, x));
@@ -1719,8 +1990,8 @@ gs_status sl_norm2(gs_ctx* c, const double* v, double* dst) {
 template <typename T>
 gs_status sl_cast_in(gs_ctx* c, const double* v) {
   Level& F = c->lv[c->L - 1];
-  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)c->p_b, F.Np, (T)1, c->st));
-  KL(K_VEC, launch_cast<double, T>(v, (T*)F.d, F.nu, (T)1, c->st));
+  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)body_in_p(c), F.Np, (T)1, c->st));
+  KL(K_VEC, launch_cast<double, T>(v, (T*)body_in_u(c), F.nu, (T)1, c->st));
   return GS_OK;
 }
 template <typename T>
@@ -1775,8 +2046,8 @@ const Recorder* slot_body(gs_ctx* c, gs_status* st) {
   *st = c->fp32 ? precond_body<float>(c) : precond_body<double>(c);
   current_recorder() = prev;
   if (*st != GS_OK) return nullptr;
-  k.zu = c->lv[c->L - 1].xA;  // where the recorded launches leave z_u and z_p
-  k.zp = c->p_xB;
+  k.zu = body_out_u(c);  // where the recorded launches leave z_u and z_p
+  k.zp = body_out_p(c);
   k.body_ok = true;
   return &k.body;
 }
@@ -2162,6 +2433,14 @@ gs_status gs_apply_level(gs_ctx* c, int level, gs_op op, int prec, const void* x
     CK(launch_coarse_solve<double>(c->Ainv, c->cfree, c->nf, (const double*)x, (double*)y, c->lv[0].nu, c->ctmp, c->st));
     return GS_OK;
   }
+  if (op == GS_OP_SADDLE_COARSE) {
+    if (level != 0 || !x || !c->mono || c->nmf == 0)
+      return fail(GS_EINVAL, "coarse saddle solve: level 0, x required, precond_kind 1, coarse_mode 0");
+    const Level& c0 = c->lv[0];
+    CK(launch_coarse_solve<double>(c->MAinv, c->mcfree, c->nmf, (const double*)x, (double*)y, c0.nu + c0.Np, c->mctmp,
+                                   c->st));
+    return GS_OK;
+  }
   if (op == GS_OP_PRECOND) {
     if (level != c->L - 1 || !x) return fail(GS_EINVAL, "preconditioner: finest level, x required");
     return precond(c, (const double*)x, (double*)y);
@@ -2198,6 +2477,8 @@ gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
   out->saddle_tile_rows = c->dim == 2 ? rows[c->saddle_shape] : 0;
   out->deflation_inclusions = c->defl_ninc;
   out->deflation_modes = c->defl_m;
+  out->precond_kind = c->mono ? 1 : 0;
+  out->saddle_coarse_free = c->nmf;
   return GS_OK;
 }
 

@@ -219,4 +219,24 @@ cudaError_t launch_defl_gemv(const double* Einv, int M, const double* c, double*
 template <typename T>
 cudaError_t launch_defl_add(const DeflArgs& d, const double* y, T* x, cudaStream_t st);
 
+
+// ---- saddle-point multigrid with the block smoother K_j (gs_mono.cu) ----
+// out[q] = diag(B diag(A)^{-1} B^T)[q] from the inverse velocity diagonal dinv (invert = 0), or its
+// inverse with 0 where it vanishes (invert = 1); constrained pressure nodes give 0
+template <typename T>
+cudaError_t launch_schur_diag(const Geom& g, const OpCoef<double>& c, const T* dinv, T* out, int invert,
+                              cudaStream_t st);
+// out[0] = z . q, out[1] = q . (dsinv q) (G blocks of partial sums in part, fixed reduction order)
+template <typename T>
+cudaError_t launch_schur_dots(const T* z, const T* q, const T* dsinv, long long n, double* part, int G, double* out,
+                              cudaStream_t st);
+// a = s[0] / s[1] (0 if s[1] = 0); x_u (+)= wt + a y, x_p (+)= -a z  (zero: overwrite)
+template <typename T>
+cudaError_t launch_mono_update(T* xu, T* xp, const T* wt, const T* y, const T* z, const double* s, long long nu,
+                               long long np, int zero, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mul(const T* a, const T* b, T* out, long long n, cudaStream_t st);  // out = a * b
+template <typename T>
+cudaError_t launch_add(const T* x, T* y, long long n, cudaStream_t st);  // y += x
+
 }  // namespace gs

@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ENOCONV, GS_EBREAKDOWN, GS_ETIMEOUT, GS_EBUSY = range(8)
 (OP_A, OP_RESIDUAL_A, OP_DIAG_A, OP_SMOOTH, OP_RESTRICT, OP_PROLONGATE, OP_B, OP_BT,
  OP_SCHUR_MASS, OP_SCHUR_INV, OP_COARSE, OP_PRECOND, OP_A_RAW, OP_PLAP, OP_PLAP_INV, OP_PRESTRICT,
- OP_PPROLONGATE) = range(17)
+ OP_PPROLONGATE, OP_SCHUR_DIAG, OP_SADDLE_SMOOTH, OP_SADDLE_VCYCLE, OP_SADDLE_COARSE) = range(21)
 
 
 class GsMesh(ctypes.Structure):
@@ -38,7 +38,8 @@ class GsOptions(ctypes.Structure):
                 ("lanczos_steps", ctypes.c_int), ("seed", ctypes.c_int), ("coarse_mode", ctypes.c_int),
                 ("schur_kind", ctypes.c_int), ("orth", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("plap_degree", ctypes.c_int), ("krylov_fp64", ctypes.c_int), ("tile_autotune", ctypes.c_int),
-                ("deflate", ctypes.c_int)]
+                ("deflate", ctypes.c_int), ("precond_kind", ctypes.c_int), ("mono_smooth", ctypes.c_int),
+                ("mono_cycles", ctypes.c_int)]
 
 
 class GsInfo(ctypes.Structure):
@@ -50,7 +51,8 @@ class GsInfo(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("schur_cc", ctypes.c_int),
                 ("pressure_coarse_free", ctypes.c_int), ("plambda_max", ctypes.c_double * 16),
                 ("tile_rows", ctypes.c_int * 16), ("saddle_tile_rows", ctypes.c_int),
-                ("deflation_inclusions", ctypes.c_int), ("deflation_modes", ctypes.c_int)]
+                ("deflation_inclusions", ctypes.c_int), ("deflation_modes", ctypes.c_int),
+                ("precond_kind", ctypes.c_int), ("saddle_coarse_free", ctypes.c_int)]
 
 
 class GsKernelStat(ctypes.Structure):
