@@ -186,6 +186,33 @@ def config_channel(nx: int = 1280, ny: int = 224, levels: int = 6, eta_solid: fl
                    void.astype(np.uint8), f, g)
 
 
+def config_extension(nx: int = 1280, ny: int = 224, levels: int = 6, tip: float = 0.02,
+                     point_a=(0.6, 0.2)) -> Problem:
+    """Mesh-extension problem on the channel geometry (Eq. "extenstion"): the solid (square obstacle
+    [0.15,0.25]^2 and bar [0.25,0.60]x[0.19,0.21]) is made of obstacle cells whose nodes carry the
+    solid displacement u_s; every outer face is Dirichlet (u = 0).  u_s: the obstacle is at rest,
+    the bar bends, u_y = tip ((x - 0.25) / 0.35)^2.  eta per cell = mu_A / 2 with
+    mu_A = 1 + 50 exp(-800 ((x - A_x)^2 + (y - A_y)^2)) (Eq. "mu_distribution") at the cell
+    centroid, A = point_a (the bar's tip); alpha = 0; no load."""
+    dim = 2
+    nn = (nx, ny)
+    L = (CHANNEL_L, CHANNEL_H)
+    c = cell_centroids(dim, nn, L)
+    obst = (c[:, 0] >= 0.15) & (c[:, 0] <= 0.25) & (c[:, 1] >= 0.15) & (c[:, 1] <= 0.25)
+    bar = (c[:, 0] >= 0.25) & (c[:, 0] <= 0.60) & (c[:, 1] >= 0.19) & (c[:, 1] <= 0.21)
+    solid = obst | bar
+    mu = 1.0 + 50.0 * np.exp(-800.0 * ((c[:, 0] - point_a[0]) ** 2 + (c[:, 1] - point_a[1]) ** 2))
+    xv = vnode_coords(dim, nn, L)
+    s = np.clip((xv[:, 0] - 0.25) / 0.35, 0.0, None)
+    on_bar = ((xv[:, 0] >= 0.25) & (xv[:, 0] <= 0.60 + 1e-12) & (xv[:, 1] >= 0.19 - 1e-12)
+              & (xv[:, 1] <= 0.21 + 1e-12))
+    uy = np.where(on_bar, tip * s * s, 0.0)
+    g = _full(dim, nn, np.stack([np.zeros_like(uy), uy], axis=1))
+    f = _full(dim, nn)
+    return Problem(f"extension{nx}x{ny}", dim, nn, L, levels, 0.5 * mu, 0.0, all_faces(dim),
+                   solid.astype(np.uint8), f, g)
+
+
 # --------------------------------------------------------------------------
 # config 3: 3D cube with random stiff spheres
 # --------------------------------------------------------------------------
