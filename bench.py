@@ -540,6 +540,47 @@ def run_serving(args):
 
 
 # --------------------------------------------------------------------------------------------
+# mesh-extension workload (Eq. "extenstion"): CG + velocity V-cycle on the channel, tol 1e-6
+# --------------------------------------------------------------------------------------------
+def run_extension(args):
+    import torch
+    from paper_2305_08986_gb300 import build as gsbuild
+    gsbuild.build(verbose=False)
+    from paper_2305_08986_gb300 import gs, inputs
+    dev = torch.device("cuda", 0)
+    p = inputs.config_extension(nx=WORKLOAD["nx"], ny=WORKLOAD["ny"], levels=WORKLOAD["levels"])
+    f = torch.tensor(p.f, device=dev)
+    g = torch.tensor(p.g, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    out = {"workload": f"mesh extension {WORKLOAD['nx']}x{WORKLOAD['ny']} Q2 (channel solid as obstacle cells, "
+                       f"bar bending 0.02 at the tip), mu_A of Eq. mu_distribution, {WORKLOAD['levels']} MG levels, "
+                       "flexible PCG FP64 + one velocity V-cycle, rel-res 1e-6",
+           "l2": "flushed (256 MiB write) before every timed run"}
+    for prec in (32, 64):
+        s = gs.Solver.from_problem(p, device=dev, mg_precision=prec)
+        b = torch.empty_like(f)
+        s.lift_rhs(f, g, b)
+        bu = b[:s.n_u].contiguous()
+        x = torch.zeros_like(bu)
+        s.solve_A(bu, x, tol=1e-6, allow_noconv=True)  # warm-up
+        ts = []
+        for _ in range(max(1, args.steps)):
+            x.zero_()
+            flush.fill_(1.0)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            it, rr, _ = s.solve_A(bu, x, tol=1e-6, allow_noconv=True)
+            e.record(st)
+            e.synchronize()
+            ts.append(a.elapsed_time(e))
+        out["fp32_multigrid" if prec == 32 else "fp64_multigrid"] = {
+            "time_to_solve_ms": statistics.median(ts), "iterations": it, "rel_residual": rr, "unknowns": s.n_u}
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------------------------
 # 3D spheres workload (64^3, 64 stiff spheres): deflated solve, FP32 vs FP64 multigrid, 3D A x
 # --------------------------------------------------------------------------------------------
 def run_spheres(args):
@@ -612,7 +653,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-mono", action="store_true", help="skip the Sec. 4 saddle-point multigrid comparison")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="channel", choices=["channel", "batched", "serving", "spheres"],
+    ap.add_argument("--workload", default="channel", choices=["channel", "batched", "serving", "spheres", "extension"],
                     help="channel: the contract line; batched / serving: the engine workloads; spheres: the 3D "
                          "64^3 inclusion workload (extra lines)")
     ap.add_argument("--instances", type=int, default=256)
@@ -628,6 +669,8 @@ def main():
         return run_serving(args)
     if args.workload == "spheres" and args.impl == "gs":
         return run_spheres(args)
+    if args.workload == "extension" and args.impl == "gs":
+        return run_extension(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -174,6 +174,22 @@ gs_status gs_vcycle(gs_ctx* ctx, const double* r, double* z);
 gs_status gs_solve(gs_ctx* ctx, const double* rhs, double* x, double tol, int* iterations,
                    double* rel_residual);
 
+/* Mesh-extension solve (Eq. "extenstion"; Sec. 5: CG preconditioned by a matrix-free multigrid
+ * with a fourth-order Chebyshev smoother): A x = rhs on the velocity block of the finest level,
+ * where A is this context's velocity block (create it with alpha = 0 and eta = mu_A / 2 per cell:
+ * A then carries int mu_A eps(u) : eps(v); solid cells are obstacle cells whose nodes hold the
+ * solid displacement as Dirichlet data).  Flexible (Polak-Ribiere) preconditioned CG, one velocity
+ * V-cycle (gs_vcycle, the context's mg_precision) per iteration, FP64 vectors; stops when
+ * ||rhs - A x|| / ||rhs|| <= tol or after max_iter iterations.  rhs: device, d*N_v, holding the
+ * Dirichlet values on constrained entries and -A_raw g elsewhere (the velocity part of
+ * gs_lift_rhs with f = 0).  x: device, d*N_v; in = initial guess on free entries (constrained
+ * entries are overwritten with rhs), out = solution.  Uses the context's Krylov workspace (not
+ * concurrently with gs_solve on the same context).  GS_ENOCONV / GS_EBREAKDOWN leave the last
+ * iterate in x; *iterations and *rel_residual (either may be NULL) receive the CG iteration count
+ * and the explicit relative residual. */
+gs_status gs_solve_A(gs_ctx* ctx, const double* rhs, double* x, double tol, int* iterations,
+                     double* rel_residual);
+
 /* rhs = [M_u f_u ; M_p f_p] - K_raw g on free entries, rhs = g on constrained entries, where
  * f is a nodal load field (full layout) and g holds Dirichlet values (full layout; only its
  * constrained entries are used).  K_raw is the saddle matrix without constraint elimination.

@@ -2355,6 +2355,104 @@ gs_status gs_vcycle(gs_ctx* c, const double* r, double* z) {
   return GS_OK;
 }
 
+// ---- mesh-extension solve (Eq. "extenstion", Sec. 5): flexible PCG on the velocity block ---------
+namespace {
+// z = V(r) on the finest level (FP64 in / out), z = r on constrained rows
+gs_status ext_precond(gs_ctx* c, const double* r, double* z, const Geom& gu) {
+  Level& F = c->lv[c->L - 1];
+  if (c->fp32) {
+    KL(K_VEC, launch_cast<double, float>(r, (float*)F.b, F.nu, 1.0f, c->st));
+    CKS(vcycle<float>(c, c->L - 1));
+    KL(K_VEC, launch_cast<float, double>((const float*)F.xA, z, F.nu, 1.0, c->st));
+  } else {
+    KL(K_VEC, launch_cast<double, double>(r, (double*)F.b, F.nu, 1.0, c->st));
+    CKS(vcycle<double>(c, c->L - 1));
+    KL(K_VEC, launch_cast<double, double>((const double*)F.xA, z, F.nu, 1.0, c->st));
+  }
+  KL(K_VEC, launch_copy_constrained(r, z, gu, c->st));
+  return GS_OK;
+}
+// y = A x (APPLY) or y = b - A x (RESID), FP64, finest level
+gs_status ext_apply(gs_ctx* c, int mode, const double* x, double* y, const double* b) {
+  const Level& F = c->lv[c->L - 1];
+  TileArgs<double> a = tile_args<double>(F);
+  a.xu = x; a.yu = y; a.bu = b;
+  KL(K_SADDLE64, launch_tile<double>(c->dim, mode, OPS_A, a, c->st));
+  return GS_OK;
+}
+}  // namespace
+
+// Flexible (Polak-Ribiere) PCG: beta = z_new . (r_new - r_old) / (z_old . r_old); x0 = rhs on the
+// identity rows (Dirichlet data), the caller's guess elsewhere.  Vectors: r and r_old in the first
+// two rows of the Krylov basis area (one fused pair of dot products), z, p, q in w, t1, t2.
+gs_status gs_solve_A(gs_ctx* c, const double* rhs, double* x, double tol, int* iterations, double* rel_residual) {
+  if (!c || !rhs || !x) return fail(GS_EINVAL, "NULL argument");
+  if (!(tol > 0.0)) return fail(GS_EINVAL, "tol must be > 0");
+  const Level& F = c->lv[c->L - 1];
+  const long long n = F.nu;
+  Geom gu = F.g;
+  gu.Np = 0;  // velocity entries only
+  double* r = c->V;
+  double* rold = c->V + c->N;
+  double *z = c->w, *p = c->t1, *q = c->t2;
+  auto dots = [&](const double* V, int k, const double* w, double* out) { return dot_host<double>(c, V, c->N, k, w, n, out); };
+  int it = 0;
+  double bn2, rn2, rel = 0.0;
+  CKS(dots(rhs, 1, rhs, &bn2));
+  const double bnorm = std::sqrt(bn2);
+  if (!std::isfinite(bnorm)) return fail(GS_EBREAKDOWN, "right-hand side is not finite");
+  KL(K_VEC, launch_copy_constrained(rhs, x, gu, c->st));
+  if (bnorm == 0.0) {
+    KL(K_VEC, launch_fill_zero<double>(x, n, c->st));
+    if (iterations) *iterations = 0;
+    if (rel_residual) *rel_residual = 0.0;
+    return GS_OK;
+  }
+  CKS(ext_apply(c, TILE_RESID, x, r, rhs));
+  CKS(dots(r, 1, r, &rn2));
+  rel = std::sqrt(rn2) / bnorm;
+  gs_status st = GS_OK;
+  if (rel > tol) {
+    CKS(ext_precond(c, r, z, gu));
+    KL(K_VEC, launch_cast<double, double>(z, p, n, 1.0, c->st));
+    double rz;
+    CKS(dots(r, 1, z, &rz));
+    const int max_it = c->opt.max_iter;
+    while (true) {
+      double pq;
+      CKS(ext_apply(c, TILE_APPLY, p, q, nullptr));
+      CKS(dots(p, 1, q, &pq));
+      if (!(pq > 0.0) || !std::isfinite(pq)) { st = GS_EBREAKDOWN; break; }
+      const double a = rz / pq;
+      KL(K_VEC, launch_cast<double, double>(r, rold, n, 1.0, c->st));
+      KL(K_AXPY, launch_axpby<double>(p, x, a, 1.0, n, c->st));
+      KL(K_AXPY, launch_axpby<double>(q, r, -a, 1.0, n, c->st));
+      ++it;
+      CKS(dots(r, 1, r, &rn2));
+      rel = std::sqrt(rn2) / bnorm;
+      if (rel <= tol) break;
+      if (it >= max_it) { st = GS_ENOCONV; break; }
+      CKS(ext_precond(c, r, z, gu));
+      double zr[2];
+      CKS(dots(r, 2, z, zr));  // z . r_new, z . r_old
+      const double beta = (zr[0] - zr[1]) / rz;
+      rz = zr[0];
+      KL(K_AXPY, launch_axpby<double>(z, p, 1.0, beta, n, c->st));
+    }
+  }
+  // explicit residual of the returned iterate
+  CKS(ext_apply(c, TILE_RESID, x, r, rhs));
+  CKS(dots(r, 1, r, &rn2));
+  rel = std::sqrt(rn2) / bnorm;
+  c->last_it = it;
+  c->last_rel = rel;
+  if (iterations) *iterations = it;
+  if (rel_residual) *rel_residual = rel;
+  if (st == GS_EBREAKDOWN) return fail(st, "CG breakdown (p . A p <= 0)");
+  if (st == GS_ENOCONV) return fail(st, "CG did not reach the tolerance");
+  return GS_OK;
+}
+
 gs_status gs_solve(gs_ctx* c, const double* rhs, double* x, double tol, int* iterations, double* rel_residual) {
   if (!c || !rhs || !x) return fail(GS_EINVAL, "NULL argument");
   if (!(tol > 0.0)) return fail(GS_EINVAL, "tol must be > 0");

@@ -74,6 +74,9 @@ _lib.gs_vcycle.argtypes = [_vp, _vp, _vp]
 _lib.gs_solve.restype = ctypes.c_int
 _lib.gs_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_double)]
+_lib.gs_solve_A.restype = ctypes.c_int
+_lib.gs_solve_A.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_double)]
 _lib.gs_lift_rhs.restype = ctypes.c_int
 _lib.gs_lift_rhs.argtypes = [_vp, _vp, _vp, _vp]
 _lib.gs_batch_solve.restype = ctypes.c_int
@@ -125,7 +128,8 @@ _lib.gs_engine_get_stats.argtypes = [_vp, ctypes.POINTER(GsEngineStats)]
 _lib.gs_engine_destroy.restype = None
 _lib.gs_engine_destroy.argtypes = [_vp]
 
-EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_vmult", "gs_vmult_A", "gs_vcycle", "gs_solve", "gs_lift_rhs",
+EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_vmult", "gs_vmult_A", "gs_vcycle", "gs_solve", "gs_solve_A",
+            "gs_lift_rhs",
             "gs_batch_solve", "gs_apply_level", "gs_get_info", "gs_set_stream", "gs_destroy", "gs_strerror",
             "gs_last_error", "gs_profile", "gs_profile_read", "gs_coarse_solve_noalloc", "gs_engine_create",
             "gs_engine_add", "gs_engine_step", "gs_engine_poll", "gs_engine_active", "gs_engine_get_stats",
@@ -249,6 +253,16 @@ class Solver:
         s = _lib.gs_solve(self.ctx, _ptr(rhs, T, self.n_total, "rhs"), _ptr(x, T, self.n_total, "x"), float(tol),
                           ctypes.byref(it), ctypes.byref(rel))
         _check(s, "gs_solve", allow=(GS_ENOCONV,) if allow_noconv else ())
+        return it.value, rel.value, s
+
+    def solve_A(self, rhs, x, tol=1e-6, allow_noconv=False):
+        """Mesh-extension solve A x = rhs on the velocity block (length d*N_v), CG + V-cycle."""
+        T = self.torch.float64
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        s = _lib.gs_solve_A(self.ctx, _ptr(rhs, T, self.n_u, "rhs"), _ptr(x, T, self.n_u, "x"), float(tol),
+                            ctypes.byref(it), ctypes.byref(rel))
+        _check(s, "gs_solve_A", allow=(GS_ENOCONV,) if allow_noconv else ())
         return it.value, rel.value, s
 
     def lift_rhs(self, f, g, rhs):
