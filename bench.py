@@ -199,7 +199,8 @@ def run_gpu(args, rank, world):
 
     p = inputs.config_channel(**WORKLOAD)
     stream = torch.cuda.current_stream(dev)
-    solver = gs.Solver.from_problem(p, device=dev, restart=args.restart, max_iter=4000)
+    solver = gs.Solver.from_problem(p, device=dev, restart=args.restart, max_iter=4000,
+                                    tile_autotune=args.tile_autotune)
     N = solver.n_total
     f = torch.tensor(p.f, device=dev)
     g = torch.tensor(p.g, device=dev)
@@ -653,6 +654,9 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-mono", action="store_true", help="skip the Sec. 4 saddle-point multigrid comparison")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-autotune", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="2D tile height of the channel solver: 0 autotune (default); 1 / 2 / 3: 32 x 16 / 17 / 8 "
+                         "(pins the launch configuration, e.g. for profiler runs whose timings would skew the tuner)")
     ap.add_argument("--workload", default="channel", choices=["channel", "batched", "serving", "spheres", "extension"],
                     help="channel: the contract line; batched / serving: the engine workloads; spheres: the 3D "
                          "64^3 inclusion workload (extra lines)")
