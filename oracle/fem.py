@@ -12,7 +12,9 @@ Eqs. "form_a_j" and "form_b", and its matrix form Eq. "stokes-discrete-block"):
 
 Readings of the paper: the viscous term carries the factor 2 of the stress
 sigma = 2 eta eps - p I (Eq. "const_fluid"); the pressure is the physical one, so
-B = -(div u, q) (the paper's p is its negative); alpha is one scalar.
+B = -(div u, q) (the paper's p is its negative).  alpha = rho / (gamma tau) is one scalar, or one
+value per cell when the solid and fluid densities differ (Sec. 5, FSI2i: rho_s = 10 rho_f); the
+mass term is then sum_K alpha_K int_K phi_i phi_j.
 
 Quadrature is tensor-product 3-point Gauss-Legendre, exact for these
 polynomial integrands on Cartesian cells.  Constraints are imposed by symmetric
@@ -155,7 +157,8 @@ class System:
 
     def __init__(self, mesh: Mesh, eta, alpha, need_pressure=True):
         self.mesh = mesh
-        self.alpha = float(alpha)
+        self.alpha = alpha
+        self.alpha_cells = cell_alpha(mesh, alpha)
         self.eta = np.asarray(eta, dtype=float)
         cm = CellMatrices(mesh.dim, mesh.h)
         self.cm = cm
@@ -164,7 +167,8 @@ class System:
         nloc = udofs.shape[1]
         e = self.eta[act]
         # velocity block: A_K = alpha * mass + eta_K * visc
-        vals = (self.alpha * cm.mass[None] + e[:, None, None] * cm.visc[None]).reshape(len(act), -1)
+        al = self.alpha_cells[act]
+        vals = (al[:, None, None] * cm.mass[None] + e[:, None, None] * cm.visc[None]).reshape(len(act), -1)
         rows = np.repeat(udofs, nloc, axis=1)
         cols = np.tile(udofs, (1, nloc))
         A_raw = sp.coo_matrix((vals.ravel(), (rows.ravel(), cols.ravel())),
@@ -216,6 +220,15 @@ class System:
         return np.where(self.constrained, g, b)
 
 
+def cell_alpha(mesh: Mesh, alpha):
+    """alpha per cell: a scalar broadcast to every cell, or an array of N_c values."""
+    a = np.asarray(alpha, dtype=float)
+    if a.ndim == 0:
+        return np.full(int(np.prod(mesh.n)), float(a))
+    assert a.shape == (int(np.prod(mesh.n)),), "alpha: a scalar or one value per cell"
+    return a
+
+
 def _eliminate(M, constrained):
     keep = sp.diags((~constrained).astype(float))
     out = (keep @ M @ keep + sp.diags(constrained.astype(float))).tocsr()
@@ -229,6 +242,7 @@ def apply_A_rows(mesh: Mesh, eta, alpha, x, rows):
     cm = CellMatrices(mesh.dim, mesh.h)
     vc = mesh.vnode_constrained()
     nb = cm.nb
+    al = cell_alpha(mesh, alpha)
     rows = np.asarray(rows, dtype=np.int64)
     out = np.zeros(len(rows))
     cell_vn = None
@@ -259,7 +273,7 @@ def apply_A_rows(mesh: Mesh, eta, alpha, x, rows):
             offs = Mesh.local_offsets(mesh.dim, 3)
             gn = mesh.vnode_flat(2 * np.array(cell)[None, :] + offs)
             xl = np.concatenate([np.where(vc[gn], 0.0, x[b * mesh.Nv + gn]) for b in range(mesh.dim)])
-            Arow = alpha * cm.mass[comp * nb + li] + eta[cflat] * cm.visc[comp * nb + li]
+            Arow = al[cflat] * cm.mass[comp * nb + li] + eta[cflat] * cm.visc[comp * nb + li]
             acc += Arow @ xl
         out[r] = acc
     return out

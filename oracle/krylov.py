@@ -128,7 +128,10 @@ class StokesOracle:
     def __init__(self, mesh: Mesh, eta, alpha, levels, degree=4, seed=0, restart=50, schur="auto",
                  coarse="cholesky", orth="cgs2", pdegree=2, deflate=False, precond="block", smooth=2, cycles=1):
         self.mesh = mesh
-        self.alpha = float(alpha)
+        # alpha: a scalar, or one value per cell (then the Cahouet-Chabard term is
+        # K_p(1/alpha)^{-1} = abar (K_p^w)^{-1}, w = abar / alpha_K, abar = max alpha; pressure.py)
+        self.alpha_cells = alpha if np.ndim(alpha) > 0 else None
+        self.alpha = float(np.max(alpha)) if np.ndim(alpha) > 0 else float(alpha)
         self.sys = System(mesh, eta, alpha)
         self.levels = levels
         self.restart = restart
@@ -150,7 +153,7 @@ class StokesOracle:
         # Schur approximation: "mass" = M_p(1/eta) only; "cc" = Cahouet-Chabard
         # M_p(1/eta)^{-1} + alpha K_p^{-1}; "auto" = cc when alpha > 0
         self.schur = ("cc" if self.alpha > 0 else "mass") if schur == "auto" else schur
-        self.pmg = (PressureHierarchy(mesh, levels, degree=pdegree, seed=seed, coarse=coarse)
+        self.pmg = (PressureHierarchy(mesh, levels, degree=pdegree, seed=seed, coarse=coarse, alpha=self.alpha_cells)
                     if self.schur == "cc" else None)
         # the finest level of the hierarchy re-assembles A; both are identical by construction
         self.nullspace = mesh.has_pressure_nullspace()

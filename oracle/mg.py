@@ -100,6 +100,7 @@ class Level:
     def __init__(self, mesh: Mesh, eta, alpha, index):
         self.mesh = mesh
         self.eta = eta
+        self.alpha = alpha
         self.index = index
         self.sys = System(mesh, eta, alpha, need_pressure=False)
         self.A = self.sys.A
@@ -157,14 +158,18 @@ class Hierarchy:
                  lanczos_steps=12, safety=1.2, ratio=15.0, coarse="cholesky", deflate=False):
         meshes = [fine]
         etas = [np.asarray(eta_fine, dtype=float)]
+        # per-cell alpha (rho_s != rho_f) is coarsened like eta: mean of the active children
+        per_cell = np.ndim(alpha) > 0
+        alphas = [np.asarray(alpha, dtype=float) if per_cell else alpha]
         for _ in range(nlevels - 1):
             c = meshes[-1].coarsen()
             etas.append(coarsen_eta(meshes[-1], c, etas[-1]))
+            alphas.append(coarsen_eta(meshes[-1], c, alphas[-1]) if per_cell else alpha)
             meshes.append(c)
-        meshes, etas = meshes[::-1], etas[::-1]
+        meshes, etas, alphas = meshes[::-1], etas[::-1], alphas[::-1]
         self.degree = degree
         self.ratio = ratio
-        self.levels = [Level(m, e, alpha, i) for i, (m, e) in enumerate(zip(meshes, etas))]
+        self.levels = [Level(m, e, a, i) for i, (m, e, a) in enumerate(zip(meshes, etas, alphas))]
         for i in range(1, len(self.levels)):
             self.levels[i].P = prolongation(meshes[i - 1], meshes[i])
         self.coarse = coarse

@@ -124,12 +124,13 @@ class MonolithicHierarchy:
                              coarse="chebyshev" if coarse == "chebyshev" else "cholesky")
         meshes = [lv.mesh for lv in self.vel.levels]
         etas = [lv.eta for lv in self.vel.levels]
+        alphas = [lv.alpha for lv in self.vel.levels]
         self.degree = degree
         self.smooth = smooth
         self.cycles = cycles
         self.schur_steps = schur_steps
         self.coarse = coarse
-        self.levels = [SaddleLevel(m, e, alpha, i) for i, (m, e) in enumerate(zip(meshes, etas))]
+        self.levels = [SaddleLevel(m, e, a, i) for i, (m, e, a) in enumerate(zip(meshes, etas, alphas))]
         for i in range(1, len(self.levels)):
             lo, hi = self.levels[i - 1], self.levels[i]
             hi.Pu = self.vel.levels[i].P

@@ -10,6 +10,9 @@ The Cahouet-Chabard approximation adds the reaction part:
 
     S^{-1} ~ M_p(1/eta)^{-1} + alpha K_p^{-1},
 
+(with alpha per cell: K_p(1/alpha)^{-1}, the Laplacian weighted by 1/alpha_K on each cell, applied
+as abar (K_p^w)^{-1} with weights w_K = abar / alpha_K and abar = max alpha; w = 1 for one alpha)
+
 K_p = Q1 stiffness matrix int grad psi_q . grad psi_r over active cells, with p = 0 on faces
 without a velocity Dirichlet condition (do-nothing outflow) and on pressure nodes touched by no
 active cell.  K_p^{-1} is applied by one V-cycle of the same kind as the velocity one (nested
@@ -28,7 +31,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from .fem import Q1_NODES, lagrange_1d, tensor_basis
-from .mesh import Mesh
+from .mesh import Mesh, coarsen_eta
 from .mg import chebyshev, lanczos_max, lanczos_start
 
 LANCZOS_PRESSURE_LEVEL = 0x80  # level field of the start-vector counter: pressure level l -> 0x80 | l
@@ -51,13 +54,14 @@ def laplacian_constraints(mesh: Mesh):
     return c
 
 
-def pressure_laplacian(mesh: Mesh):
-    """(K_p with constraints eliminated, constraint mask)."""
+def pressure_laplacian(mesh: Mesh, w=None):
+    """(K_p with constraints eliminated, constraint mask); w: optional weight per cell."""
     Ke = q1_stiffness_cell(mesh.dim, mesh.h)
     act = mesh.active_cells()
     pd = mesh.cell_pnodes()[act]
     n = pd.shape[1]
-    vals = np.broadcast_to(Ke[None], (len(act),) + Ke.shape).reshape(len(act), -1)
+    wa = np.ones(len(act)) if w is None else np.asarray(w, dtype=float)[act]
+    vals = (wa[:, None, None] * Ke[None]).reshape(len(act), -1)
     K = sp.coo_matrix((vals.ravel(), (np.repeat(pd, n, axis=1).ravel(), np.tile(pd, (1, n)).ravel())),
                       shape=(mesh.Np, mesh.Np)).tocsr()
     c = laplacian_constraints(mesh)
@@ -97,15 +101,24 @@ class PressureHierarchy:
     """Multigrid for K_p on the nested meshes (levels[0] = coarsest)."""
 
     def __init__(self, fine: Mesh, nlevels, degree=4, seed=0, lanczos_steps=12, safety=1.2, ratio=15.0,
-                 coarse="cholesky"):
+                 coarse="cholesky", alpha=None):
         meshes = [fine]
         for _ in range(nlevels - 1):
             meshes.append(meshes[-1].coarsen())
-        meshes = meshes[::-1]
+        # alpha per cell: weights w = abar / alpha_K, coarse alpha = mean of the active children
+        weights = [None] * nlevels
+        self.abar = None
+        if alpha is not None and np.ndim(alpha) > 0:
+            a = [np.asarray(alpha, dtype=float)]
+            for i in range(nlevels - 1):
+                a.append(coarsen_eta(meshes[i], meshes[i + 1], a[-1]))
+            self.abar = float(a[0].max())
+            weights = [self.abar / ai for ai in a]
+        meshes, weights = meshes[::-1], weights[::-1]
         self.degree, self.ratio = degree, ratio
         self.levels = []
         for i, m in enumerate(meshes):
-            K, c = pressure_laplacian(m)
+            K, c = pressure_laplacian(m, weights[i])
             self.levels.append(dict(mesh=m, K=K, c=c, D=K.diagonal(), P=None, lam_hi=None))
         for i in range(1, len(meshes)):
             lo, hi = self.levels[i - 1], self.levels[i]

@@ -167,9 +167,10 @@ CHANNEL_L, CHANNEL_H = 2.5, 0.41
 
 
 def config_channel(nx: int = 1280, ny: int = 224, levels: int = 6, eta_solid: float = 1e4,
-                   alpha: float = 1000.0, v_in: float = 1.0) -> Problem:
+                   alpha: float = 1000.0, v_in: float = 1.0, rho_ratio: Optional[float] = None) -> Problem:
     """Channel 2.5 x 0.41; square obstacle [0.15,0.25]^2 (void cells); bar [0.25,0.60]x[0.19,0.21]
-    with eta = eta_solid; parabolic inflow on x = 0, no-slip walls, do-nothing outflow on x = L."""
+    with eta = eta_solid; parabolic inflow on x = 0, no-slip walls, do-nothing outflow on x = L.
+    rho_ratio: alpha per cell, alpha * rho_ratio on the bar (rho_s / rho_f; 10 in FSI2i)."""
     dim = 2
     nn = (nx, ny)
     L = (CHANNEL_L, CHANNEL_H)
@@ -182,7 +183,8 @@ def config_channel(nx: int = 1280, ny: int = 224, levels: int = 6, eta_solid: fl
     g = _full(dim, nn, np.stack([ux, np.zeros_like(ux)], axis=1))
     f = _full(dim, nn)
     faces = FACE_XM | FACE_YM | FACE_YP
-    return Problem(f"channel{nx}x{ny}", dim, nn, L, levels, eta, alpha, faces,
+    al = alpha if rho_ratio is None else np.where(bar & ~void, alpha * rho_ratio, alpha)
+    return Problem(f"channel{nx}x{ny}", dim, nn, L, levels, eta, al, faces,
                    void.astype(np.uint8), f, g)
 
 
