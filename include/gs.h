@@ -154,6 +154,18 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
                     const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
                     gs_ctx** out);
 
+/* gs_create with alpha = rho / (gamma tau) given per cell (the solid's density differs from the
+ * fluid's, e.g. rho_s = 10 rho_f in FSI2i, Sec. 5): the mass term of A becomes
+ * sum_K alpha_K int_K phi_i phi_j.  alpha_per_cell: HOST array of N_c finite values >= 0 (finest
+ * level; coarse alpha = mean of the active children, like eta).  The Cahouet-Chabard Schur term
+ * becomes K_p(1/alpha)^{-1}, the pressure Laplacian with cell weights 1/alpha_K, applied as
+ * abar V(K_p^w) with w_K = abar / alpha_K and abar = max alpha_K (cells with alpha_K = 0 get
+ * w_K = 1); it is active when abar > 0 (schur_kind 0).  Everything else as gs_create; the
+ * workspace size is the same (gs_footprint_bytes reserves the per-cell arrays). */
+gs_status gs_create_ex(const gs_mesh* mesh, int levels, const double* eta_per_cell, const double* alpha_per_cell,
+                       const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
+                       gs_ctx** out);
+
 /* y = K x on the finest level, FP64 (Eq. "stokes-discrete-block" with constraints).
  * x, y: device, length N, must not alias. */
 gs_status gs_vmult(gs_ctx* ctx, const double* x, double* y);

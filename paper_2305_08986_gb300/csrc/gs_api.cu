@@ -66,11 +66,15 @@ struct Level {
   bool has_void = false;
   std::vector<uint8_t> hvoid, hvmask, hpmask;
   std::vector<double> heta;
+  std::vector<double> halpha;  // alpha per cell (when given per cell; coarse: mean of active children)
   Geom g{};
   OpCoef<double> c64{};
   OpCoef<float> c32{};
   double* eta64 = nullptr;
   float* eta32 = nullptr;
+  double* alpha64 = nullptr;  // alpha per cell, or NULL (alpha then lives in the coefficients)
+  float* alpha32 = nullptr;
+  void* pw = nullptr;         // weights abar / alpha_K of the pressure Laplacian (MG precision), or NULL
   uint8_t *vmask = nullptr, *pmask = nullptr, *cvoid = nullptr;
   void *xA = nullptr, *xB = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
   double lam_hi = 0.0;
@@ -115,7 +119,8 @@ struct KState {
 struct gs_ctx {
   int dim = 2, L = 1;
   gs_options opt{};
-  double alpha = 0.0;
+  double alpha = 0.0;        // alpha, or abar = max alpha_K when alpha is given per cell
+  bool alpha_cells = false;
   cudaStream_t st = nullptr;
   bool fp32 = true;
   std::vector<Level> lv;
@@ -277,7 +282,7 @@ const int kDeflMaxInclusions = 256;
 gs_status plan_deflation(gs_ctx* c, const gs_mesh* m);
 
 // ---- host planning: level sizes, obstacle flags, constraint masks, coarse eta -----------------
-gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
+gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c, const double* alpha_cells = nullptr) {
   if (!m) return fail(GS_EINVAL, "mesh is NULL");
   if (m->dim != 2 && m->dim != 3) return fail(GS_EINVAL, "dim must be 2 or 3");
   if (L < 1 || L > 16) return fail(GS_EINVAL, "levels must be in [1, 16]");
@@ -315,6 +320,17 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
   }
   if (eta) {
     F.heta.assign(eta, eta + F.Nc);
+    if (alpha_cells) {
+      F.halpha.assign(alpha_cells, alpha_cells + F.Nc);
+      double amax = 0.0;
+      for (long long i = 0; i < F.Nc; ++i) {
+        if (F.hvoid[i]) continue;
+        if (!(std::isfinite(alpha_cells[i]) && alpha_cells[i] >= 0.0))
+          return fail(GS_EINVAL, "alpha must be finite and >= 0 on active cells");
+        amax = std::max(amax, alpha_cells[i]);
+      }
+      c->alpha = amax;
+    }
     for (long long i = 0; i < F.Nc; ++i)
       if (!(std::isfinite(eta[i]) && eta[i] > 0.0) && !F.hvoid[i])
         return fail(GS_EINVAL, "eta must be positive and finite on active cells");
@@ -324,12 +340,14 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
     const Level& Fi = c->lv[l + 1];
     C.hvoid.assign(C.Nc, 0);
     if (eta) C.heta.assign(C.Nc, 1.0);
+    const bool pa = !Fi.halpha.empty();
+    if (pa) C.halpha.assign(C.Nc, 0.0);
     for (int k = 0; k < C.n[2]; ++k)
       for (int j = 0; j < C.n[1]; ++j)
         for (int i = 0; i < C.n[0]; ++i) {
           const long long cc = i + (long long)C.n[0] * (j + (long long)C.n[1] * k);
           int nact = 0, nch = 0;
-          double s = 0.0;
+          double s = 0.0, sa = 0.0;
           for (int dk = 0; dk < (dim == 3 ? 2 : 1); ++dk)
             for (int dj = 0; dj < 2; ++dj)
               for (int di = 0; di < 2; ++di) {
@@ -338,10 +356,12 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c) {
                 if (!Fi.hvoid[fc]) {
                   nact++;
                   if (eta) s += Fi.heta[fc];
+                  if (pa) sa += Fi.halpha[fc];
                 }
               }
           C.hvoid[cc] = (nact == 0) ? 1 : 0;
           if (eta && nact > 0) C.heta[cc] = s / nact;
+          if (pa && nact > 0) C.halpha[cc] = sa / nact;
           (void)nch;
         }
   }
@@ -576,6 +596,12 @@ void layout(gs_ctx* c, Arena& ar) {
     Level& lv = c->lv[l];
     lv.eta64 = ar.take<double>(lv.Nc);
     lv.eta32 = ar.take<float>(lv.Nc);
+    // alpha per cell (used only when gs_create_ex gets one; reserved always so that the
+    // footprint does not depend on it: 12 bytes per cell)
+    double* a64 = ar.take<double>(lv.Nc);
+    float* a32 = ar.take<float>(lv.Nc);
+    lv.alpha64 = c->alpha_cells ? a64 : nullptr;
+    lv.alpha32 = c->alpha_cells ? a32 : nullptr;
     if (lv.has_void) {
       lv.cvoid = ar.take<uint8_t>(lv.Nc);
       lv.vmask = ar.take<uint8_t>(lv.Nv);
@@ -603,6 +629,8 @@ void layout(gs_ctx* c, Arena& ar) {
     for (int l = 0; l < c->L; ++l) {
       Level& lv = c->lv[l];
       lv.pcmask = ar.take<uint8_t>(lv.Np);
+      void* pw = takeT(lv.Nc);
+      lv.pw = c->alpha_cells ? pw : nullptr;
       lv.pxA = takeT(lv.Np);
       lv.pxB = takeT(lv.Np);
       lv.pb = takeT(lv.Np);
@@ -684,8 +712,9 @@ void set_geom(gs_ctx* c, const gs_mesh* m) {
     g.vmask = lv.vmask;
     g.pmask = lv.pmask;
     g.cvoid = lv.cvoid;
-    lv.c64 = make_coef<double>(c->dim, lv.h, c->alpha);
-    lv.c32 = make_coef<float>(c->dim, lv.h, c->alpha);
+    // alpha per cell: the coefficients carry alpha = 1 and the kernels multiply by alpha_K
+    lv.c64 = make_coef<double>(c->dim, lv.h, c->alpha_cells ? 1.0 : c->alpha);
+    lv.c32 = make_coef<float>(c->dim, lv.h, c->alpha_cells ? 1.0 : c->alpha);
     // Q1 stiffness coefficients kc[a] = prod_{b != a} h_b / (6^(d-1) h_a)
     for (int a = 0; a < 3; ++a) {
       if (a >= c->dim) { lv.pkc[a] = 0.0; continue; }
@@ -712,11 +741,19 @@ template <>
 const float* etap<float>(const Level& lv) { return lv.eta32; }
 
 template <typename T>
+const T* alphap(const Level& lv);
+template <>
+const double* alphap<double>(const Level& lv) { return lv.alpha64; }
+template <>
+const float* alphap<float>(const Level& lv) { return lv.alpha32; }
+
+template <typename T>
 TileArgs<T> tile_args(const Level& lv) {
   TileArgs<T> a{};
   a.g = lv.g;
   a.c = coef<T>(lv);
   a.eta = etap<T>(lv);
+  a.alpha = alphap<T>(lv);
   a.shape = lv.shape;
   return a;
 }
@@ -831,6 +868,7 @@ PLapArgs<T> plap_args(const Level& lv) {
   PLapArgs<T> a{};
   a.g = lv.g;
   for (int i = 0; i < 3; ++i) a.kc[i] = (T)lv.pkc[i];
+  a.w = (const T*)lv.pw;
   a.cmask = lv.pcmask;
   return a;
 }
@@ -872,6 +910,7 @@ void assemble_coarse(gs_ctx* c, std::vector<double>& A) {
         const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
         if (lv.has_void && lv.hvoid[cc]) continue;
         const double eta = lv.heta[cc];
+        const double mm = c->alpha_cells ? cf.mm * lv.halpha[cc] : cf.mm;
         for (int q = 0; q < nb; ++q) {
           const int la = q % 3, lb = (q / 3) % 3, lc = q / 9;
           gn[q] = (2 * i + la) + (long long)nv0 * ((2 * j + lb) + (long long)nv1 * (dim == 3 ? 2 * k + lc : 0));
@@ -894,10 +933,10 @@ void assemble_coarse(gs_ctx* c, std::vector<double>& A) {
                   const double Mx = Mi[pi[0]][qi[0]], My = Mi[pi[1]][qi[1]];
                   const double Kx = Ki[pi[0]][qi[0]], Ky = Ki[pi[1]][qi[1]];
                   if (dim == 2) {
-                    v = Mx * (cf.mm * My + cy * Ky) + Kx * (cx * My);
+                    v = Mx * (mm * My + cy * Ky) + Kx * (cx * My);
                   } else {
                     const double Mz = Mi[pi[2]][qi[2]], Kz = Ki[pi[2]][qi[2]];
-                    v = Mx * (My * (cf.mm * Mz + cz * Kz) + cy * Ky * Mz) + Kx * (cx * My * Mz);
+                    v = Mx * (My * (mm * Mz + cz * Kz) + cy * Ky * Mz) + Kx * (cx * My * Mz);
                   }
                 } else {
                   // eta (E in direction be) (E^T in direction al) (M in the third direction)
@@ -921,7 +960,7 @@ template <typename T>
 gs_status setup_T(gs_ctx* c) {
   for (int l = 0; l < c->L; ++l) {
     Level& lv = c->lv[l];
-    CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), (T*)lv.dinv, 1, c->st));
+    CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), alphap<T>(lv), (T*)lv.dinv, 1, c->st));
   }
   for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(lanczos<T>(c, l));
   const Level& F = c->lv[c->L - 1];
@@ -935,7 +974,7 @@ gs_status setup_T(gs_ctx* c) {
     for (int l = 0; l < c->L; ++l) {
       Level& lv = c->lv[l];
       T kc[3] = {(T)lv.pkc[0], (T)lv.pkc[1], (T)lv.pkc[2]};
-      CK(launch_plap_diag<T>(lv.g, kc, lv.pcmask, (T*)lv.pdinv, c->st));
+      CK(launch_plap_diag<T>(lv.g, kc, (const T*)lv.pw, lv.pcmask, (T*)lv.pdinv, c->st));
     }
     for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(plap_lanczos<T>(c, l));
   }
@@ -958,6 +997,7 @@ void assemble_coarse_plap(gs_ctx* c, std::vector<double>& A) {
       for (int i = 0; i < lv.n[0]; ++i) {
         const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
         if (lv.hvoid[cc]) continue;
+        const double wK = (c->alpha_cells && lv.halpha[cc] > 0.0) ? c->alpha / lv.halpha[cc] : 1.0;  // abar / alpha_K
         for (int p = 0; p < nb; ++p) {
           const int pa = p & 1, pb = (p >> 1) & 1, pc = p >> 2;
           const int row = map[(i + pa) + (long long)np0 * ((j + pb) + (long long)np1 * (dim == 3 ? k + pc : 0))];
@@ -975,7 +1015,7 @@ void assemble_coarse_plap(gs_ctx* c, std::vector<double>& A) {
               const double k1c = pc == qc ? 1 : -1, ic = pc == qc ? 2 : 1;
               v = lv.pkc[0] * k1a * ib * ic + lv.pkc[1] * ia * k1b * ic + lv.pkc[2] * ia * ib * k1c;
             }
-            A[(size_t)row * nf + col] += v;
+            A[(size_t)row * nf + col] += wK * v;
           }
         }
       }
@@ -1103,6 +1143,25 @@ gs_status setup(gs_ctx* c) {
     for (long long i = 0; i < lv.Nc; ++i) e32[i] = (float)lv.heta[i];
     CK(cudaMemcpyAsync(lv.eta64, lv.heta.data(), sizeof(double) * lv.Nc, cudaMemcpyHostToDevice, c->st));
     CK(cudaMemcpyAsync(lv.eta32, e32.data(), sizeof(float) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+    std::vector<float> a32;
+    std::vector<double> w64;
+    std::vector<float> w32;
+    if (c->alpha_cells) {
+      a32.resize(lv.Nc);
+      for (long long i = 0; i < lv.Nc; ++i) a32[i] = (float)lv.halpha[i];
+      CK(cudaMemcpyAsync(lv.alpha64, lv.halpha.data(), sizeof(double) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(lv.alpha32, a32.data(), sizeof(float) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+      if (lv.pw) {  // weights abar / alpha_K of the pressure Laplacian (1 on cells without alpha)
+        w64.resize(lv.Nc);
+        for (long long i = 0; i < lv.Nc; ++i) w64[i] = lv.halpha[i] > 0.0 ? c->alpha / lv.halpha[i] : 1.0;
+        if (c->fp32) {
+          w32.assign(w64.begin(), w64.end());
+          CK(cudaMemcpyAsync(lv.pw, w32.data(), sizeof(float) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+        } else {
+          CK(cudaMemcpyAsync(lv.pw, w64.data(), sizeof(double) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+        }
+      }
+    }
     if (lv.has_void) {
       CK(cudaMemcpyAsync(lv.cvoid, lv.hvoid.data(), lv.Nc, cudaMemcpyHostToDevice, c->st));
       CK(cudaMemcpyAsync(lv.vmask, lv.hvmask.data(), lv.Nv, cudaMemcpyHostToDevice, c->st));
@@ -1747,7 +1806,7 @@ gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, co
       return GS_OK;
     }
     case GS_OP_DIAG_A:
-      CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), y, 0, c->st));
+      CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), alphap<T>(lv), y, 0, c->st));
       return GS_OK;
     case GS_OP_SMOOTH: {
       if (!mgprec || (l == 0 && c->opt.coarse_mode != 1))
@@ -2282,9 +2341,12 @@ size_t gs_footprint_bytes(const gs_mesh* mesh, int levels, const gs_options* opt
   return c.footprint;
 }
 
-gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell, double alpha,
-                    const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
-                    gs_ctx** out) {
+}  // extern "C"
+
+namespace {
+gs_status create_impl(const gs_mesh* mesh, int levels, const double* eta_per_cell, double alpha,
+                      const double* alpha_per_cell, const gs_options* opts, void* stream, void* workspace,
+                      size_t workspace_bytes, gs_ctx** out) {
   if (!out) return fail(GS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!eta_per_cell) return fail(GS_EINVAL, "eta_per_cell is NULL");
@@ -2295,8 +2357,9 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
   c->opt = normalize_opts(opts);
   c->fp32 = c->opt.mg_precision == 32;
   c->alpha = alpha;
+  c->alpha_cells = alpha_per_cell != nullptr;
   c->st = (cudaStream_t)stream;
-  gs_status s = plan(mesh, levels, eta_per_cell, c);
+  gs_status s = plan(mesh, levels, eta_per_cell, c, alpha_per_cell);
   if (s != GS_OK) { delete c; return s; }
   {
     Arena dry;
@@ -2309,7 +2372,7 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
   Arena ar;
   ar.base = (char*)workspace;
   layout(c, ar);
-  c->cc = c->cc_alloc && (c->opt.schur_kind == 2 || alpha > 0.0);
+  c->cc = c->cc_alloc && (c->opt.schur_kind == 2 || c->alpha > 0.0);
   set_geom(c, mesh);
   cudaError_t e = cudaMallocHost(&c->hpin, sizeof(double) * (2 * c->opt.restart + 8));
   if (e != cudaSuccess) { delete c; return fail(GS_ECUDA, std::string("pinned buffer: ") + cudaGetErrorString(e)); }
@@ -2325,6 +2388,22 @@ gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell,
   }
   *out = c;
   return GS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell, double alpha,
+                    const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
+                    gs_ctx** out) {
+  return create_impl(mesh, levels, eta_per_cell, alpha, nullptr, opts, stream, workspace, workspace_bytes, out);
+}
+
+gs_status gs_create_ex(const gs_mesh* mesh, int levels, const double* eta_per_cell, const double* alpha_per_cell,
+                       const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes, gs_ctx** out) {
+  if (!alpha_per_cell) return fail(GS_EINVAL, "alpha_per_cell is NULL");
+  return create_impl(mesh, levels, eta_per_cell, 0.0, alpha_per_cell, opts, stream, workspace, workspace_bytes,
+                     out);
 }
 
 gs_status gs_vmult(gs_ctx* c, const double* x, double* y) {

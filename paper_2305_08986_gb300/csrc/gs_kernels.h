@@ -20,6 +20,7 @@ struct TileArgs {
   Geom g;
   OpCoef<T> c;
   const T* eta;   // per cell
+  const T* alpha; // per cell factor of the mass term (alpha_K; NULL: 1, alpha then lives in c.mm)
   const T* xu;    // velocity input (A and B), CHEB: current iterate
   const T* xp;    // pressure input (B^T)
   T* yu;          // velocity output (APPLY / RESID)
@@ -46,7 +47,7 @@ template <typename T>
 cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, T* out, int invert,
+cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, const T* alpha, T* out, int invert,
                          cudaStream_t st);
 template <typename T>
 cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st);
@@ -84,6 +85,7 @@ template <typename T>
 struct PLapArgs {
   Geom g;
   T kc[3];
+  const T* w;  // per-cell weight (abar / alpha_K with alpha per cell); NULL: 1
   const uint8_t* cmask;
   const T* x;
   T* y;
@@ -97,7 +99,7 @@ struct PLapArgs {
 template <typename T>
 cudaError_t launch_plap(int mode, PLapArgs<T> a, cudaStream_t st);
 template <typename T>
-cudaError_t launch_plap_diag(const Geom& g, const T* kc, const uint8_t* cmask, T* dinv, cudaStream_t st);
+cudaError_t launch_plap_diag(const Geom& g, const T* kc, const T* w, const uint8_t* cmask, T* dinv, cudaStream_t st);
 // Q1 transfers between pressure levels (bilinear interpolation and its transpose)
 template <typename T>
 cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* rf,
@@ -105,8 +107,9 @@ cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf,
 template <typename T>
 cudaError_t launch_p_prolong_add(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* xc,
                                  T* xf, cudaStream_t st);
-// Tiled Q1 operators (gs_q1tile.cu): OP = Q1_PLAP (K_p, cell scalar 1) or Q1_PMASS (M_p(1/eta),
-// cell scalar pm / eta); cmask (may be NULL) marks identity rows / zero columns.
+// Tiled Q1 operators (gs_q1tile.cu): OP = Q1_PLAP (K_p, cell scalar eta[cell], or 1 when eta is
+// NULL: the per-cell weight) or Q1_PMASS (M_p(1/eta), cell scalar pm / eta); cmask (may be NULL)
+// marks identity rows / zero columns.
 enum Q1Op { Q1_PLAP = 0, Q1_PMASS = 1 };
 template <typename T>
 struct Q1Args {

@@ -20,8 +20,8 @@ inline unsigned nblk(long long n) { return (unsigned)((n + TPB - 1) / TPB); }
 
 // ---- diag(A) (Sec. 4: the Jacobi preconditioner of Cheb(A, diag(A), k_A)) ----------------------
 template <typename T, int DIM>
-__global__ void k_diagA(const Geom g, const OpCoef<T> c, const T* __restrict__ eta, T* __restrict__ out,
-                        int invert) {
+__global__ void k_diagA(const Geom g, const OpCoef<T> c, const T* __restrict__ eta, const T* __restrict__ alpha,
+                        T* __restrict__ out, int invert) {
   const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (node >= g.Nv) return;
   int I, J, K;
@@ -51,9 +51,11 @@ __global__ void k_diagA(const Geom g, const OpCoef<T> c, const T* __restrict__ e
           const long long cell = cl[0][i] + (long long)g.n[0] * (cl[1][j] + (long long)g.n[1] * (DIM == 3 ? cl[2][k] : 0));
           if (cell_void(g, cell)) continue;
           const T e = eta[cell] * c.eta_scale;
+          OpCoef<T> cK = c;  // the cell's mass coefficient (alpha per cell)
+          if (alpha) cK.mm = c.mm * alpha[cell];
 #pragma unroll
           for (int a = 0; a < DIM; ++a)
-            acc[a] += cell_diagA<T>(DIM, a, ll[0][i], ll[1][j], DIM == 3 ? ll[2][k] : 0, e, c);
+            acc[a] += cell_diagA<T>(DIM, a, ll[0][i], ll[1][j], DIM == 3 ? ll[2][k] : 0, e, cK);
         }
   }
 #pragma unroll
@@ -64,11 +66,12 @@ __global__ void k_diagA(const Geom g, const OpCoef<T> c, const T* __restrict__ e
 }
 
 template <typename T>
-cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, T* out, int invert, cudaStream_t st) {
+cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, const T* alpha, T* out, int invert,
+                         cudaStream_t st) {
   if (g.dim == 2)
-    k_diagA<T, 2><<<nblk(g.Nv), TPB, 0, st>>>(g, c, eta, out, invert);
+    k_diagA<T, 2><<<nblk(g.Nv), TPB, 0, st>>>(g, c, eta, alpha, out, invert);
   else
-    k_diagA<T, 3><<<nblk(g.Nv), TPB, 0, st>>>(g, c, eta, out, invert);
+    k_diagA<T, 3><<<nblk(g.Nv), TPB, 0, st>>>(g, c, eta, alpha, out, invert);
   return launched(cudaGetLastError());
 }
 
@@ -324,7 +327,7 @@ cudaError_t launch_pdiag(const Geom& g, const OpCoef<T>& c, const T* eta, T* din
 }
 
 #define INST(T)                                                                                    \
-  template cudaError_t launch_diagA<T>(const Geom&, const OpCoef<T>&, const T*, T*, int, cudaStream_t); \
+  template cudaError_t launch_diagA<T>(const Geom&, const OpCoef<T>&, const T*, const T*, T*, int, cudaStream_t); \
   template cudaError_t launch_restrict<T>(const Geom&, const Geom&, const T*, T*, cudaStream_t);   \
   template cudaError_t launch_prolong_add<T>(const Geom&, const Geom&, const T*, T*, cudaStream_t); \
   template cudaError_t launch_pmass<T>(int, PMassArgs<T>, cudaStream_t);                           \
@@ -339,8 +342,8 @@ INST(double)
 namespace gs {
 
 template <typename T, int DIM>
-__global__ void k_plap_diag(const Geom g, const T k0, const T k1, const T k2, const uint8_t* __restrict__ cmask,
-                            T* __restrict__ dinv) {
+__global__ void k_plap_diag(const Geom g, const T k0, const T k1, const T k2, const T* __restrict__ w,
+                            const uint8_t* __restrict__ cmask, T* __restrict__ dinv) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= g.Np) return;
   if (cmask[q]) { dinv[q] = T(1); return; }
@@ -353,16 +356,16 @@ __global__ void k_plap_diag(const Geom g, const T k0, const T k1, const T k2, co
     if (idx[ax] - 1 >= 0) cl[ax][cnt[ax]++] = idx[ax] - 1;
     if (idx[ax] < g.n[ax]) cl[ax][cnt[ax]++] = idx[ax];
   }
-  int nact = 0;
+  T wsum = T(0);  // sum of the active touching cells' weights
   const int c2n = DIM == 3 ? cnt[2] : 1;
   for (int k = 0; k < c2n; ++k)
     for (int j = 0; j < cnt[1]; ++j)
       for (int i = 0; i < cnt[0]; ++i) {
         const long long cell = cl[0][i] + (long long)g.n[0] * (cl[1][j] + (long long)g.n[1] * (DIM == 3 ? cl[2][k] : 0));
-        if (!cell_void(g, cell)) nact++;
+        if (!cell_void(g, cell)) wsum += w ? w[cell] : T(1);
       }
   const T per_cell = DIM == 2 ? T(2) * (k0 + k1) : T(4) * (k0 + k1 + k2);
-  dinv[q] = T(1) / (T(nact) * per_cell);
+  dinv[q] = T(1) / (wsum * per_cell);
 }
 
 template <typename T>
@@ -477,17 +480,18 @@ cudaError_t launch_plap(int mode, PLapArgs<T> a, cudaStream_t st) {
   q.g = a.g;
   for (int i = 0; i < 3; ++i) q.kc[i] = a.kc[i];
   q.cmask = a.cmask;
+  q.eta = a.w;  // Q1_PLAP: the per-cell weight
   q.x = a.x; q.y = a.y; q.b = a.b; q.d = a.d; q.dinv = a.dinv; q.xout = a.xout;
   q.c1 = a.c1; q.c2 = a.c2; q.use_d = a.use_d;
   return launch_q1tile<T>(Q1_PLAP, mode, q, st);
 }
 
 template <typename T>
-cudaError_t launch_plap_diag(const Geom& g, const T* kc, const uint8_t* cmask, T* dinv, cudaStream_t st) {
+cudaError_t launch_plap_diag(const Geom& g, const T* kc, const T* w, const uint8_t* cmask, T* dinv, cudaStream_t st) {
   if (g.dim == 2)
-    k_plap_diag<T, 2><<<nblk(g.Np), TPB, 0, st>>>(g, kc[0], kc[1], kc[2], cmask, dinv);
+    k_plap_diag<T, 2><<<nblk(g.Np), TPB, 0, st>>>(g, kc[0], kc[1], kc[2], w, cmask, dinv);
   else
-    k_plap_diag<T, 3><<<nblk(g.Np), TPB, 0, st>>>(g, kc[0], kc[1], kc[2], cmask, dinv);
+    k_plap_diag<T, 3><<<nblk(g.Np), TPB, 0, st>>>(g, kc[0], kc[1], kc[2], w, cmask, dinv);
   return launched(cudaGetLastError());
 }
 template <typename T>
@@ -515,7 +519,7 @@ cudaError_t launch_cc_combine(const T* m, const T* v, const uint8_t* mask, T alp
 
 #define INSTP(T)                                                                                          \
   template cudaError_t launch_plap<T>(int, PLapArgs<T>, cudaStream_t);                                    \
-  template cudaError_t launch_plap_diag<T>(const Geom&, const T*, const uint8_t*, T*, cudaStream_t);      \
+  template cudaError_t launch_plap_diag<T>(const Geom&, const T*, const T*, const uint8_t*, T*, cudaStream_t); \
   template cudaError_t launch_p_restrict<T>(const Geom&, const Geom&, const uint8_t*, const uint8_t*,      \
                                             const T*, T*, cudaStream_t);                                  \
   template cudaError_t launch_p_prolong_add<T>(const Geom&, const Geom&, const uint8_t*, const uint8_t*,   \

@@ -5,10 +5,11 @@
 // A CTA owns a box of pressure nodes (32 x 8 in 2D, 8 x 8 x 4 in 3D, one thread per node).  It
 // stages, with cp.async, the box plus a one-node halo of the input vector (constrained entries
 // and nodes outside the mesh zero-filled) and one scalar per touching cell (0 for obstacle
-// cells and cells outside the mesh, 1 for K_p, pm / eta for the mass).  Each thread then sums
+// cells and cells outside the mesh, the cell weight for K_p (1, or abar / alpha_K with alpha
+// per cell), pm / eta for the mass).  Each thread then sums
 // its <= 2^d cells x 2^d nodes from shared memory and applies the epilogue (apply, residual,
 // or fused Chebyshev step).  The cell matrices are
-//   K_p:  sum_a kc[a] (K1 in direction a, Pi elsewhere),   K1 = [1 -1; -1 1], Pi = [2 1; 1 2],
+//   K_p:  w_K sum_a kc[a] (K1 in direction a, Pi elsewhere),   K1 = [1 -1; -1 1], Pi = [2 1; 1 2],
 //   mass: pm / eta_K  prod_a Pi,                            pm = prod h / 6^d.
 #include "gs_kernels.h"
 
@@ -69,7 +70,7 @@ __device__ __forceinline__ void q1tile_body(const Q1Args<T>& A, int bid) {
     T v = T(0);
     if (inr) {
       const long long cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
-      if (!cell_void(g, cell)) v = OP == Q1_PLAP ? T(1) : A.pm / A.eta[cell];
+      if (!cell_void(g, cell)) v = OP == Q1_PLAP ? (A.eta ? A.eta[cell] : T(1)) : A.pm / A.eta[cell];
     }
     sc[i] = v;
   }

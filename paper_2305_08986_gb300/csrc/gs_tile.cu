@@ -107,6 +107,8 @@ __device__ __forceinline__ void tile_body(const TileArgs<T>& A, int bid) {
     }
     if (active) {
       const T eta = A.eta[cell] * c.eta_scale;
+      OpCoef<T> cK = c;  // the cell's mass coefficient (alpha per cell)
+      if (A.alpha) cK.mm = c.mm * A.alpha[cell];
       T xl[DIM][NN];
       T pl[NP];
       const bool need_u = WA || (WB && comp == 0);
@@ -141,8 +143,8 @@ __device__ __forceinline__ void tile_body(const TileArgs<T>& A, int bid) {
         if (DIM == 2) {
           T yl[2][9];
           if (WA) {
-            cell_A2(0, reinterpret_cast<const T(&)[2][9]>(xl), yl[0], eta, c);
-            cell_A2(1, reinterpret_cast<const T(&)[2][9]>(xl), yl[1], eta, c);
+            cell_A2(0, reinterpret_cast<const T(&)[2][9]>(xl), yl[0], eta, cK);
+            cell_A2(1, reinterpret_cast<const T(&)[2][9]>(xl), yl[1], eta, cK);
           }
           if (WBT) cell_BT2(reinterpret_cast<const T(&)[4]>(pl), yl, c, WA);
 #pragma unroll
@@ -163,13 +165,13 @@ __device__ __forceinline__ void tile_body(const TileArgs<T>& A, int bid) {
           const T(&x3)[3][27] = reinterpret_cast<const T(&)[3][27]>(xl);
           const T(&p3)[8] = reinterpret_cast<const T(&)[8]>(pl);
           if (comp == 0) {
-            if (WA) cell_A3<T, 0>(x3, yl, eta, c);
+            if (WA) cell_A3<T, 0>(x3, yl, eta, cK);
             if (WBT) cell_BT3<T, 0>(p3, yl, c, WA);
           } else if (comp == 1) {
-            if (WA) cell_A3<T, 1>(x3, yl, eta, c);
+            if (WA) cell_A3<T, 1>(x3, yl, eta, cK);
             if (WBT) cell_BT3<T, 1>(p3, yl, c, WA);
           } else {
-            if (WA) cell_A3<T, 2>(x3, yl, eta, c);
+            if (WA) cell_A3<T, 2>(x3, yl, eta, cK);
             if (WBT) cell_BT3<T, 2>(p3, yl, c, WA);
           }
           T* sc = su + comp * D::VSZ;
@@ -421,6 +423,7 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
     }
     if (active) {
       const T eta = A.eta[cell] * c.eta_scale;
+      const T mmK = A.alpha ? c.mm * A.alpha[cell] : c.mm;  // the cell's mass coefficient
       int o[3][3];  // window offsets of the cell's nodes along each logical axis
 #pragma unroll
       for (int q = 0; q < 3; ++q)
@@ -429,7 +432,7 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
       if (WU) {
         T yl[27];
         if (WA)
-          cell_A3p(sx + pa[0] * WVA, sx + pa[1] * WVA, sx + pa[2] * WVA, o[0], o[1], o[2], yl, eta, c.mm, km_l, ex_l);
+          cell_A3p(sx + pa[0] * WVA, sx + pa[1] * WVA, sx + pa[2] * WVA, o[0], o[1], o[2], yl, eta, mmK, km_l, ex_l);
         if (WBT) {
           T pl[8];  // the cell's pressure nodes in the logical frame
 #pragma unroll

@@ -262,6 +262,8 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
     for (int i = 0; i < 4; ++i) ob[i] = T(0);
     if (active) {
       const T eta = A.eta[cell] * c.eta_scale;
+      OpCoef<T> cK = c;  // the cell's mass coefficient (alpha per cell)
+      if (A.alpha) cK.mm = c.mm * A.alpha[cell];
       T xl[2][9];
       if (NEED_U) {
         const T* s0p = sx + 2 * e0 + IN0 * 2 * e1;
@@ -274,8 +276,8 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
           }
       }
       if (WA) {
-        cell_A2(0, xl, yl[0], eta, c);
-        cell_A2(1, xl, yl[1], eta, c);
+        cell_A2(0, xl, yl[0], eta, cK);
+        cell_A2(1, xl, yl[1], eta, cK);
       }
       if (WBT) {
         T pl[4];

@@ -65,6 +65,10 @@ _lib.gs_footprint_bytes.argtypes = [ctypes.POINTER(GsMesh), ctypes.c_int, ctypes
 _lib.gs_create.restype = ctypes.c_int
 _lib.gs_create.argtypes = [ctypes.POINTER(GsMesh), ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                            ctypes.POINTER(GsOptions), _vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp)]
+_lib.gs_create_ex.restype = ctypes.c_int
+_lib.gs_create_ex.argtypes = [ctypes.POINTER(GsMesh), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(GsOptions), _vp, _vp, ctypes.c_size_t,
+                              ctypes.POINTER(_vp)]
 _lib.gs_vmult.restype = ctypes.c_int
 _lib.gs_vmult.argtypes = [_vp, _vp, _vp]
 _lib.gs_vmult_A.restype = ctypes.c_int
@@ -128,7 +132,7 @@ _lib.gs_engine_get_stats.argtypes = [_vp, ctypes.POINTER(GsEngineStats)]
 _lib.gs_engine_destroy.restype = None
 _lib.gs_engine_destroy.argtypes = [_vp]
 
-EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_vmult", "gs_vmult_A", "gs_vcycle", "gs_solve", "gs_solve_A",
+EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_create_ex", "gs_vmult", "gs_vmult_A", "gs_vcycle", "gs_solve", "gs_solve_A",
             "gs_lift_rhs",
             "gs_batch_solve", "gs_apply_level", "gs_get_info", "gs_set_stream", "gs_destroy", "gs_strerror",
             "gs_last_error", "gs_profile", "gs_profile_read", "gs_coarse_solve_noalloc", "gs_engine_create",
@@ -217,11 +221,20 @@ class Solver:
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.stream = st
         ctx = ctypes.c_void_p()
+        dp = ctypes.POINTER(ctypes.c_double)
         with torch.cuda.device(self.device):
-            _check(_lib.gs_create(ctypes.byref(mesh), self.levels,
-                                  eta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(alpha),
-                                  ctypes.byref(o), ctypes.c_void_p(st.cuda_stream), ctypes.c_void_p(self._ws_ptr),
-                                  ctypes.c_size_t(nbytes), ctypes.byref(ctx)), "gs_create")
+            if np.ndim(alpha) > 0:  # alpha per cell (gs_create_ex)
+                al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64))
+                if al.shape != eta.shape:
+                    raise ValueError("alpha: a scalar or one value per cell")
+                _check(_lib.gs_create_ex(ctypes.byref(mesh), self.levels, eta.ctypes.data_as(dp),
+                                         al.ctypes.data_as(dp), ctypes.byref(o), ctypes.c_void_p(st.cuda_stream),
+                                         ctypes.c_void_p(self._ws_ptr), ctypes.c_size_t(nbytes), ctypes.byref(ctx)),
+                       "gs_create_ex")
+            else:
+                _check(_lib.gs_create(ctypes.byref(mesh), self.levels, eta.ctypes.data_as(dp), float(alpha),
+                                      ctypes.byref(o), ctypes.c_void_p(st.cuda_stream), ctypes.c_void_p(self._ws_ptr),
+                                      ctypes.c_size_t(nbytes), ctypes.byref(ctx)), "gs_create")
         self.ctx = ctx
         info = self.info()
         self.n_total, self.n_u, self.n_p = info.n_total, info.n_u, info.n_p
