@@ -167,7 +167,7 @@ def run_reference(args, rank, world):
 # at the 1280 x 224 workload, from one ncu --set full capture of the kernel as built now (cold,
 # standalone launch, 32 x 8 tiles: the height the autotuner picks on this workload): the fused
 # FP32 Chebyshev step and the FP64 saddle operator.
-NCU_TRAFFIC_BYTES = {"cheb_step": 39.4112e6 + 3.584e3, "saddle_fp64": 24.768e6 + 3.072e3}
+NCU_TRAFFIC_BYTES = {"cheb_step": 39.409664e6 + 6.144e3, "saddle_fp64": 24.769024e6 + 4.096e3}
 
 
 def algorithmic_cost(kind, dim, n_cells, n_u, n_p, elem_bytes):
