@@ -167,7 +167,7 @@ struct gs_ctx {
   double* part = nullptr;
   int G = 1;   // blocks of the multi-dot partial sums
   int GA = 1;  // blocks of the fused axpy + norm (G * (m + 2) >= GA partial sums)
-  int GF = 1;  // blocks of the fused CGS2 update + dots (one wave, 2 CTAs per SM; GF <= G)
+  int GF = 1;  // blocks of the fused CGS2 update + dots (one wave, 4 CTAs per SM)
   double* dsc = nullptr;
   double* hpin = nullptr;
   int last_it = 0;
@@ -688,8 +688,11 @@ void layout(gs_ctx* c, Arena& ar) {
   if (GA > (long long)c->G * (m + 2)) GA = (long long)c->G * (m + 2);
   if (GA < 1) GA = 1;
   c->GA = (int)GA;
-  c->GF = (int)std::min<long long>(G, 2 * 152);
-  c->part = ar.take<double>((long long)c->G * (m + 2));
+  long long GF = (c->N + 2047) / 2048;  // strips of 256 elements, at least 8 per block
+  if (GF > 4 * 152) GF = 4 * 152;
+  if (GF < 1) GF = 1;
+  c->GF = (int)GF;
+  c->part = ar.take<double>((long long)std::max(c->G, c->GF) * (m + 2));
   c->dsc = ar.take<double>(4 * (m + 4));
   c->footprint = ar.off + 256;
 }

@@ -373,7 +373,7 @@ cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, con
 struct MultiAxpyDotsDfK {
   static constexpr int KW = 8;  // basis vectors per warp (k <= 64)
   struct Args { const float2* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
-  static constexpr int THREADS = TPB, MINB = 2;
+  static constexpr int THREADS = TPB, MINB = 4;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
     extern __shared__ float2 cs2[];
     __shared__ float2 wt[TPB];
