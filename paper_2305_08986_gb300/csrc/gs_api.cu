@@ -1620,8 +1620,8 @@ gs_status norm2_host(gs_ctx* c, const double* x, double* out) {
 const int kFusedGsMax = 64;
 gs_status cgs2_fused(gs_ctx* c, const float2* Vdf, int j, double* h1, double* h2, double* nrm) {
   const long long N = c->N;
-  KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
-  KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->G, h1, c->st));
+  KL(K_DOTS, launch_dots_strip_df(Vdf, N, j + 1, c->w, N, c->part, c->GF, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->GF, h1, c->st));
   KL(K_AXPY, launch_multi_axpy_dots_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GF, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->GF, h2, c->st));
   KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));

@@ -316,6 +316,62 @@ cudaError_t launch_dots_partial_df(const float2* V, long long ldv, int k, const 
   return submit<DotsDfK<8>>({V, ldv, k, w, n, part, self_dot}, G, 0, st);
 }
 
+// part[i * nblk + blk] = partial sums of V[i] . w (i < k <= 64), double-float products: a block
+// stages a 256-element strip of w in shared memory as double-float, and warp q dots basis rows
+// q, q + 8, q + 16, ... against it (coalesced rows, eight loads in flight per thread); every
+// row and w are read once.  The dot-only counterpart of MultiAxpyDotsDfK's second phase.
+struct DotsStripDfK {
+  static constexpr int KW = 8;  // basis vectors per warp
+  struct Args { const float2* V; long long ldv; int k; const double* w; long long n; double* part; };
+  static constexpr int THREADS = TPB, MINB = 4;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ float2 wt[TPB];
+    const float2* __restrict__ V = a.V;
+    const long long ldv = a.ldv, n = a.n;
+    const int k = a.k;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float2 acc[KW];
+#pragma unroll
+    for (int q = 0; q < KW; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (long long base = (long long)blk * TPB; base < n; base += (long long)nblk * TPB) {
+      const long long e = base + tid;
+      wt[tid] = e < n ? df_split(a.w[e]) : make_float2(0.f, 0.f);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < KW; ++q) {
+        const int i = wid + 8 * q;
+        if (i < k) {
+          const float2* Vi = V + i * ldv + base;
+          float2 v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int el = lane + 32 * t;
+            v[t] = base + el < n ? Vi[el] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int t = 0; t < 8; ++t) df_fma(acc[q], v[t], wt[lane + 32 * t]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+      const int i = wid + 8 * q;
+      if (i < k) {
+        double v = df_join(acc[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) a.part[(long long)i * nblk + blk] = v;
+      }
+    }
+  }
+};
+cudaError_t launch_dots_strip_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
+                                 int G, cudaStream_t st) {
+  if (k > 8 * DotsStripDfK::KW) return cudaErrorInvalidValue;
+  return submit<DotsStripDfK>({V, ldv, k, w, n, part}, G, 0, st);
+}
+
 // w <- w + sign * sum_i coef[i] V[i] (sum carried in double-float), partial sums of the new |w|^2
 struct MultiAxpyNormDfK {
   struct Args { const float2* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };

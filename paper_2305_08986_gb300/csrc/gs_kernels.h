@@ -167,6 +167,10 @@ cudaError_t launch_dots_partial_df(const float2* V, long long ldv, int k, const 
                                    double* part, int G, int self_dot, cudaStream_t st);
 cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, const double* coef, double sign,
                                       double* w, long long n, double* part, int G, cudaStream_t st);
+// part[i * G + block] = partial sums of V[i] . w (k <= 64; strips of w staged in shared memory,
+// every row read once)
+cudaError_t launch_dots_strip_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
+                                 int G, cudaStream_t st);
 // w <- w + sign * sum_i coef[i] V[i], then part[i * G + block] = partial sums of V[i] . w_new
 // (first CGS2 update fused with the second pass's dots; k <= 64)
 cudaError_t launch_multi_axpy_dots_df(const float2* V, long long ldv, int k, const double* coef, double sign,
