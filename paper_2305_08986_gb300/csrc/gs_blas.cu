@@ -503,7 +503,11 @@ struct ScaleDfK {
   struct Args { const double* w; const double* nrm2; float2* v; double* vd; long long n; };
   static constexpr int THREADS = TPB, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
-    const double sc = 1.0 / sqrt(a.nrm2[0]);
+    // the scale once per block: FP64 division and square root are slow on the FP64 pipe
+    __shared__ double ssc;
+    if (threadIdx.x == 0) ssc = 1.0 / sqrt(a.nrm2[0]);
+    __syncthreads();
+    const double sc = ssc;
     GS_FOR(i, a.n) {
       const double x = a.w[i] * sc;
       a.v[i] = df_split(x);
@@ -562,7 +566,10 @@ struct ScaleK {
   struct Args { const double* w; const double* nrm2; double* v; long long n; };
   static constexpr int THREADS = TPB, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
-    const double s = 1.0 / sqrt(a.nrm2[0]);
+    __shared__ double ssc;  // the scale once per block (FP64 division and square root)
+    if (threadIdx.x == 0) ssc = 1.0 / sqrt(a.nrm2[0]);
+    __syncthreads();
+    const double s = ssc;
     GS_FOR(i, a.n) a.v[i] = a.w[i] * s;
   }
 };

@@ -133,8 +133,13 @@ struct MonoUpdateK {
   struct Args { T* xu; T* xp; const T* wt; const T* y; const T* z; const double* s; long long nu, np; int zero; };
   static constexpr int THREADS = TPB, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
-    const double s1 = a.s[1];
-    const T al = (T)(s1 > 0.0 ? a.s[0] / s1 : 0.0);
+    __shared__ double sal;  // the step length once per block (FP64 division)
+    if (threadIdx.x == 0) {
+      const double s1 = a.s[1];
+      sal = s1 > 0.0 ? a.s[0] / s1 : 0.0;
+    }
+    __syncthreads();
+    const T al = (T)sal;
     GS_FOR(i, a.nu + a.np) {
       if (i < a.nu) {
         const T v = a.wt[i] + al * a.y[i];
