@@ -7,6 +7,12 @@
 //   k_many<K>  many instances in one launch: block b runs work[b] = (args row, blk, nblk, slot)
 //              with the args row read from a device table.  Blocks of a slot whose entry in
 //              `active` is 0 return at once (the slot left the batch).
+// Both entry points are launched with programmatic stream serialization (programmatic dependent
+// launch): a kernel may be scheduled while its predecessor in the stream is still running, and
+// its first instruction, griddepcontrol.wait, holds every thread until the predecessor grid has
+// completed and its memory is visible.  No block touches memory before that wait, so the order of
+// the launches is preserved; only the launch latency overlaps the predecessor's tail.  (Without
+// the launch attribute the wait returns at once.)
 // submit<K>() launches k_one immediately, or, while a Recorder is installed on the calling
 // thread, appends (kernel, args, nblk, shared bytes) to it instead.  The batching engine records
 // the same host code for every instance and merges the recordings step by step into k_many
@@ -57,14 +63,18 @@ struct Recorder {
 // recorder installed on this thread (nullptr: launch immediately)
 Recorder*& current_recorder();
 
+__device__ __forceinline__ void wait_prerequisite_grids() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <class K>
 __global__ void __launch_bounds__(K::THREADS, K::MINB) k_one(const typename K::Args a) {
+  wait_prerequisite_grids();
   K::body(a, (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <class K>
 __global__ void __launch_bounds__(K::THREADS, K::MINB)
     k_many(const typename K::Args* __restrict__ tab, const WorkItem* __restrict__ work, const int* __restrict__ active) {
+  wait_prerequisite_grids();
   const WorkItem w = work[blockIdx.x];
   if (active != nullptr && w.slot >= 0 && active[w.slot] == 0) return;
   K::body(tab[w.arg], w.blk, w.nblk);
@@ -80,8 +90,17 @@ cudaError_t batch_launch(const void* tab, const WorkItem* work, int nwork, const
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_many<K><<<(unsigned)nwork, K::THREADS, smem, st>>>((const typename K::Args*)tab, work, active);
-  return launched(cudaGetLastError(), 1);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)nwork);
+  cfg.blockDim = dim3(K::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return launched(cudaLaunchKernelEx(&cfg, k_many<K>, (const typename K::Args*)tab, work, active), 1);
 }
 
 template <class K>
@@ -97,8 +116,17 @@ cudaError_t submit(const typename K::Args& a, long long nblk, size_t smem, cudaS
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_one<K><<<(unsigned)nblk, K::THREADS, smem, st>>>(a);
-  return launched(cudaGetLastError(), 1);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)nblk);
+  cfg.blockDim = dim3(K::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return launched(cudaLaunchKernelEx(&cfg, k_one<K>, a), 1);
 }
 
 }  // namespace gs
