@@ -66,3 +66,34 @@ def test_engine_argument_checks(lib_path):
     assert gs._lib.gs_engine_poll(None, None, 4) == 0
     assert gs._lib.gs_engine_active(None) == 0
     assert gs._lib.gs_strerror(gs.GS_EBUSY) == b"busy (no free slot)"
+
+
+def test_new_entry_points_reject_bad_arguments_on_the_host(lib_path):
+    """gs_create_ex, gs_solve_A and the saddle-point multigrid options are validated before any
+    CUDA call: NULL pointers, a missing alpha array, deflation with precond_kind 1."""
+    import ctypes
+    import numpy as np
+    from paper_2305_08986_gb300 import gs
+    m, _keep = gs.make_mesh(2, (16, 16), (1.0, 1.0))
+    eta = np.ones(256)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ctx = ctypes.c_void_p()
+    o = gs.make_options()
+    # alpha_per_cell NULL
+    assert gs._lib.gs_create_ex(ctypes.byref(m), 3, eta.ctypes.data_as(dp), None, ctypes.byref(o), None,
+                                ctypes.c_void_p(256), ctypes.c_size_t(1 << 40), ctypes.byref(ctx)) == gs.GS_EINVAL
+    # negative alpha on an active cell
+    al = np.ones(256)
+    al[7] = -1.0
+    assert gs._lib.gs_create_ex(ctypes.byref(m), 3, eta.ctypes.data_as(dp), al.ctypes.data_as(dp), ctypes.byref(o),
+                                None, ctypes.c_void_p(256), ctypes.c_size_t(1 << 40), ctypes.byref(ctx)) == gs.GS_EINVAL
+    # deflation belongs to the block-triangular preconditioner
+    o2 = gs.make_options(precond_kind=1, deflate=1)
+    assert gs._lib.gs_create(ctypes.byref(m), 3, eta.ctypes.data_as(dp), 1.0, ctypes.byref(o2), None,
+                             ctypes.c_void_p(256), ctypes.c_size_t(1 << 40), ctypes.byref(ctx)) == gs.GS_EINVAL
+    assert gs._lib.gs_solve_A(None, None, None, 1e-6, None, None) == gs.GS_EINVAL
+    # the saddle-point multigrid reserves its level vectors and coarse inverse in the workspace
+    a = gs.footprint_bytes(2, (16, 16), (1.0, 1.0), 3)
+    b = gs.footprint_bytes(2, (16, 16), (1.0, 1.0), 3, precond_kind=1)
+    c = gs.footprint_bytes(2, (16, 16), (1.0, 1.0), 3, precond_kind=1, mono_cycles=2)
+    assert 0 < a < b < c
