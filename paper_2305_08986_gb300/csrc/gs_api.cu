@@ -1235,8 +1235,13 @@ gs_status setup(gs_ctx* c) {
 }
 
 // ---- Chebyshev smoother on level l: result in lv.xA (Sec. 4, Cheb(A, diag(A), k)) -------------
+// 1 / theta of a Chebyshev interval [hi / 15, hi] (the first step from zero is x = dinv b / theta)
+double cheb_inv_theta(double hi) { return 1.0 / (0.5 * (hi + hi / 15.0)); }
+
+// started: the first step from zero (d = x = dinv b / theta) was already done by the restriction
+// that produced b (launch_restrict with a Chebyshev start)
 template <typename T>
-gs_status cheb(gs_ctx* c, int l, const T* b, bool zero_init) {
+gs_status cheb(gs_ctx* c, int l, const T* b, bool zero_init, bool started = false) {
   Level& lv = c->lv[l];
   const double hi = lv.lam_hi, lo = hi / 15.0;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
@@ -1244,7 +1249,7 @@ gs_status cheb(gs_ctx* c, int l, const T* b, bool zero_init) {
   T* dinv = (T*)lv.dinv;
   T* d = (T*)lv.d;
   if (zero_init) {
-    KL(K_VEC, launch_cheb_init0<T>(b, dinv, (T)(1.0 / theta), d, (T*)lv.xA, lv.nu, c->st));
+    if (!started) KL(K_VEC, launch_cheb_init0<T>(b, dinv, (T)(1.0 / theta), d, (T*)lv.xA, lv.nu, c->st));
   } else {
     TileArgs<T> a = tile_args<T>(lv);
     a.xu = (const T*)lv.xA; a.bu = b; a.d = d; a.dinv = dinv; a.xout = (T*)lv.xB;
@@ -1265,16 +1270,16 @@ gs_status cheb(gs_ctx* c, int l, const T* b, bool zero_init) {
   return GS_OK;
 }
 
-// V-cycle on level l: input lv.b, output lv.xA
+// V-cycle on level l: input lv.b, output lv.xA (started: see cheb)
 template <typename T>
-gs_status vcycle(gs_ctx* c, int l) {
+gs_status vcycle(gs_ctx* c, int l, bool started = false) {
   Level& lv = c->lv[l];
   if (l == 0) {
-    if (c->opt.coarse_mode == 1) return cheb<T>(c, 0, (const T*)lv.b, true);
+    if (c->opt.coarse_mode == 1) return cheb<T>(c, 0, (const T*)lv.b, true, started);
     KL(K_COARSE, launch_coarse_solve<T>(c->Ainv, c->cfree, c->nf, (const T*)lv.b, (T*)lv.xA, lv.nu, c->ctmp, c->st));
     return GS_OK;
   }
-  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, s == 0));
+  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, s == 0, s == 0 && started));
   {
     TileArgs<T> a = tile_args<T>(lv);
     a.xu = (const T*)lv.xA; a.bu = (const T*)lv.b; a.yu = (T*)lv.d;
@@ -1287,8 +1292,14 @@ gs_status vcycle(gs_ctx* c, int l) {
     KL(K_VEC, launch_defl_gemv(c->d_Einv, c->defl_M, c->d_c, c->d_y, c->st));
   }
   Level& cl = c->lv[l - 1];
-  KL(K_TRANSFER, launch_restrict<T>(lv.g, cl.g, (const T*)lv.d, (T*)cl.b, c->st));
-  CKS(vcycle<T>(c, l - 1));
+  // the coarse level's first smoothing step from zero is started inside the restriction
+  const bool start = c->opt.smooth_steps >= 1 && (l - 1 >= 1 || c->opt.coarse_mode == 1);
+  if (start)
+    KL(K_TRANSFER, launch_restrict<T>(lv.g, cl.g, (const T*)lv.d, (T*)cl.b, c->st, (const T*)cl.dinv,
+                                      (T)cheb_inv_theta(cl.lam_hi), (T*)cl.d, (T*)cl.xA));
+  else
+    KL(K_TRANSFER, launch_restrict<T>(lv.g, cl.g, (const T*)lv.d, (T*)cl.b, c->st));
+  CKS(vcycle<T>(c, l - 1, start));
   KL(K_TRANSFER, launch_prolong_add<T>(lv.g, cl.g, (const T*)cl.xA, (T*)lv.xA, c->st));
   if (defl) KL(K_VEC, launch_defl_add<T>(c->defl, c->d_y, (T*)lv.xA, c->st));
   for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, false));
@@ -1318,7 +1329,7 @@ gs_status schur_inv(gs_ctx* c, const T* b) {
 
 // Chebyshev smoother of the pressure Laplacian on level l (result in lv.pxA)
 template <typename T>
-gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init) {
+gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init, bool started = false) {
   Level& lv = c->lv[l];
   const double hi = lv.plam_hi, lo = hi / 15.0;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
@@ -1326,7 +1337,7 @@ gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init) {
   T* dinv = (T*)lv.pdinv;
   T* d = (T*)lv.pd;
   if (zero_init) {
-    KL(K_SCHUR, launch_cheb_init0<T>(b, dinv, (T)(1.0 / theta), d, (T*)lv.pxA, lv.Np, c->st));
+    if (!started) KL(K_SCHUR, launch_cheb_init0<T>(b, dinv, (T)(1.0 / theta), d, (T*)lv.pxA, lv.Np, c->st));
   } else {
     PLapArgs<T> a = plap_args<T>(lv);
     a.x = (const T*)lv.pxA; a.b = b; a.d = d; a.dinv = dinv; a.xout = (T*)lv.pxB;
@@ -1349,22 +1360,27 @@ gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init) {
 
 // V-cycle for the pressure Laplacian: input lv.pb, output lv.pxA
 template <typename T>
-gs_status pvcycle(gs_ctx* c, int l) {
+gs_status pvcycle(gs_ctx* c, int l, bool started = false) {
   Level& lv = c->lv[l];
   if (l == 0) {
-    if (c->opt.coarse_mode == 1) return pcheb<T>(c, 0, (const T*)lv.pb, true);
+    if (c->opt.coarse_mode == 1) return pcheb<T>(c, 0, (const T*)lv.pb, true, started);
     KL(K_SCHUR, launch_coarse_solve<T>(c->PAinv, c->pcfree, c->nfp, (const T*)lv.pb, (T*)lv.pxA, lv.Np, c->pctmp, c->st));
     return GS_OK;
   }
-  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(pcheb<T>(c, l, (const T*)lv.pb, s == 0));
+  for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(pcheb<T>(c, l, (const T*)lv.pb, s == 0, s == 0 && started));
   {
     PLapArgs<T> a = plap_args<T>(lv);
     a.x = (const T*)lv.pxA; a.b = (const T*)lv.pb; a.y = (T*)lv.pd;
     KL(K_SCHUR, launch_plap<T>(TILE_RESID, a, c->st));
   }
   Level& cl = c->lv[l - 1];
-  KL(K_SCHUR, launch_p_restrict<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, (const T*)lv.pd, (T*)cl.pb, c->st));
-  CKS(pvcycle<T>(c, l - 1));
+  const bool start = c->opt.smooth_steps >= 1 && (l - 1 >= 1 || c->opt.coarse_mode == 1);
+  if (start)
+    KL(K_SCHUR, launch_p_restrict<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, (const T*)lv.pd, (T*)cl.pb, c->st,
+                                     (const T*)cl.pdinv, (T)cheb_inv_theta(cl.plam_hi), (T*)cl.pd, (T*)cl.pxA));
+  else
+    KL(K_SCHUR, launch_p_restrict<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, (const T*)lv.pd, (T*)cl.pb, c->st));
+  CKS(pvcycle<T>(c, l - 1, start));
   KL(K_SCHUR, launch_p_prolong_add<T>(lv.g, cl.g, lv.pcmask, cl.pcmask, (const T*)cl.pxA, (T*)lv.pxA, c->st));
   for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(pcheb<T>(c, l, (const T*)lv.pb, false));
   return GS_OK;

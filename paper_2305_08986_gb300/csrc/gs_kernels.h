@@ -49,8 +49,11 @@ cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, const T* alpha, T* out, int invert,
                          cudaStream_t st);
+// rc = R rf; with d != NULL also the start of the coarse level's Chebyshev smoother from zero,
+// d = x = dinv * rc * inv_theta (the expression of launch_cheb_init0)
 template <typename T>
-cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st);
+cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st,
+                            const T* dinv = nullptr, T inv_theta = T(0), T* d = nullptr, T* x = nullptr);
 template <typename T>
 cudaError_t launch_prolong_add(const Geom& gf, const Geom& gc, const T* xc, T* xf, cudaStream_t st);
 
@@ -103,7 +106,8 @@ cudaError_t launch_plap_diag(const Geom& g, const T* kc, const T* w, const uint8
 // Q1 transfers between pressure levels (bilinear interpolation and its transpose)
 template <typename T>
 cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* rf,
-                              T* rc, cudaStream_t st);
+                              T* rc, cudaStream_t st, const T* dinv = nullptr, T inv_theta = T(0), T* d = nullptr,
+                              T* x = nullptr);
 template <typename T>
 cudaError_t launch_p_prolong_add(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* xc,
                                  T* xf, cudaStream_t st);

@@ -99,16 +99,28 @@ __device__ __forceinline__ int restrict_stencil(int C, int nvf, int* fi, float* 
   return m;
 }
 
+// Optional start of the coarse level's Chebyshev smoother from zero, fused into the restriction
+// that produces its right-hand side: d = x = dinv * rc * inv_theta (the same expression as the
+// separate start kernel, so the same bits).  d == NULL: restriction only.
+template <typename T>
+struct ChebStart {
+  const T* dinv;
+  T inv_theta;
+  T* d;
+  T* x;
+};
+
 template <typename T>
 struct XferArgs {
   Geom gf, gc;
   const T* in;
   T* out;
+  ChebStart<T> cs;
 };
 
 template <typename T, int DIM>
 __device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, const T* __restrict__ rf,
-                                              T* __restrict__ rc, int blk) {
+                                              T* __restrict__ rc, const ChebStart<T>& cs, int blk) {
   const long long node = blk * (long long)blockDim.x + threadIdx.x;
   if (node >= gc.Nv) return;
   int I, J, K;
@@ -139,6 +151,15 @@ __device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, co
   }
 #pragma unroll
   for (int a = 0; a < DIM; ++a) rc[a * gc.Nv + node] = acc[a];
+  if (cs.d) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const long long i = a * gc.Nv + node;
+      const T v = cs.dinv[i] * acc[a] * cs.inv_theta;
+      cs.d[i] = v;
+      cs.x[i] = v;
+    }
+  }
 }
 
 __device__ __forceinline__ int prolong_stencil(int I, int* ci, float* w) {
@@ -192,7 +213,7 @@ struct RestrictK {
   using Args = XferArgs<T>;
   static constexpr int THREADS = TPB, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int) {
-    restrict_body<T, DIM>(a.gf, a.gc, a.in, a.out, blk);
+    restrict_body<T, DIM>(a.gf, a.gc, a.in, a.out, a.cs, blk);
   }
 };
 template <typename T, int DIM>
@@ -205,8 +226,9 @@ struct ProlongAddK {
 };
 
 template <typename T>
-cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st) {
-  const XferArgs<T> a{gf, gc, rf, rc};
+cudaError_t launch_restrict(const Geom& gf, const Geom& gc, const T* rf, T* rc, cudaStream_t st, const T* dinv,
+                            T inv_theta, T* d, T* x) {
+  const XferArgs<T> a{gf, gc, rf, rc, ChebStart<T>{dinv, inv_theta, d, x}};
   if (gf.dim == 2) return submit<RestrictK<T, 2>>(a, nblk(gc.Nv), 0, st);
   return submit<RestrictK<T, 3>>(a, nblk(gc.Nv), 0, st);
 }
@@ -330,7 +352,7 @@ cudaError_t launch_pdiag(const Geom& g, const OpCoef<T>& c, const T* eta, T* din
 
 #define INST(T)                                                                                    \
   template cudaError_t launch_diagA<T>(const Geom&, const OpCoef<T>&, const T*, const T*, T*, int, cudaStream_t); \
-  template cudaError_t launch_restrict<T>(const Geom&, const Geom&, const T*, T*, cudaStream_t);   \
+  template cudaError_t launch_restrict<T>(const Geom&, const Geom&, const T*, T*, cudaStream_t, const T*, T, T*, T*); \
   template cudaError_t launch_prolong_add<T>(const Geom&, const Geom&, const T*, T*, cudaStream_t); \
   template cudaError_t launch_pmass<T>(int, PMassArgs<T>, cudaStream_t);                           \
   template cudaError_t launch_pdiag<T>(const Geom&, const OpCoef<T>&, const T*, T*, cudaStream_t);
@@ -377,15 +399,20 @@ struct PXferArgs {
   const uint8_t* mc;
   const T* in;
   T* out;
+  ChebStart<T> cs;
 };
 
 template <typename T, int DIM>
 __device__ __forceinline__ void p_restrict_body(const Geom& gf, const Geom& gc, const uint8_t* __restrict__ mf,
                                                 const uint8_t* __restrict__ mc, const T* __restrict__ rf,
-                                                T* __restrict__ rc, int blk) {
+                                                T* __restrict__ rc, const ChebStart<T>& cs, int blk) {
   const long long q = blk * (long long)blockDim.x + threadIdx.x;
   if (q >= gc.Np) return;
-  if (mc[q]) { rc[q] = T(0); return; }
+  if (mc[q]) {
+    rc[q] = T(0);
+    if (cs.d) cs.d[q] = cs.x[q] = cs.dinv[q] * T(0) * cs.inv_theta;
+    return;
+  }
   int I, J, K;
   unflat(q, gc.npn, DIM, I, J, K);
   const int idx[3] = {I, J, K};
@@ -409,6 +436,11 @@ __device__ __forceinline__ void p_restrict_body(const Geom& gf, const Geom& gc, 
         acc += w[0][i] * w[1][j] * w[2][k] * rf[fq];
       }
   rc[q] = acc;
+  if (cs.d) {  // start of the coarse level's Chebyshev smoother (ChebStart)
+    const T v = cs.dinv[q] * acc * cs.inv_theta;
+    cs.d[q] = v;
+    cs.x[q] = v;
+  }
 }
 
 template <typename T, int DIM>
@@ -445,7 +477,7 @@ struct PRestrictK {
   using Args = PXferArgs<T>;
   static constexpr int THREADS = TPB, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int) {
-    p_restrict_body<T, DIM>(a.gf, a.gc, a.mf, a.mc, a.in, a.out, blk);
+    p_restrict_body<T, DIM>(a.gf, a.gc, a.mf, a.mc, a.in, a.out, a.cs, blk);
   }
 };
 template <typename T, int DIM>
@@ -498,15 +530,15 @@ cudaError_t launch_plap_diag(const Geom& g, const T* kc, const T* w, const uint8
 }
 template <typename T>
 cudaError_t launch_p_restrict(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* rf, T* rc,
-                              cudaStream_t st) {
-  const PXferArgs<T> a{gf, gc, mf, mc, rf, rc};
+                              cudaStream_t st, const T* dinv, T inv_theta, T* d, T* x) {
+  const PXferArgs<T> a{gf, gc, mf, mc, rf, rc, ChebStart<T>{dinv, inv_theta, d, x}};
   if (gf.dim == 2) return submit<PRestrictK<T, 2>>(a, nblk(gc.Np), 0, st);
   return submit<PRestrictK<T, 3>>(a, nblk(gc.Np), 0, st);
 }
 template <typename T>
 cudaError_t launch_p_prolong_add(const Geom& gf, const Geom& gc, const uint8_t* mf, const uint8_t* mc, const T* xc,
                                  T* xf, cudaStream_t st) {
-  const PXferArgs<T> a{gf, gc, mf, mc, xc, xf};
+  const PXferArgs<T> a{gf, gc, mf, mc, xc, xf, ChebStart<T>{nullptr, T(0), nullptr, nullptr}};
   if (gf.dim == 2) return submit<PProlongAddK<T, 2>>(a, nblk(gf.Np), 0, st);
   return submit<PProlongAddK<T, 3>>(a, nblk(gf.Np), 0, st);
 }
@@ -523,7 +555,7 @@ cudaError_t launch_cc_combine(const T* m, const T* v, const uint8_t* mask, T alp
   template cudaError_t launch_plap<T>(int, PLapArgs<T>, cudaStream_t);                                    \
   template cudaError_t launch_plap_diag<T>(const Geom&, const T*, const T*, const uint8_t*, T*, cudaStream_t); \
   template cudaError_t launch_p_restrict<T>(const Geom&, const Geom&, const uint8_t*, const uint8_t*,      \
-                                            const T*, T*, cudaStream_t);                                  \
+                                            const T*, T*, cudaStream_t, const T*, T, T*, T*);             \
   template cudaError_t launch_p_prolong_add<T>(const Geom&, const Geom&, const uint8_t*, const uint8_t*,   \
                                                const T*, T*, cudaStream_t);                               \
   template cudaError_t launch_mask_copy<T>(const T*, const uint8_t*, T*, long long, cudaStream_t);        \
