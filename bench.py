@@ -143,6 +143,21 @@ def cpu_baseline_entry(res):
                        f"to rel-res 1e-8 ({statistics.median(res['it'])} iterations), median of {len(res['t'])}")}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest value of x over the ranks of the default process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(unknowns_per_rank: int, steps: int, world: int, max_total_ms: float) -> float:
+    """GDoF/s of the whole job: unknowns solved by all ranks / the max-over-ranks timed region."""
+    return unknowns_per_rank * steps * world / (max_total_ms * 1e-3) / 1e9
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -238,13 +253,9 @@ def run_gpu(args, rank, world):
     barrier()
     clk = clocks.stop()
     launches = solver.info().kernel_launches - launches0 - 0
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = N * args.steps * world / (total_ms * 1e-3) / 1e9
+    value = whole_job_value(N, args.steps, world, total_ms)
 
     # ---- per-kernel profile of one solve (dominant kernel, roofline) ----
     solver.profile(True)
