@@ -186,7 +186,10 @@ NCU_TRAFFIC_BYTES = {"cheb_step": 39.409664e6 + 6.144e3, "saddle_fp64": 24.76902
 
 
 def algorithmic_cost(kind, dim, n_cells, n_u, n_p, elem_bytes):
-    """Algorithmic bytes / flops per launch of the dominant kernel classes."""
+    """Algorithmic bytes / flops per launch of the dominant kernel classes.  Chebyshev step: x, b, d,
+    D^-1 read and d, x' written (6 vectors of d N_v entries) plus eta per cell; residual: x, b read
+    and r written; FP64 saddle: x and y of the full vector plus eta, 534 flops per cell for A and
+    75 each for B and B^T (2D sum-factorised sweeps)."""
     if kind == "saddle_fp64":
         # flops of the sum-factorised cell operator (A, B^T, B) per cell, 2D
         return {"flops": n_cells * (534 + 2 * 75), "bytes": 8 * (2 * (n_u + n_p)) + 8 * n_cells}
