@@ -641,6 +641,15 @@ def run_spheres(args):
                     "unknowns": s.n_total, "deflation_inclusions": inf.deflation_inclusions,
                     "deflation_modes": inf.deflation_modes}
         if prec == 32:
+            x32 = x.clone()
+        else:  # FP32- against FP64-multigrid solution (both FP64 FGMRES to rel-res 1e-8); velocity part
+            # and whole vector (the pressure inside an eta = 1e6 sphere is pinned only to ~1e-3)
+            n_u = s.n_u
+            out[key]["velocity_rel_diff_vs_fp32mg"] = float(torch.linalg.vector_norm(x[:n_u] - x32[:n_u]) /
+                                                            torch.linalg.vector_norm(x[:n_u]))
+            out[key]["solution_rel_diff_vs_fp32mg"] = float(torch.linalg.vector_norm(x - x32) /
+                                                            torch.linalg.vector_norm(x))
+        if prec == 32:
             for dt, name in ((torch.float32, "fp32"), (torch.float64, "fp64")):
                 xx = torch.randn(s.n_u, dtype=dt, device=dev)
                 yy = torch.empty_like(xx)
