@@ -156,65 +156,6 @@ __device__ __forceinline__ void cell_A2(int comp, const T (&x)[2][9], T (&y)[9],
   }
 }
 
-template <typename T, int COMP>
-__device__ __forceinline__ void cell_A3(const T (&x)[3][27], T (&y)[27], T eta, const OpCoef<T>& c) {
-  T a[27], k[27], b[27];
-  // diagonal block
-  sweep<OpM, 2, 3, 3, 3, false>(x[COMP], a);
-  sweep<OpK, 2, 3, 3, 3, false>(x[COMP], k);
-  {
-    const T ckz = (COMP == 2 ? T(2) : T(1)) * eta * c.km[2];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) b[i] = c.mm * a[i] + ckz * k[i];
-  }
-  // k <- My b + cky Ky a
-  sweep<OpM, 1, 3, 3, 3, false>(b, k);
-  sweep<OpK, 1, 3, 3, 3, false>(a, b);
-  {
-    const T cky = (COMP == 1 ? T(2) : T(1)) * eta * c.km[1];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] += cky * b[i];
-  }
-  // b <- ckx My a
-  sweep<OpM, 1, 3, 3, 3, false>(a, b);
-  {
-    const T ckx = (COMP == 0 ? T(2) : T(1)) * eta * c.km[0];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) b[i] *= ckx;
-  }
-  sweep<OpM, 0, 3, 3, 3, false>(k, y);
-  sweep<OpK, 0, 3, 3, 3, true>(b, y);
-  // off-diagonal blocks; the direction of the output component is applied last
-  if (COMP == 0) {
-    sweep<OpM, 2, 3, 3, 3, false>(x[1], a);
-    sweep<OpE, 1, 3, 3, 3, false>(a, k);
-    sweep<OpE, 2, 3, 3, 3, false>(x[2], a);
-    sweep<OpM, 1, 3, 3, 3, false>(a, b);
-    const T c1 = eta * c.ex[2], c2 = eta * c.ex[1];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
-    sweep<OpET, 0, 3, 3, 3, true>(k, y);
-  } else if (COMP == 1) {
-    sweep<OpM, 2, 3, 3, 3, false>(x[0], a);
-    sweep<OpE, 0, 3, 3, 3, false>(a, k);
-    sweep<OpE, 2, 3, 3, 3, false>(x[2], a);
-    sweep<OpM, 0, 3, 3, 3, false>(a, b);
-    const T c1 = eta * c.ex[2], c2 = eta * c.ex[0];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
-    sweep<OpET, 1, 3, 3, 3, true>(k, y);
-  } else {
-    sweep<OpM, 1, 3, 3, 3, false>(x[0], a);
-    sweep<OpE, 0, 3, 3, 3, false>(a, k);
-    sweep<OpE, 1, 3, 3, 3, false>(x[1], a);
-    sweep<OpM, 0, 3, 3, 3, false>(a, b);
-    const T c1 = eta * c.ex[1], c2 = eta * c.ex[0];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
-    sweep<OpET, 2, 3, 3, 3, true>(k, y);
-  }
-}
-
 // ---- 3D cell operators reading their input nodes from a shared-memory window ----------------------
 // x_a points to the cell's local node (0, 0, 0) of component a in the window; local node (i, j, k)
 // sits at x_a[i + ro[j] + po[k]] (row and plane offsets of the cell, which absorb any skew of the
@@ -250,63 +191,6 @@ __device__ __forceinline__ void sweep_w(const T* __restrict__ in, const int* ro,
   }
 }
 
-template <typename T, int COMP>
-__device__ __forceinline__ void cell_A3w(const T* x0, const T* x1, const T* x2, const int* ro, const int* po,
-                                         T (&y)[27], T eta, const OpCoef<T>& c) {
-  const T* xc = COMP == 0 ? x0 : (COMP == 1 ? x1 : x2);
-  T a[27], k[27], b[27];
-  sweep_w<OpM, 2>(xc, ro, po, a);
-  sweep_w<OpK, 2>(xc, ro, po, k);
-  {
-    const T ckz = (COMP == 2 ? T(2) : T(1)) * eta * c.km[2];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) b[i] = c.mm * a[i] + ckz * k[i];
-  }
-  sweep<OpM, 1, 3, 3, 3, false>(b, k);
-  sweep<OpK, 1, 3, 3, 3, false>(a, b);
-  {
-    const T cky = (COMP == 1 ? T(2) : T(1)) * eta * c.km[1];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] += cky * b[i];
-  }
-  sweep<OpM, 1, 3, 3, 3, false>(a, b);
-  {
-    const T ckx = (COMP == 0 ? T(2) : T(1)) * eta * c.km[0];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) b[i] *= ckx;
-  }
-  sweep<OpM, 0, 3, 3, 3, false>(k, y);
-  sweep<OpK, 0, 3, 3, 3, true>(b, y);
-  if (COMP == 0) {
-    sweep_w<OpM, 2>(x1, ro, po, a);
-    sweep<OpE, 1, 3, 3, 3, false>(a, k);
-    sweep_w<OpE, 2>(x2, ro, po, a);
-    sweep<OpM, 1, 3, 3, 3, false>(a, b);
-    const T c1 = eta * c.ex[2], c2 = eta * c.ex[1];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
-    sweep<OpET, 0, 3, 3, 3, true>(k, y);
-  } else if (COMP == 1) {
-    sweep_w<OpM, 2>(x0, ro, po, a);
-    sweep<OpE, 0, 3, 3, 3, false>(a, k);
-    sweep_w<OpE, 2>(x2, ro, po, a);
-    sweep<OpM, 0, 3, 3, 3, false>(a, b);
-    const T c1 = eta * c.ex[2], c2 = eta * c.ex[0];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
-    sweep<OpET, 1, 3, 3, 3, true>(k, y);
-  } else {
-    sweep_w<OpM, 1>(x0, ro, po, a);
-    sweep<OpE, 0, 3, 3, 3, false>(a, k);
-    sweep_w<OpE, 1>(x1, ro, po, a);
-    sweep<OpM, 0, 3, 3, 3, false>(a, b);
-    const T c1 = eta * c.ex[1], c2 = eta * c.ex[0];
-#pragma unroll
-    for (int i = 0; i < 27; ++i) k[i] = c1 * k[i] + c2 * b[i];
-    sweep<OpET, 2, 3, 3, 3, true>(k, y);
-  }
-}
-
 // ---- divergence block B and its transpose -----------------------------------------------------
 // (B u)_q = - sum_b int psi_q d phi_j/dx_b u_jb :  -sum_b (G in direction b, N elsewhere) u_b
 template <typename T>
@@ -333,29 +217,14 @@ __device__ __forceinline__ void cell_BT2(const T (&p)[4], T (&u)[2][9], const Op
   for (int i = 0; i < 9; ++i) u[1][i] = (acc ? u[1][i] : T(0)) - c.bd[1] * v[i];
 }
 
-template <typename T>
-__device__ __forceinline__ void cell_B3(const T (&u)[3][27], T (&out)[8], const OpCoef<T>& c) {
-  T t0[18], t1[18], s0[12], s1[12], o[8];
-  sweep<OpN, 2, 3, 3, 3, false>(u[0], t0);  // (3,3,2)
-  sweep<OpN, 2, 3, 3, 3, false>(u[1], t1);
-  sweep<OpN, 1, 3, 3, 2, false>(t0, s0);    // (3,2,2)
-  sweep<OpG, 0, 3, 2, 2, false>(s0, out);   // (2,2,2)
-  sweep<OpG, 1, 3, 3, 2, false>(t1, s1);
-  sweep<OpG, 2, 3, 3, 3, false>(u[2], t0);
-  sweep<OpN, 1, 3, 3, 2, false>(t0, s0);
-  const T c1 = c.bd[1], c2 = c.bd[2];
-#pragma unroll
-  for (int i = 0; i < 12; ++i) s1[i] = c1 * s1[i] + c2 * s0[i];
-  sweep<OpN, 0, 3, 2, 2, false>(s1, o);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) out[i] = -(c.bd[0] * out[i] + o[i]);
-}
-
 // ---- 3D operator in a rotated frame: one code path for every output component ------------------
 // Local node (i, j, k) of the window sits at in[o0[i] + o1[j] + o2[k]]: the three offset tables map
 // the logical axes to any physical axes.  A thread computing output component a uses the frame
 // (a, a + 1, a + 2) (cyclic), rotated coefficients, and its own component as the logical x input,
-// so the component-0 expression of cell_A3w serves all three components (one instruction stream).
+// so one expression -- the one for output component 0 -- serves all three components (one
+// instruction stream).  Diagonal block: alpha MMM + eta (1 + [a = x]) KMM + eta (1 + [a = y]) MKM +
+// eta (1 + [a = z]) MMK; off-diagonal blocks: eta (E in direction b) (E^T in direction a) (M in
+// the third direction).
 template <class Op, int AX, typename T>
 __device__ __forceinline__ void sweep_p(const T* __restrict__ in, const int* o0, const int* o1, const int* o2,
                                         T* __restrict__ out) {
@@ -425,8 +294,8 @@ __device__ __forceinline__ void cell_A3p(const T* xc, const T* x1, const T* x2, 
   sweep<OpET, 0, 3, 3, 3, true>(k, y);
 }
 
-// B^T contribution to output component "logical x" in the rotated frame (cell_BT3<T, 0> with the
-// pressure nodes given in the logical frame and the output axis's coefficient bd_a)
+// B^T contribution to output component "logical x" in the rotated frame: -bd_a (Gi^T along x, Ni^T
+// along y and z) applied to the cell's pressure nodes given in the logical frame
 template <typename T>
 __device__ __forceinline__ void cell_BT3p(const T (&p)[8], T (&u)[27], T bd_a, bool acc) {
   T a[12], b[18], v[27];
@@ -437,7 +306,8 @@ __device__ __forceinline__ void cell_BT3p(const T (&p)[8], T (&u)[27], T bd_a, b
   for (int i = 0; i < 27; ++i) u[i] = (acc ? u[i] : T(0)) - bd_a * v[i];
 }
 
-// (B u) of one 3D cell with the velocity read from a shared-memory window (sweeps of cell_B3)
+// (B u) of one 3D cell with the velocity read from a shared-memory window:
+// (B u)_q = -sum_b bd[b] (Gi in direction b, Ni elsewhere) u_b
 template <typename T>
 __device__ __forceinline__ void cell_B3w(const T* u0, const T* u1, const T* u2, const int* ro, const int* po,
                                          T (&out)[8], const OpCoef<T>& c) {
@@ -455,18 +325,6 @@ __device__ __forceinline__ void cell_B3w(const T* u0, const T* u1, const T* u2, 
   sweep<OpN, 0, 3, 2, 2, false>(s1v, o);
 #pragma unroll
   for (int i = 0; i < 8; ++i) out[i] = -(c.bd[0] * out[i] + o[i]);
-}
-
-// B^T restricted to one output component (3D threads split by component)
-template <typename T, int COMP>
-__device__ __forceinline__ void cell_BT3(const T (&p)[8], T (&u)[27], const OpCoef<T>& c, bool acc) {
-  T a[12], b[18], v[27];
-  if (COMP == 2) sweep<OpGT, 2, 2, 2, 2, false>(p, a); else sweep<OpNT, 2, 2, 2, 2, false>(p, a);  // (2,2,3)
-  if (COMP == 1) sweep<OpGT, 1, 2, 2, 3, false>(a, b); else sweep<OpNT, 1, 2, 2, 3, false>(a, b);  // (2,3,3)
-  if (COMP == 0) sweep<OpGT, 0, 2, 3, 3, false>(b, v); else sweep<OpNT, 0, 2, 3, 3, false>(b, v);  // (3,3,3)
-  const T s = c.bd[COMP];
-#pragma unroll
-  for (int i = 0; i < 27; ++i) u[i] = (acc ? u[i] : T(0)) - s * v[i];
 }
 
 // ---- diagonal of the viscous + mass block at one local node -------------------------------------

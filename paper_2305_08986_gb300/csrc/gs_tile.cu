@@ -20,12 +20,6 @@ namespace gs {
 template <int DIM>
 struct TileShape;
 template <>
-struct TileShape<2> {  // (2D launches use gs_tile2d.cu; kept for completeness of the template)
-  static constexpr int TC0 = 32, TC1 = 16, TC2 = 1;
-  static constexpr int G0 = 16, G1 = 8, G2 = 1;
-  static constexpr int SPLIT = 1;
-};
-template <>
 struct TileShape<3> {  // 8^3 evaluated cells, 7^3 owned; one thread per (2x2x2 group, component)
   static constexpr int TC0 = 8, TC1 = 8, TC2 = 8;
   static constexpr int G0 = 4, G1 = 4, G2 = 4;
@@ -52,225 +46,12 @@ __device__ __forceinline__ int owned_p_ext(int cs, int TO, int n) {
   return (cs + TO >= n) ? (n + 1 - cs) : TO;
 }
 
-template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
-__device__ __forceinline__ void tile_body(const TileArgs<T>& A, int bid) {
-  using S = TileShape<DIM>;
-  using D = TileDims<DIM>;
-  constexpr int NN = DIM == 2 ? 9 : 27;  // Q2 nodes per cell
-  constexpr int NP = DIM == 2 ? 4 : 8;   // Q1 nodes per cell
-  constexpr bool WU = WA || WBT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* su = reinterpret_cast<T*>(smem_raw);
-  T* sp = su + (WU ? DIM * D::VSZ : 0);
-  const Geom& g = A.g;
-  const OpCoef<T>& c = A.c;
-
-  int tile = bid;
-  const int t0 = tile % A.tiles[0];
-  tile /= A.tiles[0];
-  const int t1 = tile % A.tiles[1];
-  const int t2 = tile / A.tiles[1];
-  const int cs0 = t0 * (S::TC0 - 1);
-  const int cs1 = t1 * (S::TC1 - 1);
-  const int cs2 = DIM == 3 ? t2 * (S::TC2 - 1) : 0;
-  const int ve0 = owned_v_ext(cs0, S::TC0 - 1, g.n[0]);
-  const int ve1 = owned_v_ext(cs1, S::TC1 - 1, g.n[1]);
-  const int ve2 = DIM == 3 ? owned_v_ext(cs2, S::TC2 - 1, g.n[2]) : 1;
-  const int pe0 = owned_p_ext(cs0, S::TC0 - 1, g.n[0]);
-  const int pe1 = owned_p_ext(cs1, S::TC1 - 1, g.n[1]);
-  const int pe2 = DIM == 3 ? owned_p_ext(cs2, S::TC2 - 1, g.n[2]) : 1;
-
-  const int tot = (WU ? DIM * D::VSZ : 0) + (WB ? D::PSZ : 0);
-  for (int i = threadIdx.x; i < tot; i += D::THREADS) su[i] = T(0);
-  __syncthreads();
-
-  const int comp = threadIdx.x / D::NG;  // warp-uniform component (3D)
-  const int grp = threadIdx.x % D::NG;
-  const int g0 = grp % S::G0;
-  const int g1 = (grp / S::G0) % S::G1;
-  const int g2 = grp / (S::G0 * S::G1);
-  const long long Nv = g.Nv;
-  const bool raw = A.raw != 0;
-
-#pragma unroll 1
-  for (int ph = 0; ph < (1 << DIM); ++ph) {
-    const int l0 = 2 * g0 + (ph & 1);
-    const int l1 = 2 * g1 + ((ph >> 1) & 1);
-    const int l2 = DIM == 3 ? 2 * g2 + ((ph >> 2) & 1) : 0;
-    const int c0 = cs0 - 1 + l0, c1 = cs1 - 1 + l1, c2 = DIM == 3 ? cs2 - 1 + l2 : 0;
-    bool active = c0 >= 0 && c0 < g.n[0] && c1 >= 0 && c1 < g.n[1];
-    if (DIM == 3) active = active && c2 >= 0 && c2 < g.n[2];
-    long long cell = 0;
-    if (active) {
-      cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
-      if (cell_void(g, cell)) active = false;
-    }
-    if (active) {
-      const T eta = A.eta[cell] * c.eta_scale;
-      OpCoef<T> cK = c;  // the cell's mass coefficient (alpha per cell)
-      if (A.alpha) cK.mm = c.mm * A.alpha[cell];
-      T xl[DIM][NN];
-      T pl[NP];
-      const bool need_u = WA || (WB && comp == 0);
-      if (need_u) {
-#pragma unroll
-        for (int lc = 0; lc < (DIM == 3 ? 3 : 1); ++lc)
-#pragma unroll
-          for (int lb = 0; lb < 3; ++lb)
-#pragma unroll
-            for (int la = 0; la < 3; ++la) {
-              const int I = 2 * c0 + la, J = 2 * c1 + lb, K = 2 * c2 + lc;
-              const long long node = I + (long long)g.nv[0] * (J + (long long)g.nv[1] * K);
-              const bool con = !raw && vnode_constrained(g, node, I, J, K);
-#pragma unroll
-              for (int a = 0; a < DIM; ++a)
-                xl[a][la + 3 * lb + 9 * lc] = con ? T(0) : ldg(A.xu + a * Nv + node);
-            }
-      }
-      if (WBT) {
-#pragma unroll
-        for (int lc = 0; lc < (DIM == 3 ? 2 : 1); ++lc)
-#pragma unroll
-          for (int lb = 0; lb < 2; ++lb)
-#pragma unroll
-            for (int la = 0; la < 2; ++la) {
-              const long long q = (c0 + la) + (long long)g.npn[0] * ((c1 + lb) + (long long)g.npn[1] * (c2 + lc));
-              const bool con = !raw && pnode_constrained(g, q);
-              pl[la + 2 * lb + 4 * lc] = con ? T(0) : ldg(A.xp + q);
-            }
-      }
-      if (WU) {
-        if (DIM == 2) {
-          T yl[2][9];
-          if (WA) {
-            cell_A2(0, reinterpret_cast<const T(&)[2][9]>(xl), yl[0], eta, cK);
-            cell_A2(1, reinterpret_cast<const T(&)[2][9]>(xl), yl[1], eta, cK);
-          }
-          if (WBT) cell_BT2(reinterpret_cast<const T(&)[4]>(pl), yl, c, WA);
-#pragma unroll
-          for (int lb = 0; lb < 3; ++lb) {
-            const int i1 = 2 * (l1 - 1) + lb;
-            if (i1 < 0 || i1 >= ve1) continue;
-#pragma unroll
-            for (int la = 0; la < 3; ++la) {
-              const int i0 = 2 * (l0 - 1) + la;
-              if (i0 < 0 || i0 >= ve0) continue;
-              const int s = i0 + D::VE0 * i1;
-              su[s] += yl[0][la + 3 * lb];
-              su[D::VSZ + s] += yl[1][la + 3 * lb];
-            }
-          }
-        } else {
-          T yl[27];
-          const T(&x3)[3][27] = reinterpret_cast<const T(&)[3][27]>(xl);
-          const T(&p3)[8] = reinterpret_cast<const T(&)[8]>(pl);
-          if (comp == 0) {
-            if (WA) cell_A3<T, 0>(x3, yl, eta, cK);
-            if (WBT) cell_BT3<T, 0>(p3, yl, c, WA);
-          } else if (comp == 1) {
-            if (WA) cell_A3<T, 1>(x3, yl, eta, cK);
-            if (WBT) cell_BT3<T, 1>(p3, yl, c, WA);
-          } else {
-            if (WA) cell_A3<T, 2>(x3, yl, eta, cK);
-            if (WBT) cell_BT3<T, 2>(p3, yl, c, WA);
-          }
-          T* sc = su + comp * D::VSZ;
-#pragma unroll
-          for (int lc = 0; lc < 3; ++lc) {
-            const int i2 = 2 * (l2 - 1) + lc;
-            if (i2 < 0 || i2 >= ve2) continue;
-#pragma unroll
-            for (int lb = 0; lb < 3; ++lb) {
-              const int i1 = 2 * (l1 - 1) + lb;
-              if (i1 < 0 || i1 >= ve1) continue;
-#pragma unroll
-              for (int la = 0; la < 3; ++la) {
-                const int i0 = 2 * (l0 - 1) + la;
-                if (i0 < 0 || i0 >= ve0) continue;
-                sc[i0 + D::VE0 * (i1 + D::VE1 * i2)] += yl[la + 3 * lb + 9 * lc];
-              }
-            }
-          }
-        }
-      }
-      if (WB && comp == 0) {
-        T ob[NP];
-        if (DIM == 2)
-          cell_B2(reinterpret_cast<const T(&)[2][9]>(xl), reinterpret_cast<T(&)[4]>(ob), c);
-        else
-          cell_B3(reinterpret_cast<const T(&)[3][27]>(xl), reinterpret_cast<T(&)[8]>(ob), c);
-#pragma unroll
-        for (int lc = 0; lc < (DIM == 3 ? 2 : 1); ++lc) {
-          const int i2 = (l2 - 1) + lc;
-          if (DIM == 3 && (i2 < 0 || i2 >= pe2)) continue;
-#pragma unroll
-          for (int lb = 0; lb < 2; ++lb) {
-            const int i1 = (l1 - 1) + lb;
-            if (i1 < 0 || i1 >= pe1) continue;
-#pragma unroll
-            for (int la = 0; la < 2; ++la) {
-              const int i0 = (l0 - 1) + la;
-              if (i0 < 0 || i0 >= pe0) continue;
-              sp[i0 + D::PE0 * (i1 + D::PE1 * (DIM == 3 ? i2 : 0))] += ob[la + 2 * lb + 4 * lc];
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---- write back owned velocity nodes ----
-  if (WU) {
-    const int nown = ve0 * ve1 * ve2;
-    for (int i = threadIdx.x; i < nown; i += D::THREADS) {
-      const int i0 = i % ve0;
-      const int i1 = (i / ve0) % ve1;
-      const int i2 = i / (ve0 * ve1);
-      const int I = 2 * cs0 + i0, J = 2 * cs1 + i1, K = 2 * cs2 + i2;
-      const long long node = I + (long long)g.nv[0] * (J + (long long)g.nv[1] * K);
-      const bool con = !raw && vnode_constrained(g, node, I, J, K);
-      const int s = i0 + D::VE0 * (i1 + D::VE1 * i2);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const long long gi = a * Nv + node;
-        const T ax = con ? (WA ? A.xu[gi] : T(0)) : su[a * D::VSZ + s];
-        if (MODE == TILE_APPLY) {
-          A.yu[gi] = ax;
-        } else if (MODE == TILE_RESID) {
-          A.yu[gi] = A.bu[gi] - ax;
-        } else {
-          const T r = A.bu[gi] - ax;
-          T dn = A.c2 * A.dinv[gi] * r;
-          if (A.use_d) dn += A.c1 * A.d[gi];
-          A.d[gi] = dn;
-          A.xout[gi] = A.xu[gi] + dn;
-        }
-      }
-    }
-  }
-  if (WB) {
-    const int nown = pe0 * pe1 * pe2;
-    for (int i = threadIdx.x; i < nown; i += D::THREADS) {
-      const int i0 = i % pe0;
-      const int i1 = (i / pe0) % pe1;
-      const int i2 = i / (pe0 * pe1);
-      const long long q = (cs0 + i0) + (long long)g.npn[0] * ((cs1 + i1) + (long long)g.npn[1] * (cs2 + i2));
-      const bool con = !raw && pnode_constrained(g, q);
-      const T bx = con ? (WBT ? A.xp[q] : T(0)) : sp[i0 + D::PE0 * (i1 + D::PE1 * i2)];
-      if (MODE == TILE_RESID)
-        A.yp[q] = A.bp[q] - bx;
-      else
-        A.yp[q] = bx;
-    }
-  }
-}
-
 // ---- 3D tile with a staged input window --------------------------------------------------------
 // The CTA copies the velocity nodes of all its evaluated cells (a W^3 window per component, W =
 // 2 TC0 + 1, with cp.async: zero fill outside the mesh and on constrained nodes) and, for B^T, the
-// pressure nodes (PW^3), then runs the parity-class phases of tile_body with every cell reading
-// its nodes from the window.  Outputs and epilogue as in tile_body.
+// pressure nodes (PW^3), then runs the 8 parity-class phases (one cell and one output component
+// per thread), every cell reading its nodes from the window, and writes the owned nodes with the
+// mode's epilogue.
 namespace {
 template <typename T>
 __device__ __forceinline__ void cp_async_3d(T* smem, const T* gmem, bool load) {
@@ -546,11 +327,9 @@ template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
 struct TileK {
   using Args = TileArgs<T>;
   static constexpr int THREADS = TileDims<DIM>::THREADS, MINB = 1;
+  static_assert(DIM == 3, "2D launches use the tiles of gs_tile2d.cuh");
   static __device__ __forceinline__ void body(const Args& a, int blk, int) {
-    if constexpr (DIM == 3)
-      tile3d_body<T, MODE, WA, WBT, WB>(a, blk);
-    else
-      tile_body<T, DIM, MODE, WA, WBT, WB>(a, blk);
+    tile3d_body<T, MODE, WA, WBT, WB>(a, blk);
   }
 };
 
