@@ -143,6 +143,32 @@ def cpu_baseline_entry(res):
                        f"to rel-res 1e-8 ({statistics.median(res['it'])} iterations), median of {len(res['t'])}")}
 
 
+def krylov_bytes(n: int, iterations: int, restart: int):
+    """Algorithmic HBM bytes of the CGS2 kernels over one solve (double-float basis, 8 B per entry,
+    iteration k uses the j + 1 = (k mod restart) + 1 basis rows of its cycle):
+      first pass (strip dots): the j + 1 rows and w, read once;
+      second pass (update + dots) and third pass (update + norm): the j + 1 rows read, w read and
+      written, each; the new basis vector: w read, v (double-float) and v (double) written."""
+    dots = axpy = 0
+    for k in range(iterations):
+        rows = (k % restart) + 1
+        dots += (rows + 1) * n * 8
+        axpy += 2 * (rows + 2) * n * 8 + 3 * n * 8
+    return dots, axpy
+
+
+def krylov_rooflines(prof: dict, n: int, iterations: int, restart: int, peak_gbs: float):
+    """Achieved GB/s and fraction of the measured HBM peak of the Gram-Schmidt classes, from the
+    live per-class device time of one solve (CUDA events, one pair per launch: slightly long)."""
+    dots_b, axpy_b = krylov_bytes(n, iterations, restart)
+    out = {}
+    for cls, b in (("gram_schmidt_dots", dots_b), ("krylov_axpy", axpy_b)):
+        if cls in prof and prof[cls][1] > 0:
+            gbs = b / (prof[cls][1] * 1e-3) / 1e9
+            out[cls] = {"algorithmic_bytes": b, "ms": prof[cls][1], "achieved_gbs": gbs, "frac": gbs / peak_gbs}
+    return out
+
+
 def max_over_ranks(x: float, dist=None, device="cpu") -> float:
     """Largest value of x over the ranks of the default process group (x itself without one)."""
     if dist is None:
@@ -288,6 +314,12 @@ def run_gpu(args, rank, world):
                     "frac": ach / peak, "traffic": NCU_TRAFFIC_BYTES.get(dom[0]), "avg_launch_us": avg_s * 1e6,
                     "launches": dom[1][0], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
 
+    krylov_table = None
+    try:  # secondary figures: never let them break the bench line
+        krylov_table = krylov_rooflines(prof, N, int(statistics.median(its)), args.restart, peaks.get("hbm_gbs", 6800.0))
+    except Exception as ex:
+        krylov_table = {"error": str(ex)}
+
     # ---- A x throughput (FP64 / FP32), L2 flushed between launches ----
     def time_apply(dtype, reps=30):
         xx = torch.randn(n_u, dtype=dtype, device=dev)
@@ -404,6 +436,7 @@ def run_gpu(args, rank, world):
             "fp64_multigrid": fp64,
             "monolithic_precond": mono,
             "roofline": roof,
+            "krylov_rooflines": krylov_table,
             "kernel_profile_ms": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
             "cpu_baseline": cb,
             "e2e": {"value": N / (e2e_t * 1e-3) / 1e9, "unit": "GDoF/s", "ms": e2e_t,
