@@ -35,6 +35,13 @@ Readings taken here (the paper gives the ingredients, not the loop):
   rows of M_j are identity rows that never couple to free entries; the preconditioner returns
   z = r on them, as the block-triangular one does.
 
+Corrector mode (option corrector = (v°, rho), Sec. 4 for a non-symmetric A): every level's
+velocity block is the corrector block of corrector.py (convection by v° injected to the level,
+streamline diffusion), diag and the Chebyshev bounds are those of that block (Lanczos on its
+symmetric part), and Shat^{-1} = ChebBiCGStab(n_S, k_S = 1): n_S BiCGStab steps on
+S = B Ahat^{-1} B^T with the same preconditioner (the paper replaces MINRES by BiCGStab when A is
+not symmetric).
+
 Parity pins (tests): the smoother inverts the block matrix of Eq. "smoother" when Shat^{-1} is
 an exact inverse; one MINRES step equals the closed-form minimiser of the preconditioned
 residual norm, is invariant to scaling the preconditioner, and n MINRES steps solve an n x n
@@ -46,11 +53,46 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse as sp
 
 from .fem import System
 from .mesh import Mesh
-from .mg import Hierarchy, chebyshev
+from .mg import Hierarchy, chebyshev, lanczos_max, lanczos_start
 from .pressure import q1_prolongation
+
+
+def bicgstab(apply_S, apply_P, b, steps):
+    """`steps` iterations of preconditioned BiCGStab for S x = b from x = 0 (van der Vorst 1992, with
+    the preconditioner P applied to the search directions; shadow residual = b)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    rh = b.copy()
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    for _ in range(steps):
+        rho_new = float(rh @ r)
+        if rho_new == 0.0:
+            break
+        beta = (rho_new / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = apply_P(p)
+        v = apply_S(ph)
+        den = float(rh @ v)
+        if den == 0.0:
+            break
+        alpha = rho_new / den
+        s_ = r - alpha * v
+        sh = apply_P(s_)
+        t = apply_S(sh)
+        tt = float(t @ t)
+        omega = float(t @ s_) / tt if tt > 0.0 else 0.0
+        x = x + alpha * ph + omega * sh
+        r = s_ - omega * t
+        rho_old = rho_new
+        if omega == 0.0:
+            break
+    return x
 
 
 def minres(apply_S, apply_P, b, steps):
@@ -99,17 +141,21 @@ def minres(apply_S, apply_P, b, steps):
 
 
 class SaddleLevel:
-    def __init__(self, mesh: Mesh, eta, alpha, index):
+    def __init__(self, mesh: Mesh, eta, alpha, index, A=None):
+        """A: the level's velocity block when it is not System's (corrector mode)."""
         self.mesh = mesh
         self.index = index
         self.sys = System(mesh, eta, alpha)
-        self.K = self.sys.K
+        self.A = self.sys.A if A is None else A
+        self.K = self.sys.K if A is None else sp.bmat([[A, self.sys.B.T], [self.sys.B, self.sys.C]]).tocsr()
         self.B = self.sys.B
         self.n_u = mesh.n_u
         self.Pp = None  # pressure prolongation from level index-1
         self.Pu = None
+        self.D = self.A.diagonal()
+        self.lam_hi = None
         # D_S = diag(B diag(A)^{-1} B^T): sum over velocity entries j of B_qj^2 / A_jj
-        D = self.sys.A.diagonal()
+        D = self.D
         ds = np.asarray(self.B.multiply(self.B) @ (1.0 / D)).ravel()
         self.ds = ds
         self.dsinv = np.where(ds > 0.0, 1.0 / np.where(ds > 0.0, ds, 1.0), 0.0)
@@ -119,7 +165,7 @@ class MonolithicHierarchy:
     """Saddle-point multigrid of Sec. 4, levels[0] = coarsest."""
 
     def __init__(self, fine: Mesh, eta_fine, alpha, nlevels, degree=4, smooth=2, cycles=1, schur_steps=1,
-                 seed=0, coarse="dense"):
+                 seed=0, coarse="dense", corrector=None):
         self.vel = Hierarchy(fine, eta_fine, alpha, nlevels, degree=degree, seed=seed,
                              coarse="chebyshev" if coarse == "chebyshev" else "cholesky")
         meshes = [lv.mesh for lv in self.vel.levels]
@@ -130,7 +176,27 @@ class MonolithicHierarchy:
         self.cycles = cycles
         self.schur_steps = schur_steps
         self.coarse = coarse
-        self.levels = [SaddleLevel(m, e, a, i) for i, (m, e, a) in enumerate(zip(meshes, etas, alphas))]
+        self.corrector = corrector is not None
+        blocks = [None] * len(meshes)
+        if corrector is not None:
+            from .corrector import convection_matrices, inject
+            from .fem import _eliminate
+            vcirc, rho = corrector
+            fields = [np.asarray(vcirc, dtype=float)]
+            for i in range(len(meshes) - 1, 0, -1):
+                fields.append(inject(meshes[i], meshes[i - 1], fields[-1]))
+            fields = fields[::-1]
+            for i, lv in enumerate(self.vel.levels):
+                Craw, Sraw = convection_matrices(lv.mesh, fields[i], lv.eta, rho)
+                blocks[i] = _eliminate((lv.sys.A_raw + Craw + Sraw).tocsr(), lv.sys.u_constrained)
+        self.levels = [SaddleLevel(m, e, a, i, blocks[i]) for i, (m, e, a) in enumerate(zip(meshes, etas, alphas))]
+        for i, lv in enumerate(self.levels):
+            if corrector is None:
+                lv.lam_hi = self.vel.levels[i].lam_hi
+            elif i > 0 or coarse == "chebyshev":
+                v0 = lanczos_start(lv.mesh.n_u, seed, i)
+                v0[lv.sys.u_constrained] = 0.0
+                lv.lam_hi = 1.2 * lanczos_max(((lv.A + lv.A.T) * 0.5).tocsr(), lv.D, v0, 12)
         for i in range(1, len(self.levels)):
             lo, hi = self.levels[i - 1], self.levels[i]
             hi.Pu = self.vel.levels[i].P
@@ -149,7 +215,7 @@ class MonolithicHierarchy:
     # ---- pieces ----------------------------------------------------------------------------------
     def ahat_inv(self, level, r):
         """Ahat^{-1} r = Cheb(A, diag A, k_A) from zero."""
-        lv = self.vel.levels[level]
+        lv = self.levels[level]
         return chebyshev(lv.A, 1.0 / lv.D, r, None, self.degree, lv.lam_hi / self.vel.ratio, lv.lam_hi)
 
     def schur_inv(self, level, v):
@@ -157,7 +223,8 @@ class MonolithicHierarchy:
         one Chebyshev step with diag(B diag(A)^{-1} B^T)."""
         lv = self.levels[level]
         B = lv.B
-        return minres(lambda z: B @ self.ahat_inv(level, B.T @ z), lambda r: lv.dsinv * r, v, self.schur_steps)
+        krylov = bicgstab if self.corrector else minres   # ChebBiCGStab for a non-symmetric A
+        return krylov(lambda z: B @ self.ahat_inv(level, B.T @ z), lambda r: lv.dsinv * r, v, self.schur_steps)
 
     def smoother(self, level, r, schur=None):
         """w = K_j r (Eq. "smoother") by the block factorisation; `schur` replaces Shat^{-1}."""

@@ -93,3 +93,50 @@ def test_corrector_solve_reaches_the_direct_solution():
     xd = spla.spsolve(K.tocsc(), b)
     assert rel <= 1e-10 and it < 80, (it, rel)
     assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
+
+
+def test_bicgstab_facts():
+    """S = c I is solved in one step; n_S steps converge on a non-symmetric, diagonally dominant
+    system; a positive scaling of the preconditioner leaves every iterate unchanged."""
+    from oracle.monolithic import bicgstab
+    rng = np.random.default_rng(8)
+    n = 10
+    b = rng.standard_normal(n)
+    np.testing.assert_allclose(bicgstab(lambda z: 3.5 * z, lambda r: r, b, 1), b / 3.5, rtol=1e-14)
+    S = rng.standard_normal((n, n)) + 6.0 * np.eye(n)
+    d = rng.uniform(0.5, 2.0, n)
+    x = bicgstab(lambda z: S @ z, lambda r: d * r, b, 3 * n)
+    np.testing.assert_allclose(S @ x, b, rtol=0, atol=1e-10 * np.abs(b).max())
+    for k in (1, 2, 4):
+        np.testing.assert_allclose(bicgstab(lambda z: S @ z, lambda r: 9.0 * d * r, b, k),
+                                   bicgstab(lambda z: S @ z, lambda r: d * r, b, k), rtol=1e-12, atol=1e-14)
+
+
+def test_corrector_with_the_monolithic_preconditioner():
+    """Sec. 4's saddle-point multigrid on the corrector block (ChebBiCGStab Schur solves): FGMRES
+    reaches the sparse direct solution of the non-symmetric system."""
+    from oracle.krylov import StokesOracle, fgmres
+    from oracle.monolithic import MonolithicHierarchy
+    p = inputs.config_box_inclusion(2, (32, 16), 3, 1e4, 30.0, seed=7,
+                                    faces=inputs.FACE_XM | inputs.FACE_YM | inputs.FACE_YP, align_coarse=True)
+    m = mesh_from_problem(p)
+    pred = StokesOracle(m, p.eta, p.alpha, 3)
+    x0, _, _, _ = pred.solve(pred.sys.lift_rhs(p.f, p.g), tol=1e-8)
+    vcirc = 5.0 * x0[:m.n_u] / np.abs(x0[:m.n_u]).max()       # a field of size 5
+    rho = 40.0                                                 # Pe_K up to ~4: streamline term on ~120 cells
+    _, pe, _ = cell_parameters(m, vcirc, p.eta, rho)
+    assert (pe >= 1.0).any()                                   # the streamline term is active somewhere
+    cs = CorrectorSystem(m, p.eta, p.alpha, vcirc, rho)
+    mono = MonolithicHierarchy(m, p.eta, p.alpha, 3, corrector=(vcirc, rho))
+
+    def precond(r):
+        z = mono.apply(r)
+        z[cs.constrained] = r[cs.constrained]
+        return z
+
+    b = cs.lift_rhs(p.f, p.g)
+    x, it, rel, _ = fgmres(lambda v: cs.K @ v, precond, b, tol=1e-10, max_iter=300)
+    xd = spla.spsolve(cs.K.tocsc(), b)
+    assert rel <= 1e-10 and it < 40, (it, rel)
+    n_u = m.n_u
+    assert np.linalg.norm(x[:n_u] - xd[:n_u]) <= 1e-6 * np.linalg.norm(xd[:n_u])
