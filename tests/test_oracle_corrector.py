@@ -140,3 +140,18 @@ def test_corrector_with_the_monolithic_preconditioner():
     assert rel <= 1e-10 and it < 40, (it, rel)
     n_u = m.n_u
     assert np.linalg.norm(x[:n_u] - xd[:n_u]) <= 1e-6 * np.linalg.norm(xd[:n_u])
+
+
+def test_constant_field_cell_matrix_3d():
+    """3D: int_K phi_i (v° . grad) phi_j = sum_a v°_a (Ei^T/6 in direction a, h Mi/30 elsewhere),
+    Kronecker factors ordered z (outer), y, x (inner)."""
+    m = Mesh(3, (1, 1, 1), (0.7, 0.3, 0.5), dirichlet_faces=0)
+    vv = (0.8, -1.3, 0.4)
+    v = np.concatenate([np.full(m.Nv, c) for c in vv])
+    C, _ = convection_matrices(m, v, np.ones(1), 1.0)
+    h = m.h
+    fac = lambda a, ax: EI.T if a == ax else h[ax] * MI
+    ref = sum(vv[a] * np.kron(fac(a, 2), np.kron(fac(a, 1), fac(a, 0))) for a in range(3))
+    for comp in range(3):
+        blk = C.toarray()[27 * comp:27 * (comp + 1), 27 * comp:27 * (comp + 1)]
+        np.testing.assert_allclose(blk, ref, rtol=1e-13, atol=1e-15)
