@@ -100,18 +100,20 @@ class Clocks:
 # --------------------------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle on a bounded sample
 # --------------------------------------------------------------------------------------------
-ORACLE_SAMPLE = dict(nx=320, ny=56, levels=4)  # ~5 s of host work per solve
+ORACLE_SAMPLE = dict(nx=320, ny=56, levels=4)  # ~5 s of host work per solve and core
 
 
 def oracle_sample_run(steps: int, warmup: int):
-    """Time the oracle solve of the channel workload at a reduced mesh (same geometry and
-    coefficients); returns (seconds per solve list, unknowns, iterations)."""
+    """Time the oracle on the channel workload at a reduced mesh (same geometry and coefficients):
+    full setup + FGMRES solve to rel-res 1e-8, and one CSR SpMV of the assembled velocity block A
+    (median of 20).  Returns a dict of per-solve seconds, unknowns, iterations and SpMV seconds."""
+    import numpy as np
     from oracle.krylov import StokesOracle
     from oracle.mesh import mesh_from_problem
     from paper_2305_08986_gb300 import inputs
     p = inputs.config_channel(**ORACLE_SAMPLE)
     m = mesh_from_problem(p)
-    times, its = [], []
+    times, its, spmv = [], [], []
     for i in range(warmup + steps):
         t0 = time.perf_counter()
         o = StokesOracle(m, p.eta, p.alpha, p.levels)
@@ -121,26 +123,65 @@ def oracle_sample_run(steps: int, warmup: int):
         if i >= warmup:
             times.append(dt)
             its.append(it)
-    return times, m.N, its
+    A = o.sys.A
+    xv = np.random.default_rng(0).standard_normal(A.shape[0])
+    for _ in range(22):
+        t0 = time.perf_counter()
+        A @ xv
+        spmv.append(time.perf_counter() - t0)
+    return {"t": times, "n": m.N, "n_u": m.n_u, "it": its, "spmv_s": statistics.median(spmv[2:]),
+            "csr_nnz": int(A.nnz)}
 
 
-def oracle_subprocess(steps: int, warmup: int):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "t,n,it=bench.oracle_sample_run(%d,%d); print(json.dumps({'t':t,'n':n,'it':it}))"
-            % (ROOT, steps, warmup))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def _oracle_worker(args):
+    steps, warmup = args
+    return oracle_sample_run(steps, warmup)
 
 
-def cpu_baseline_entry(res):
-    t = statistics.median(res["t"])
-    return {"value": res["n"] / t / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+def host_cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_all_cores(steps: int, warmup: int, cores: int = 0):
+    """The oracle as it stands (single-threaded NumPy / SciPy code) on every host core at once: one
+    independent solve per core in spawned worker processes (BLAS pinned to one thread each), so
+    the throughput is whole-machine.  Returns the per-worker results and the wall time."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(steps, warmup)] * cores)
+    return res, time.perf_counter() - t0, cores
+
+
+def cpu_baseline_entry(res, cores):
+    """GDoF/s of the whole host: unknowns solved by all workers / the slowest worker's time."""
+    t = max(sum(r["t"]) for r in res)
+    n = res[0]["n"]
+    solves = sum(len(r["t"]) for r in res)
+    spmv = statistics.median(r["spmv_s"] for r in res)
+    return {"value": n * solves / t / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "cpu_model": host_cpu_model(),
+            "csr_spmv_gdofs": res[0]["n_u"] * cores / spmv / 1e9,
+            "csr_spmv_gdofs_per_core": res[0]["n_u"] / spmv / 1e9,
+            "csr_bytes_per_dof": (res[0]["csr_nnz"] * 12 + 8 * res[0]["n_u"]) / res[0]["n_u"],
             "sample": (f"channel geometry at {ORACLE_SAMPLE['nx']}x{ORACLE_SAMPLE['ny']} cells, "
-                       f"{ORACLE_SAMPLE['levels']} levels ({res['n']} unknowns), full setup + FGMRES solve "
-                       f"to rel-res 1e-8 ({statistics.median(res['it'])} iterations), median of {len(res['t'])}")}
+                       f"{ORACLE_SAMPLE['levels']} levels ({n} unknowns): full setup + FGMRES solve to rel-res "
+                       f"1e-8 ({statistics.median(res[0]['it'])} iterations), {len(res[0]['t'])} per core on "
+                       f"{cores} cores at once (one process per core); CSR SpMV of the assembled A "
+                       f"({res[0]['n_u']} rows, {res[0]['csr_nnz']} nonzeros), median of 20 per core")}
 
 
 def krylov_bytes(n: int, iterations: int, restart: int):
@@ -187,15 +228,15 @@ def whole_job_value(unknowns_per_rank: int, steps: int, world: int, max_total_ms
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    steps = max(1, min(args.steps, 3))
-    res = oracle_subprocess(steps, 0)
-    cb = cpu_baseline_entry(res)
-    t = statistics.median(res["t"])
+    steps = max(1, min(args.steps, 2))
+    res, wall, cores = oracle_all_cores(steps, 0)
+    cb = cpu_baseline_entry(res, cores)
+    t = max(sum(r["t"]) for r in res) / steps
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GDoF/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"channel {WORKLOAD['nx']}x{WORKLOAD['ny']} (sampled at "
-                                   f"{ORACLE_SAMPLE['nx']}x{ORACLE_SAMPLE['ny']})", "tol": TOL},
+                                   f"{ORACLE_SAMPLE['nx']}x{ORACLE_SAMPLE['ny']}, one solve per host core)", "tol": TOL},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -204,26 +245,55 @@ def run_reference(args, rank, world):
 # --------------------------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------------------------
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the dominant kernels
-# at the 1280 x 224 workload, from one ncu --set full capture of the kernel as built now (cold,
-# standalone launch, 32 x 8 tiles: the height the autotuner picks on this workload): the fused
-# FP32 Chebyshev step and the FP64 saddle operator.
-NCU_TRAFFIC_BYTES = {"cheb_step": 39.409664e6 + 6.144e3, "saddle_fp64": 24.769024e6 + 4.096e3}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the finest-level
+# fused Chebyshev step at the 1280 x 224 workload, from one ncu capture of the kernel as built now
+# (profiles/); None until the current kernel has been captured.
+NCU_TRAFFIC_BYTES = {"cheb_step": None, "saddle_fp64": None}
 
 
-def algorithmic_cost(kind, dim, n_cells, n_u, n_p, elem_bytes):
-    """Algorithmic bytes / flops per launch of the dominant kernel classes.  Chebyshev step: x, b, d,
-    D^-1 read and d, x' written (6 vectors of d N_v entries) plus eta per cell; residual: x, b read
-    and r written; FP64 saddle: x and y of the full vector plus eta, 534 flops per cell for A and
-    75 each for B and B^T (2D sum-factorised sweeps)."""
-    if kind == "saddle_fp64":
-        # flops of the sum-factorised cell operator (A, B^T, B) per cell, 2D
-        return {"flops": n_cells * (534 + 2 * 75), "bytes": 8 * (2 * (n_u + n_p)) + 8 * n_cells}
-    if kind in ("cheb_step", "residual_A"):
-        vec = n_u * elem_bytes
-        nvec = 6 if kind == "cheb_step" else 3
-        return {"bytes": nvec * vec + n_cells * elem_bytes, "flops": n_cells * 534}
-    return None
+def tile_step_bytes(n_u: int, n_cells: int, elem: int, kind: str) -> int:
+    """Algorithmic HBM bytes of one launch of a velocity tile kernel on one level.
+    cheb_step: x, b, d, D^-1 read, d and x' written (6 vectors of d N_v entries) plus eta per cell;
+    residual_A: x, b read, r written (3 vectors) plus eta; apply: x read, y written plus eta."""
+    nvec = {"cheb_step": 6, "residual_A": 3, "apply": 2}[kind]
+    return nvec * n_u * elem + n_cells * elem
+
+
+def level_sizes(dim: int, n_fine, levels: int):
+    """(n_u, n_cells) per level, coarsest first (n_l = n_fine / 2^(L-1-l) per axis)."""
+    out = []
+    for l in range(levels):
+        n = [k >> (levels - 1 - l) for k in n_fine]
+        nv = 1
+        nc = 1
+        for k in n:
+            nv *= 2 * k + 1
+            nc *= k
+        out.append((dim * nv, nc))
+    return out
+
+
+def level_weighted_roofline(per_level: dict, sizes, cls: str, elem: int, peak_gbs: float):
+    """Roofline of a tile-kernel class over all levels from the live per-level profile:
+    achieved = sum_l bytes_l x launches_l / sum_l device time_l."""
+    tot_b = tot_ms = 0.0
+    n = 0
+    rows = []
+    for l, st in per_level.items():
+        if l < 0 or cls not in st or st[cls][0] == 0:
+            continue
+        nl, ms = st[cls]
+        bl = tile_step_bytes(sizes[l][0], sizes[l][1], elem, cls)
+        tot_b += bl * nl
+        tot_ms += ms
+        n += nl
+        rows.append({"level": l, "launches": nl, "bytes_per_launch": bl, "us_per_launch": 1e3 * ms / nl,
+                     "frac": bl / (ms / nl * 1e-3) / 1e9 / peak_gbs})
+    if n == 0:
+        return None
+    ach = tot_b / (tot_ms * 1e-3) / 1e9
+    return {"achieved": ach, "frac": ach / peak_gbs, "launches": n, "ms": tot_ms,
+            "bytes_per_launch": tot_b / n, "per_level": rows}
 
 
 def run_gpu(args, rank, world):
@@ -286,37 +356,89 @@ def run_gpu(args, rank, world):
     ms_per_step = total_ms / args.steps
     value = whole_job_value(N, args.steps, world, total_ms)
 
-    # ---- per-kernel profile of one solve (dominant kernel, roofline) ----
+    # ---- per-kernel profile of one solve: per class and per multigrid level ----
     solver.profile(True)
     x.zero_()
     solver.solve(rhs, x, tol=TOL, allow_noconv=True)
     solver.profile(False)
     prof = solver.profile_read()
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    per_level = {l: solver.profile_read(level=l) for l in range(-1, p.levels)}
     peaks = _peaks()
+    peak_gbs = peaks.get("hbm_gbs", 6800.0)
     n_cells = p.n_cells
     n_u, n_p = solver.n_u, solver.n_p
-    cost = algorithmic_cost(dom[0], 2, n_cells, n_u, n_p, 4)
+    sizes = level_sizes(2, (WORKLOAD["nx"], WORKLOAD["ny"]), p.levels)
+
+    # the finest-level fused Chebyshev step alone: 60 back-to-back launches (one event pair around
+    # all of them) cycling through enough copies of its vectors that no launch finds its inputs in L2
+    finest = None
+    try:
+        set_bytes = 5 * n_u * 4
+        nsets = max(2, int(math.ceil(3 * 129e6 / set_bytes)) + 1)
+        sets = []
+        for k in range(nsets):
+            xs_ = torch.randn(n_u, dtype=torch.float32, device=dev)
+            aux = torch.randn(3 * n_u, dtype=torch.float32, device=dev)
+            aux[2 * n_u:].abs_().mul_(1e-3)
+            sets.append((xs_, aux, torch.empty_like(xs_)))
+        L = p.levels - 1
+        for xs_, aux, ys_ in sets:
+            solver.apply_level(L, gs.OP_CHEB_STEP, xs_, ys_, aux=aux)
+        reps = 60
+        ts = []
+        for _ in range(3):
+            flush.fill_(3.0)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            for r_ in range(reps):
+                xs_, aux, ys_ = sets[r_ % nsets]
+                solver.apply_level(L, gs.OP_CHEB_STEP, xs_, ys_, aux=aux)
+            b_.record(stream)
+            b_.synchronize()
+            ts.append(a_.elapsed_time(b_) / reps)
+        us = 1e3 * min(ts)
+        fb = tile_step_bytes(n_u, n_cells, 4, "cheb_step")
+        finest = {"bytes": fb, "us": us, "achieved_gbs": fb / (us * 1e-6) / 1e9,
+                  "frac": fb / (us * 1e-6) / 1e9 / peak_gbs, "launches": reps, "buffer_sets": nsets,
+                  "how": f"{reps} back-to-back launches of gs_apply_level(GS_OP_CHEB_STEP) on level {L}, one event "
+                         f"pair around them, cycling {nsets} vector sets of {set_bytes / 1e6:.0f} MB (> L2)"}
+        del sets
+    except Exception as ex:  # secondary figure: never break the bench line
+        finest = {"error": str(ex)}
+
+    cheb_roof = level_weighted_roofline(per_level, sizes, "cheb_step", 4, peak_gbs)
     roof = None
-    if dom[1][0] > 0:
-        avg_s = dom[1][1] / dom[1][0] * 1e-3
-        if dom[0] == "saddle_fp64":
-            peak = args.fp64_peak_tflops
-            ach = cost["flops"] / avg_s / 1e12
-            roof = {"bound": "alu", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": NCU_TRAFFIC_BYTES.get(dom[0]), "avg_launch_us": avg_s * 1e6,
-                    "launches": dom[1][0],
-                    "peak_source": "FP64 FMA microbenchmark on this GB300 (profiles/alu_peaks_gb300.md)"}
-        elif cost is not None:
-            ach = cost["bytes"] / avg_s / 1e9
-            peak = peaks.get("hbm_gbs", 6800.0)
-            roof = {"bound": "hbm", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": NCU_TRAFFIC_BYTES.get(dom[0]), "avg_launch_us": avg_s * 1e6,
-                    "launches": dom[1][0], "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    if cheb_roof is not None:
+        tr = NCU_TRAFFIC_BYTES.get("cheb_step")
+        roof = {"bound": "hbm", "kernel": "cheb_step (fused Chebyshev step, FP32 tile kernel, all MG levels)",
+                "achieved": cheb_roof["achieved"], "peak": peak_gbs, "unit": "GB/s", "frac": cheb_roof["frac"],
+                "traffic": tr, "traffic_over_algorithmic": (tr / tile_step_bytes(n_u, n_cells, 4, "cheb_step")
+                                                            if tr else None),
+                "launches": cheb_roof["launches"], "avg_launch_us": 1e3 * cheb_roof["ms"] / cheb_roof["launches"],
+                "bytes_per_launch": cheb_roof["bytes_per_launch"], "per_level": cheb_roof["per_level"],
+                "finest": finest,
+                "how": "sum over levels of algorithmic bytes x launches / summed device time of the class in one "
+                       "solve (CUDA event pair per launch, which lengthens short launches: a lower bound); "
+                       "finest: the finest-level step alone, back to back, inputs beyond L2",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
+    saddle = None
+    if "saddle_fp64" in prof and prof["saddle_fp64"][0] > 0:
+        nl, ms = prof["saddle_fp64"]
+        fl = n_cells * (534 + 2 * 75)
+        ach = fl / (ms / nl * 1e-3) / 1e12
+        saddle = {"bound": "alu", "achieved": ach, "peak": args.fp64_peak_tflops, "unit": "TFLOP/s",
+                  "frac": ach / args.fp64_peak_tflops, "launches": nl, "avg_launch_us": 1e3 * ms / nl,
+                  "peak_source": "FP64 FMA microbenchmark on a GB300 of this pool (profiles/alu_peaks_gb300.md)"}
+
+    # the line's roofline is the class with the most device time in the profiled solve
+    dominant = roof
+    if saddle is not None and (roof is None or prof["saddle_fp64"][1] > cheb_roof["ms"]):
+        dominant = dict(saddle, kernel="saddle_fp64 (FP64 saddle operator of the FGMRES matvec)",
+                        traffic=NCU_TRAFFIC_BYTES.get("saddle_fp64"))
 
     krylov_table = None
     try:  # secondary figures: never let them break the bench line
-        krylov_table = krylov_rooflines(prof, N, int(statistics.median(its)), args.restart, peaks.get("hbm_gbs", 6800.0))
+        krylov_table = krylov_rooflines(prof, N, int(statistics.median(its)), args.restart, peak_gbs)
     except Exception as ex:
         krylov_table = {"error": str(ex)}
 
@@ -362,6 +484,31 @@ def run_gpu(args, rank, world):
         fp64 = {"time_to_solve_ms": statistics.median(t64), "iterations": it64, "rel_residual": rel64,
                 "solution_rel_diff_vs_fp32mg": diff}
         s64.close()
+
+    # ---- the same solve with the IEEE FP64 Krylov basis (krylov_fp64 = 1) ----
+    kfp64 = None
+    if rank == 0:
+        try:
+            sk = gs.Solver.from_problem(p, device=dev, krylov_fp64=1, restart=args.restart, max_iter=4000,
+                                        tile_autotune=args.tile_autotune)
+            xk = torch.zeros_like(f)
+            sk.solve(rhs, xk, tol=TOL, allow_noconv=True)
+            tk = []
+            for _ in range(max(1, min(3, args.steps))):
+                xk.zero_()
+                flush.fill_(1.0)
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                itk, relk, _ = sk.solve(rhs, xk, tol=TOL, allow_noconv=True)
+                b_.record(stream)
+                b_.synchronize()
+                tk.append(a_.elapsed_time(b_))
+            kfp64 = {"time_to_solve_ms": statistics.median(tk), "iterations": itk, "rel_residual": relk,
+                     "solution_rel_diff_vs_default": float(torch.linalg.vector_norm(xk - x) /
+                                                           torch.linalg.vector_norm(x))}
+            sk.close()
+        except Exception as ex:
+            kfp64 = {"error": str(ex)}
 
     # ---- the preconditioner of Sec. 4 itself: saddle-point multigrid with the block smoother, with
     # the paper's m = 2 smoothing steps and with m = 6 ----
@@ -416,9 +563,11 @@ def run_gpu(args, rank, world):
         cb = None
         if not args.skip_cpu_baseline and world == 1:
             try:
-                cb = cpu_baseline_entry(oracle_subprocess(3, 0))
+                res, _, cores = oracle_all_cores(1, 0)
+                cb = cpu_baseline_entry(res, cores)
             except Exception as ex:  # the baseline must not break the GPU line
-                cb = {"value": None, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+                cb = {"value": None, "unit": "GDoF/s", "cores": os.cpu_count(), "kind": "oracle",
+                      "sample": f"failed: {ex}"}
         ts = sorted(times)
         line = {
             "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -435,9 +584,12 @@ def run_gpu(args, rank, world):
             "ax_gdofs": {"fp64": ax64, "fp32": ax32},
             "fp64_multigrid": fp64,
             "monolithic_precond": mono,
-            "roofline": roof,
+            "roofline": dominant,
+            "rooflines": {"cheb_step": roof, "saddle_fp64": saddle},
             "krylov_rooflines": krylov_table,
+            "krylov_fp64_basis": kfp64,
             "kernel_profile_ms": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+            "kernel_profile_note": "one CUDA event pair per launch (lengthens short launches); sums exceed the solve time",
             "cpu_baseline": cb,
             "e2e": {"value": N / (e2e_t * 1e-3) / 1e9, "unit": "GDoF/s", "ms": e2e_t,
                     "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},
@@ -704,6 +856,63 @@ def run_spheres(args):
     print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------------------------------------------------
+# one operator, repeated (the command the committed ncu summaries were taken with)
+# --------------------------------------------------------------------------------------------
+def run_op(args):
+    """Repeat one operator on a one-level context (L2 flushed before each launch) and print its median
+    device time: a32 / a64 (gs_vmult_A), saddle64 (gs_vmult), chebstep (GS_OP_CHEB_STEP, FP32) on the
+    channel geometry at --mesh, or on the 3D sphere workload with --dim3 n."""
+    import torch
+    from paper_2305_08986_gb300 import build as gsbuild
+    gsbuild.build(verbose=False)
+    from paper_2305_08986_gb300 import gs, inputs
+    dev = torch.device("cuda", 0)
+    if args.dim3:
+        p = inputs.config_spheres(n=args.dim3, levels=1)
+    else:
+        nx, ny = (int(v) for v in args.mesh.split("x"))
+        p = inputs.config_channel(nx=nx, ny=ny, levels=1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    for op in args.op.split(","):
+        prec = 64 if op.endswith("64") else 32
+        s = gs.Solver.from_problem(p, levels=1, coarse_mode=1, mg_precision=prec, restart=2,
+                                   tile_autotune=args.tile_autotune)
+        dt = torch.float64 if prec == 64 else torch.float32
+        nu = s.n_u
+        if op == "saddle64":
+            xx = torch.randn(s.n_total, dtype=dt, device=dev)
+            yy = torch.empty_like(xx)
+            run = lambda: s.vmult(xx, yy)
+        elif op == "chebstep":
+            xx = torch.randn(nu, dtype=dt, device=dev)
+            aux = torch.randn(3 * nu, dtype=dt, device=dev)
+            aux[2 * nu:].abs_().mul_(1e-3)
+            yy = torch.empty_like(xx)
+            run = lambda: s.apply_level(0, gs.OP_CHEB_STEP, xx, yy, aux=aux)
+        else:
+            xx = torch.randn(nu, dtype=dt, device=dev)
+            yy = torch.empty_like(xx)
+            run = lambda: s.vmult_A(xx, yy)
+        for _ in range(3):
+            run()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(st)
+            run()
+            b_.record(st)
+            b_.synchronize()
+            ts.append(a_.elapsed_time(b_))
+        t = statistics.median(ts)
+        print(json.dumps({"op": op, "mesh": args.mesh if not args.dim3 else f"{args.dim3}^3", "n_u": nu,
+                          "median_us": 1e3 * t, "min_us": 1e3 * min(ts), "gdofs": nu / (t * 1e-3) / 1e9}),
+              flush=True)
+        s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -718,7 +927,11 @@ def main():
     ap.add_argument("--tile-autotune", type=int, default=0, choices=[0, 1, 2, 3],
                     help="2D tile height of the channel solver: 0 autotune (default); 1 / 2 / 3: 32 x 16 / 17 / 8 "
                          "(pins the launch configuration, e.g. for profiler runs whose timings would skew the tuner)")
-    ap.add_argument("--workload", default="channel", choices=["channel", "batched", "serving", "spheres", "extension"],
+    ap.add_argument("--op", default="chebstep,a32,a64", help="--workload op: operators to repeat")
+    ap.add_argument("--mesh", default="1280x224", help="--workload op: channel mesh")
+    ap.add_argument("--dim3", type=int, default=0, help="--workload op: 3D sphere mesh n^3 instead")
+    ap.add_argument("--workload", default="channel",
+                    choices=["channel", "batched", "serving", "spheres", "extension", "op"],
                     help="channel: the contract line; batched / serving: the engine workloads; spheres: the 3D "
                          "64^3 inclusion workload (extra lines)")
     ap.add_argument("--instances", type=int, default=256)
@@ -736,6 +949,8 @@ def main():
         return run_spheres(args)
     if args.workload == "extension" and args.impl == "gs":
         return run_extension(args)
+    if args.workload == "op" and args.impl == "gs":
+        return run_op(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -242,8 +242,17 @@ typedef enum {
   GS_OP_SADDLE_SMOOTH = 18, /* y = K_j x: one block-smoother application (Eq. "smoother") to
                             the level vector x; level >= 1 (or level 0 with coarse_mode 1) */
   GS_OP_SADDLE_VCYCLE = 19, /* y = V_l(x): one saddle-point V-cycle on level l, level vectors */
-  GS_OP_SADDLE_COARSE = 20  /* y = M_0^{-1} x: dense saddle solve of level 0 (FP64 level
+  GS_OP_SADDLE_COARSE = 20, /* y = M_0^{-1} x: dense saddle solve of level 0 (FP64 level
                             vectors, free unknowns; constrained entries of y are 0) */
+  GS_OP_CHEB_STEP = 21   /* one fused Chebyshev-Jacobi step on the caller's vectors (the kernel
+                            the smoother of Sec. 4 launches k_A - 1 times per call): with
+                            aux = [b | d | D^-1] (3 x d N_v,l contiguous entries), r = b - A_l x,
+                            d <- c1 d + c2 D^-1 r (in place in aux), y = x + d, where c1, c2 are
+                            the coefficients of the level's second Chebyshev step (Saad's
+                            recurrence on [lambda_hi / 15, lambda_hi]); x and y must not alias;
+                            levels with Chebyshev bounds only (not level 0 with the dense
+                            coarse solve).  Lets a caller time the step on vectors of its own,
+                            e.g. several copies that together exceed L2. */
 } gs_op;
 
 /* Apply one operator of level `level` (0 = coarsest).  prec = 64: x, y, aux are double*;
@@ -291,6 +300,11 @@ typedef struct {
 } gs_kernel_stat;
 gs_status gs_profile(gs_ctx* ctx, int enable);
 int gs_profile_read(gs_ctx* ctx, gs_kernel_stat* out, int max);
+/* The same, restricted to the launches recorded on multigrid level `level` (0 = coarsest; the
+ * velocity and pressure-Laplacian cycles and the saddle-point cycle tag their launches with
+ * the level they run on; -1 selects the launches tied to no level: FGMRES kernels, the FP64
+ * saddle operator).  Lets a caller weight a class's algorithmic bytes by level. */
+int gs_profile_read_level(gs_ctx* ctx, int level, gs_kernel_stat* out, int max);
 
 /* Coarse-level solve y = A_0^{-1} b that allocates nothing and uses no workspace scratch.
  * The paper has no counterpart: this is a service entry point for callers that cannot

@@ -184,7 +184,13 @@ struct gs_ctx {
   bool prof = false;
   std::vector<cudaEvent_t> evs;
   size_t ev_used = 0;
-  std::vector<std::pair<int, size_t>> recs;
+  struct ProfRec {
+    int cls;
+    int level;  // multigrid level of the launch (-1: not tied to a level)
+    size_t ev;
+  };
+  std::vector<ProfRec> recs;
+  int prof_lv = -1;  // level tag of the launches being enqueued
   // batching engine state
   KState ks;
 };
@@ -203,12 +209,20 @@ long prof_begin(gs_ctx* c, int cls) {
   const size_t i = c->ev_used;
   c->ev_used += 2;
   cudaEventRecord(c->evs[i], c->st);
-  c->recs.push_back({cls, i});
+  c->recs.push_back({cls, c->prof_lv, i});
   return (long)i;
 }
 void prof_end(gs_ctx* c, long i) {
   if (i >= 0) cudaEventRecord(c->evs[(size_t)i + 1], c->st);
 }
+
+// Tags the launches enqueued while it lives with multigrid level l (profiling only).
+struct LevelTag {
+  gs_ctx* c;
+  int old;
+  LevelTag(gs_ctx* cc, int l) : c(cc), old(cc->prof_lv) { c->prof_lv = l; }
+  ~LevelTag() { c->prof_lv = old; }
+};
 
 #define KL(cls, ...)                      \
   do {                                    \
@@ -1242,6 +1256,7 @@ double cheb_inv_theta(double hi) { return 1.0 / (0.5 * (hi + hi / 15.0)); }
 // that produced b (launch_restrict with a Chebyshev start)
 template <typename T>
 gs_status cheb(gs_ctx* c, int l, const T* b, bool zero_init, bool started = false) {
+  const LevelTag tag__(c, l);
   Level& lv = c->lv[l];
   const double hi = lv.lam_hi, lo = hi / 15.0;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
@@ -1273,6 +1288,7 @@ gs_status cheb(gs_ctx* c, int l, const T* b, bool zero_init, bool started = fals
 // V-cycle on level l: input lv.b, output lv.xA (started: see cheb)
 template <typename T>
 gs_status vcycle(gs_ctx* c, int l, bool started = false) {
+  const LevelTag tag__(c, l);
   Level& lv = c->lv[l];
   if (l == 0) {
     if (c->opt.coarse_mode == 1) return cheb<T>(c, 0, (const T*)lv.b, true, started);
@@ -1330,6 +1346,7 @@ gs_status schur_inv(gs_ctx* c, const T* b) {
 // Chebyshev smoother of the pressure Laplacian on level l (result in lv.pxA)
 template <typename T>
 gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init, bool started = false) {
+  const LevelTag tag__(c, l);
   Level& lv = c->lv[l];
   const double hi = lv.plam_hi, lo = hi / 15.0;
   const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
@@ -1361,6 +1378,7 @@ gs_status pcheb(gs_ctx* c, int l, const T* b, bool zero_init, bool started = fal
 // V-cycle for the pressure Laplacian: input lv.pb, output lv.pxA
 template <typename T>
 gs_status pvcycle(gs_ctx* c, int l, bool started = false) {
+  const LevelTag tag__(c, l);
   Level& lv = c->lv[l];
   if (l == 0) {
     if (c->opt.coarse_mode == 1) return pcheb<T>(c, 0, (const T*)lv.pb, true, started);
@@ -1407,6 +1425,7 @@ gs_status plap_inverse(gs_ctx* c, const T* r) {
 // kernels run on -z, -y and -S z (from r_p - B w~), which leaves a and the update unchanged.
 template <typename T>
 gs_status mono_smooth_step(gs_ctx* c, int l, bool zero) {
+  const LevelTag tag__(c, l);
   Level& lv = c->lv[l];
   T* x = (T*)lv.ms;
   const T* b = (const T*)lv.mr;
@@ -1452,6 +1471,7 @@ gs_status mono_smooth_step(gs_ctx* c, int l, bool zero) {
 // 0: dense saddle solve (coarse_mode 0) or m smoothing steps from zero.
 template <typename T>
 gs_status mono_vcycle(gs_ctx* c, int l) {
+  const LevelTag tag__(c, l);
   Level& lv = c->lv[l];
   if (l == 0 && c->opt.coarse_mode != 1) {
     KL(K_COARSE, launch_coarse_solve<T>(c->MAinv, c->mcfree, c->nmf, (const T*)lv.mr, (T*)lv.ms, lv.nu + lv.Np,
@@ -1834,6 +1854,21 @@ gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, co
       CK(cudaMemcpyAsync(lv.b, x, sizeof(T) * lv.nu, cudaMemcpyDeviceToDevice, c->st));
       for (int s = 0; s < c->opt.smooth_steps; ++s) CKS(cheb<T>(c, l, (const T*)lv.b, s == 0 && !aux));
       CK(cudaMemcpyAsync(y, lv.xA, sizeof(T) * lv.nu, cudaMemcpyDeviceToDevice, c->st));
+      return GS_OK;
+    }
+    case GS_OP_CHEB_STEP: {
+      // one fused step r = b - A x, d = c1 d + c2 D^-1 r, y = x + d with the coefficients of the
+      // level's second Chebyshev step; aux = [b | d | D^-1] (3 d N_v,l entries, d updated in place)
+      if (!aux) return fail(GS_EINVAL, "Chebyshev step needs aux = [b | d | D^-1]");
+      if (!(lv.lam_hi > 0.0)) return fail(GS_EINVAL, "level has no Chebyshev bounds (level 0 with a dense coarse solve)");
+      if ((const void*)x == (const void*)y) return fail(GS_EINVAL, "x and y must not alias");
+      const double hi = lv.lam_hi, lo = hi / 15.0;
+      const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+      const double rho = 1.0 / sigma, rn = 1.0 / (2.0 * sigma - rho);
+      TileArgs<T> a = tile_args<T>(lv);
+      a.xu = x; a.bu = aux; a.d = const_cast<T*>(aux) + lv.nu; a.dinv = aux + 2 * lv.nu; a.xout = y;
+      a.c1 = (T)(rn * rho); a.c2 = (T)(2.0 * rn / delta); a.use_d = 1;
+      CK(launch_tile<T>(c->dim, TILE_CHEB, OPS_A, a, c->st));
       return GS_OK;
     }
     case GS_OP_RESTRICT:
@@ -2678,6 +2713,29 @@ gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
   return GS_OK;
 }
 
+int gs_profile_read_level(gs_ctx* c, int level, gs_kernel_stat* out, int max) {
+  if (!c || !out || max <= 0) return 0;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return 0;
+  double ms[K_NCLASS] = {0};
+  long long cnt[K_NCLASS] = {0};
+  for (auto& r : c->recs) {
+    if (r.level != level) continue;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->evs[r.ev], c->evs[r.ev + 1]) == cudaSuccess) {
+      ms[r.cls] += t;
+      cnt[r.cls] += 1;
+    }
+  }
+  int n = 0;
+  for (int k = 0; k < K_NCLASS && n < max; ++k) {
+    out[n].name = kclass_name[k];
+    out[n].launches = cnt[k];
+    out[n].total_ms = ms[k];
+    ++n;
+  }
+  return n;
+}
+
 gs_status gs_profile(gs_ctx* c, int enable) {
   if (!c) return fail(GS_EINVAL, "NULL argument");
   if (enable) {
@@ -2696,9 +2754,9 @@ int gs_profile_read(gs_ctx* c, gs_kernel_stat* out, int max) {
   long long cnt[K_NCLASS] = {0};
   for (auto& r : c->recs) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, c->evs[r.second], c->evs[r.second + 1]) == cudaSuccess) {
-      ms[r.first] += t;
-      cnt[r.first] += 1;
+    if (cudaEventElapsedTime(&t, c->evs[r.ev], c->evs[r.ev + 1]) == cudaSuccess) {
+      ms[r.cls] += t;
+      cnt[r.cls] += 1;
     }
   }
   int n = 0;

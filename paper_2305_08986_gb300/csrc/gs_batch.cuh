@@ -20,6 +20,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -63,6 +64,26 @@ struct Recorder {
 // recorder installed on this thread (nullptr: launch immediately)
 Recorder*& current_recorder();
 
+// Raise a kernel's dynamic shared memory limit to at least smem bytes on the current device.  The
+// attribute is per device, so the largest size enabled so far is kept per (kernel, device); the
+// counters are atomics because contexts are built on several host threads at once.
+constexpr int kMaxDevices = 64;
+template <class F>
+cudaError_t ensure_dynamic_smem(F* fn, size_t smem, std::atomic<size_t>* enabled) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (enabled[dev].load(std::memory_order_acquire) >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  size_t cur = enabled[dev].load(std::memory_order_relaxed);
+  while (cur < smem && !enabled[dev].compare_exchange_weak(cur, smem, std::memory_order_acq_rel)) {
+  }
+  return cudaSuccess;
+}
+
 __device__ __forceinline__ void wait_prerequisite_grids() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <class K>
@@ -84,12 +105,9 @@ template <class K>
 cudaError_t batch_launch(const void* tab, const WorkItem* work, int nwork, const int* active, size_t smem,
                          cudaStream_t st) {
   if (nwork <= 0) return cudaSuccess;
-  static size_t configured = 48 * 1024;  // per instantiation: largest dynamic size enabled so far
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_many<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  static std::atomic<size_t> enabled[kMaxDevices];  // zero-initialised (static storage)
+  cudaError_t e = ensure_dynamic_smem(k_many<K>, smem, enabled);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)nwork);
   cfg.blockDim = dim3(K::THREADS);
@@ -110,12 +128,9 @@ cudaError_t submit(const typename K::Args& a, long long nblk, size_t smem, cudaS
     r->add(&batch_launch<K>, &a, (int)sizeof(a), (int)nblk, smem);
     return cudaSuccess;
   }
-  static size_t configured = 48 * 1024;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_one<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  static std::atomic<size_t> enabled[kMaxDevices];
+  cudaError_t e = ensure_dynamic_smem(k_one<K>, smem, enabled);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)nblk);
   cfg.blockDim = dim3(K::THREADS);

@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ENOCONV, GS_EBREAKDOWN, GS_ETIMEOUT, GS_EBUSY = range(8)
 (OP_A, OP_RESIDUAL_A, OP_DIAG_A, OP_SMOOTH, OP_RESTRICT, OP_PROLONGATE, OP_B, OP_BT,
  OP_SCHUR_MASS, OP_SCHUR_INV, OP_COARSE, OP_PRECOND, OP_A_RAW, OP_PLAP, OP_PLAP_INV, OP_PRESTRICT,
- OP_PPROLONGATE, OP_SCHUR_DIAG, OP_SADDLE_SMOOTH, OP_SADDLE_VCYCLE, OP_SADDLE_COARSE) = range(21)
+ OP_PPROLONGATE, OP_SCHUR_DIAG, OP_SADDLE_SMOOTH, OP_SADDLE_VCYCLE, OP_SADDLE_COARSE, OP_CHEB_STEP) = range(22)
 
 
 class GsMesh(ctypes.Structure):
@@ -94,6 +94,8 @@ _lib.gs_profile.restype = ctypes.c_int
 _lib.gs_profile.argtypes = [_vp, ctypes.c_int]
 _lib.gs_profile_read.restype = ctypes.c_int
 _lib.gs_profile_read.argtypes = [_vp, ctypes.POINTER(GsKernelStat), ctypes.c_int]
+_lib.gs_profile_read_level.restype = ctypes.c_int
+_lib.gs_profile_read_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(GsKernelStat), ctypes.c_int]
 _lib.gs_coarse_solve_noalloc.restype = ctypes.c_int
 _lib.gs_coarse_solve_noalloc.argtypes = [_vp, _vp, _vp]
 _lib.gs_set_stream.restype = ctypes.c_int
@@ -135,7 +137,8 @@ _lib.gs_engine_destroy.argtypes = [_vp]
 EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_create_ex", "gs_vmult", "gs_vmult_A", "gs_vcycle", "gs_solve", "gs_solve_A",
             "gs_lift_rhs",
             "gs_batch_solve", "gs_apply_level", "gs_get_info", "gs_set_stream", "gs_destroy", "gs_strerror",
-            "gs_last_error", "gs_profile", "gs_profile_read", "gs_coarse_solve_noalloc", "gs_engine_create",
+            "gs_last_error", "gs_profile", "gs_profile_read", "gs_profile_read_level", "gs_coarse_solve_noalloc",
+            "gs_engine_create",
             "gs_engine_add", "gs_engine_step", "gs_engine_poll", "gs_engine_active", "gs_engine_get_stats",
             "gs_engine_destroy"]
 
@@ -299,9 +302,14 @@ class Solver:
     def profile(self, enable: bool):
         _check(_lib.gs_profile(self.ctx, int(bool(enable))), "gs_profile")
 
-    def profile_read(self):
+    def profile_read(self, level=None):
+        """{class: (launches, device ms)} over all launches, or over those of one multigrid level
+        (level=-1: launches tied to no level)."""
         arr = (GsKernelStat * 32)()
-        n = _lib.gs_profile_read(self.ctx, arr, 32)
+        if level is None:
+            n = _lib.gs_profile_read(self.ctx, arr, 32)
+        else:
+            n = _lib.gs_profile_read_level(self.ctx, int(level), arr, 32)
         return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n)}
 
     def set_stream(self, stream):

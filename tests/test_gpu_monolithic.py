@@ -1,8 +1,8 @@
 """GPU parity of the saddle-point multigrid of Sec. 4 (precond_kind = 1) against the FP64 oracle
 (oracle/monolithic.py), through the C ABI.
 
-Operators (FP64 multigrid): the Schur diagonal diag(B diag(A)^{-1} B^T) per level (1e-12, a sum of
-a few hundred exact products), the block smoother K_j, the dense coarse saddle solve and one
+Operators (FP64 multigrid): the Schur diagonal diag(B diag(A)^{-1} B^T) per level (1e-12 entry by
+entry, a sum of a few hundred non-negative products), the block smoother K_j, the dense coarse saddle solve and one
 V-cycle (1e-9 norm-wise: Chebyshev recurrences and one MINRES step, whose step length a is a
 ratio of two inner products and so carries their rounding).  Solves: FP64-multigrid iteration
 counts within max(2, 5 %) of the oracle's (the same algorithm; counts drift only through
@@ -52,7 +52,9 @@ def test_schur_diagonal_per_level(case):
     for l, lv in enumerate(h.levels):
         y = torch.empty(lv.mesh.Np, dtype=torch.float64, device="cuda")
         s.apply_level(l, 17, torch.zeros(1, dtype=torch.float64, device="cuda"), y)
-        assert rel(y.cpu().numpy(), lv.ds) <= 1e-12
+        # entry by entry (a sum of non-negative products: no cancellation)
+        nz = lv.ds != 0.0
+        assert np.max(np.abs(y.cpu().numpy()[nz] - lv.ds[nz]) / lv.ds[nz]) <= 1e-12
         assert np.all(y.cpu().numpy()[lv.sys.p_constrained] == 0.0)
 
 

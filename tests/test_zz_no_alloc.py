@@ -56,3 +56,21 @@ def test_noalloc_coarse_solve_rejects_bad_contexts():
     assert st == gs.GS_EINVAL
     assert gs._lib.gs_coarse_solve_noalloc(s.ctx, None, ctypes.c_void_p(y.data_ptr())) == gs.GS_EINVAL
     s.close()
+
+
+def test_noalloc_coarse_solve_rejects_a_coarse_level_above_the_limit():
+    """46 x 46 cells, every face Dirichlet, one level: 2 x 91^2 = 16,562 free coarse unknowns, just
+    above the 16,384 entries of the static array; the call must refuse instead of overrunning it."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+
+    p = inputs.config_random_field(2, (46, 46), levels=1, seed=2, contrast=10.0, alpha=1.0)
+    s = gs.Solver.from_problem(p)
+    inf = s.info()
+    assert inf.coarse_free == 2 * 91 * 91 > 16384
+    b = torch.zeros(s.n_u, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(b)
+    st = gs._lib.gs_coarse_solve_noalloc(s.ctx, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(y.data_ptr()))
+    assert st == gs.GS_EINVAL
+    assert b"at most 16384" in gs._lib.gs_last_error()
+    s.close()
