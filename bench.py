@@ -246,9 +246,10 @@ def run_reference(args, rank, world):
 # GPU arm
 # --------------------------------------------------------------------------------------------
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the finest-level
-# fused Chebyshev step at the 1280 x 224 workload, from one ncu capture of the kernel as built now
-# (profiles/); None until the current kernel has been captured.
-NCU_TRAFFIC_BYTES = {"cheb_step": None, "saddle_fp64": None}
+# fused Chebyshev step at the 1280 x 224 workload (the strip kernel the autotuner picks there), from
+# one ncu --set full capture of the kernel as built now (profiles/strip2d_cheb_fp32_channel1280x224.md).
+# The writes (d, x') stay in L2 within the capture, so the figure is the read traffic.
+NCU_TRAFFIC_BYTES = {"cheb_step": 38.566912e6 + 9.728e3, "saddle_fp64": None}
 
 
 def tile_step_bytes(n_u: int, n_cells: int, elem: int, kind: str) -> int:
@@ -860,9 +861,11 @@ def run_spheres(args):
 # one operator, repeated (the command the committed ncu summaries were taken with)
 # --------------------------------------------------------------------------------------------
 def run_op(args):
-    """Repeat one operator on a one-level context (L2 flushed before each launch) and print its median
-    device time: a32 / a64 (gs_vmult_A), saddle64 (gs_vmult), chebstep (GS_OP_CHEB_STEP, FP32) on the
-    channel geometry at --mesh, or on the 3D sphere workload with --dim3 n."""
+    """Repeat one operator on a one-level context and print its device time per launch: a32 / a64
+    (gs_vmult_A), saddle64 (gs_vmult), chebstep (GS_OP_CHEB_STEP, FP32) on the channel geometry at
+    --mesh, or on the 3D sphere workload with --dim3 n.  --steps launches run back to back (one
+    CUDA event pair around them) cycling through copies of the operands that together exceed
+    three times L2, so no launch finds its inputs in L2 and none pays for another's dirty lines."""
     import torch
     from paper_2305_08986_gb300 import build as gsbuild
     gsbuild.build(verbose=False)
@@ -873,43 +876,60 @@ def run_op(args):
     else:
         nx, ny = (int(v) for v in args.mesh.split("x"))
         p = inputs.config_channel(nx=nx, ny=ny, levels=1)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
     for op in args.op.split(","):
         prec = 64 if op.endswith("64") else 32
         s = gs.Solver.from_problem(p, levels=1, coarse_mode=1, mg_precision=prec, restart=2,
                                    tile_autotune=args.tile_autotune)
         dt = torch.float64 if prec == 64 else torch.float32
+        es = 8 if prec == 64 else 4
         nu = s.n_u
         if op == "saddle64":
-            xx = torch.randn(s.n_total, dtype=dt, device=dev)
-            yy = torch.empty_like(xx)
-            run = lambda: s.vmult(xx, yy)
+            per_set = 2 * s.n_total * es
         elif op == "chebstep":
-            xx = torch.randn(nu, dtype=dt, device=dev)
-            aux = torch.randn(3 * nu, dtype=dt, device=dev)
-            aux[2 * nu:].abs_().mul_(1e-3)
-            yy = torch.empty_like(xx)
-            run = lambda: s.apply_level(0, gs.OP_CHEB_STEP, xx, yy, aux=aux)
+            per_set = 5 * nu * es
         else:
-            xx = torch.randn(nu, dtype=dt, device=dev)
-            yy = torch.empty_like(xx)
-            run = lambda: s.vmult_A(xx, yy)
-        for _ in range(3):
-            run()
+            per_set = 2 * nu * es
+        nsets = max(2, int(math.ceil(3 * 129e6 / per_set)) + 1)
+        sets = []
+        for _ in range(nsets):
+            if op == "saddle64":
+                xx = torch.randn(s.n_total, dtype=dt, device=dev)
+                sets.append((xx, torch.empty_like(xx), None))
+            elif op == "chebstep":
+                xx = torch.randn(nu, dtype=dt, device=dev)
+                aux = torch.randn(3 * nu, dtype=dt, device=dev)
+                aux[2 * nu:].abs_().mul_(1e-3)
+                sets.append((xx, torch.empty_like(xx), aux))
+            else:
+                xx = torch.randn(nu, dtype=dt, device=dev)
+                sets.append((xx, torch.empty_like(xx), None))
+
+        def run(i):
+            xx, yy, aux = sets[i % nsets]
+            if op == "saddle64":
+                s.vmult(xx, yy)
+            elif op == "chebstep":
+                s.apply_level(0, gs.OP_CHEB_STEP, xx, yy, aux=aux)
+            else:
+                s.vmult_A(xx, yy)
+        for i in range(nsets):
+            run(i)
+        reps = max(args.steps, nsets)
         ts = []
-        for _ in range(args.steps):
-            flush.fill_(1.0)
+        for _ in range(3):
             a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a_.record(st)
-            run()
+            for i in range(reps):
+                run(i)
             b_.record(st)
             b_.synchronize()
-            ts.append(a_.elapsed_time(b_))
-        t = statistics.median(ts)
+            ts.append(a_.elapsed_time(b_) / reps)
+        t = min(ts)
         print(json.dumps({"op": op, "mesh": args.mesh if not args.dim3 else f"{args.dim3}^3", "n_u": nu,
-                          "median_us": 1e3 * t, "min_us": 1e3 * min(ts), "gdofs": nu / (t * 1e-3) / 1e9}),
-              flush=True)
+                          "us_per_launch": 1e3 * t, "launches": reps, "buffer_sets": nsets,
+                          "tile_rows": s.info().tile_rows[0], "gdofs": nu / (t * 1e-3) / 1e9}), flush=True)
+        del sets
         s.close()
 
 
@@ -924,9 +944,10 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-mono", action="store_true", help="skip the Sec. 4 saddle-point multigrid comparison")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
-    ap.add_argument("--tile-autotune", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="2D tile height of the channel solver: 0 autotune (default); 1 / 2 / 3: 32 x 16 / 17 / 8 "
-                         "(pins the launch configuration, e.g. for profiler runs whose timings would skew the tuner)")
+    ap.add_argument("--tile-autotune", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="2D velocity-block kernel of the channel solver: 0 autotune (default); 1 / 2 / 3: tiles of "
+                         "32 x 16 / 17 / 8; 4: the strip kernel (pins the launch configuration, e.g. for profiler "
+                         "runs whose timings would skew the tuner)")
     ap.add_argument("--op", default="chebstep,a32,a64", help="--workload op: operators to repeat")
     ap.add_argument("--mesh", default="1280x224", help="--workload op: channel mesh")
     ap.add_argument("--dim3", type=int, default=0, help="--workload op: 3D sphere mesh n^3 instead")

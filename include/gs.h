@@ -64,8 +64,11 @@ typedef enum {
   GS_ENOMEM = 2, /* workspace smaller than gs_footprint_bytes() */
   GS_ECUDA = 3,
   GS_ENOCONV = 4,
-  GS_EBREAKDOWN = 5,
-  GS_ETIMEOUT = 6,
+  GS_EBREAKDOWN = 5, /* a non-finite right-hand side, initial guess, residual or Krylov vector */
+  GS_ETIMEOUT = 6,   /* a kernel's bounded wait for its staged data (an mbarrier of the bulk copies
+                        of the 2D strip kernel) gave up after about a second; the launch completed
+                        with unusable results.  Reported by gs_solve / gs_solve_A for any launch of
+                        the context since the previous report. */
   GS_EBUSY = 7 /* batching engine: every slot is occupied */
 } gs_status;
 
@@ -112,11 +115,14 @@ typedef struct {            /* zero-initialised = defaults */
   int krylov_fp64;          /* 0: FGMRES basis V stored as double-float pairs (hi + lo, 48-bit),
                                   Gram-Schmidt products on the FP32 pipes (default);
                                1: basis and Gram-Schmidt in IEEE FP64 */
-  int tile_autotune;        /* 2D meshes: 0 -> at gs_create, time each compiled tile height of the
-                                  cell kernel (32 x 16, 32 x 17, 32 x 8 evaluated cells) on every
-                                  level and keep the fastest (default); 1 / 2 / 3 -> always
-                                  32 x 16 / 32 x 17 / 32 x 8.  The results do not depend on the
-                                  choice. */
+  int tile_autotune;        /* 2D meshes: 0 -> at gs_create, time each compiled variant of the
+                                  velocity-block kernel on every level (cell tiles of 32 x 16,
+                                  32 x 17, 32 x 8 evaluated cells; the strip kernel, 31-cell column
+                                  strips marching up row segments) and keep the fastest (default);
+                                  1 / 2 / 3 -> always the 32 x 16 / 32 x 17 / 32 x 8 tile; 4 -> always
+                                  the strip kernel (the FP64 saddle operator then uses 32 x 8 tiles).
+                                  Every variant sums a node's cell contributions in the same order,
+                                  so the results do not depend on the choice. */
   int deflate;              /* 1: rigid-body deflation of stiff inclusions in the V-cycle's finest
                                   level (not part of the paper's method; for stiff inclusions
                                   smaller than a coarse cell, whose near-rigid motions no coarse
@@ -279,7 +285,8 @@ typedef struct {
   int schur_cc;            /* 1 if the Cahouet-Chabard term is active */
   int pressure_coarse_free;/* unknowns of the dense coarse pressure-Laplacian solve */
   double plambda_max[16];  /* Chebyshev upper bound of the pressure Laplacian per level */
-  int tile_rows[16];       /* 2D: evaluated cell rows per tile chosen for each level's multigrid kernels */
+  int tile_rows[16];       /* 2D: evaluated cell rows per tile chosen for each level's multigrid kernels
+                              (0: the strip kernel) */
   int saddle_tile_rows;    /* 2D: the same for the FP64 saddle operator (0 in 3D) */
   int deflation_inclusions;/* stiff inclusions in the deflation space (option deflate) */
   int deflation_modes;     /* rigid modes kept (modes vanishing on unconstrained nodes dropped) */

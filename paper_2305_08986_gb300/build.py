@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgs.so")
-SOURCES = ["gs_tile.cu", "gs_tile2d_e16.cu", "gs_tile2d_e17.cu", "gs_tile2d_e8.cu", "gs_q1tile.cu", "gs_node.cu", "gs_blas.cu", "gs_api.cu", "gs_engine.cu", "gs_defl.cu", "gs_mono.cu"]
+SOURCES = ["gs_tile.cu", "gs_tile2d_e16.cu", "gs_tile2d_e17.cu", "gs_tile2d_e8.cu", "gs_strip2d.cu", "gs_q1tile.cu", "gs_node.cu", "gs_blas.cu", "gs_api.cu", "gs_engine.cu", "gs_defl.cu", "gs_mono.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

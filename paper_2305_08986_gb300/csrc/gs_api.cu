@@ -76,8 +76,11 @@ struct Level {
   float* alpha32 = nullptr;
   void* pw = nullptr;         // weights abar / alpha_K of the pressure Laplacian (MG precision), or NULL
   uint8_t *vmask = nullptr, *pmask = nullptr, *cvoid = nullptr;
+  std::vector<uint16_t> hccmask;  // 2D with obstacles: per cell, constrained local nodes + obstacle bit
+  uint16_t* ccmask = nullptr;
   void *xA = nullptr, *xB = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
   double lam_hi = 0.0;
+  int* errw = nullptr;  // the context's device error word (bounded waits that gave up)
   // pressure Laplacian level (Cahouet-Chabard term): constraint mask, MG vectors, bound
   std::vector<uint8_t> hpc;
   uint8_t* pcmask = nullptr;
@@ -142,6 +145,7 @@ struct gs_ctx {
   double* Ainv = nullptr;
   int* cfree = nullptr;
   double *ctmp = nullptr, *gjrow = nullptr, *gjcol = nullptr;
+  int* errw = nullptr;  // device word: nonzero after a kernel's bounded wait gave up
   // saddle-point multigrid (precond_kind 1): dense coarse saddle inverse on its free unknowns
   // (velocity free entries, then free pressure entries offset by d N_v of level 0), MINRES sums,
   // finest-level right-hand side and cycle sum (mono_cycles > 1)
@@ -251,7 +255,7 @@ gs_options normalize_opts(const gs_options* o) {
   r.graphs = r.graphs == 1 ? 1 : 0;
   r.plap_degree = opt_or(r.plap_degree, 2);
   r.krylov_fp64 = r.krylov_fp64 == 1 ? 1 : 0;
-  r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 3) ? r.tile_autotune : 0;
+  r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 4) ? r.tile_autotune : 0;
   r.deflate = r.deflate == 1 ? 1 : 0;
   r.precond_kind = r.precond_kind == 1 ? 1 : 0;
   r.mono_smooth = opt_or(r.mono_smooth, 2);
@@ -620,6 +624,7 @@ void layout(gs_ctx* c, Arena& ar) {
       lv.cvoid = ar.take<uint8_t>(lv.Nc);
       lv.vmask = ar.take<uint8_t>(lv.Nv);
       lv.pmask = ar.take<uint8_t>(lv.Np);
+      if (c->dim == 2) lv.ccmask = ar.take<uint16_t>(lv.Nc);
     }
     lv.xA = takeT(lv.nu);
     lv.xB = takeT(lv.nu);
@@ -636,6 +641,8 @@ void layout(gs_ctx* c, Arena& ar) {
   c->Ainv = ar.take<double>((long long)c->nf * c->nf);
   c->cfree = ar.take<int>(c->nf);
   c->ctmp = ar.take<double>(c->nf);
+  c->errw = ar.take<int>(4);
+  for (int l = 0; l < c->L; ++l) c->lv[l].errw = c->errw;
   const int gjn = std::max(c->nf, std::max(c->nfp, c->nmf));
   c->gjrow = ar.take<double>(gjn);
   c->gjcol = ar.take<double>(gjn);
@@ -729,6 +736,7 @@ void set_geom(gs_ctx* c, const gs_mesh* m) {
     g.vmask = lv.vmask;
     g.pmask = lv.pmask;
     g.cvoid = lv.cvoid;
+    g.ccmask = lv.ccmask;
     // alpha per cell: the coefficients carry alpha = 1 and the kernels multiply by alpha_K
     lv.c64 = make_coef<double>(c->dim, lv.h, c->alpha_cells ? 1.0 : c->alpha);
     lv.c32 = make_coef<float>(c->dim, lv.h, c->alpha_cells ? 1.0 : c->alpha);
@@ -772,7 +780,21 @@ TileArgs<T> tile_args(const Level& lv) {
   a.eta = etap<T>(lv);
   a.alpha = alphap<T>(lv);
   a.shape = lv.shape;
+  a.err = lv.errw;
   return a;
+}
+
+// Report (and clear) a bounded wait that gave up in any kernel since the last check.
+gs_status check_device_error(gs_ctx* c) {
+  if (!c->errw) return GS_OK;
+  int* h = reinterpret_cast<int*>(c->hpin);
+  CK(cudaMemcpyAsync(h, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (*h != 0) {
+    CK(cudaMemsetAsync(c->errw, 0, sizeof(int), c->st));
+    return fail(GS_ETIMEOUT, "a kernel's wait for its staged data gave up after about a second");
+  }
+  return GS_OK;
 }
 
 // dot products of T vectors accumulated in FP64, result copied to host
@@ -1141,7 +1163,7 @@ gs_status autotune(gs_ctx* c) {
   CK(cudaMemsetAsync(c->r, 0, sizeof(double) * c->N, c->st));
   double best_us = 0.0;
   int best = 0;
-  for (int s = 0; s < kTileShapes2D; ++s) {
+  for (int s = 0; s < kTileHeights2D; ++s) {
     c->saddle_shape = s;
     double us;
     CKS(time_launches(c, [&]() -> cudaError_t {
@@ -1153,6 +1175,7 @@ gs_status autotune(gs_ctx* c) {
 }
 
 gs_status setup(gs_ctx* c) {
+  CK(cudaMemsetAsync(c->errw, 0, sizeof(int) * 4, c->st));
   // upload per-level data
   for (int l = 0; l < c->L; ++l) {
     Level& lv = c->lv[l];
@@ -1182,6 +1205,21 @@ gs_status setup(gs_ctx* c) {
     if (lv.has_void) {
       CK(cudaMemcpyAsync(lv.cvoid, lv.hvoid.data(), lv.Nc, cudaMemcpyHostToDevice, c->st));
       CK(cudaMemcpyAsync(lv.vmask, lv.hvmask.data(), lv.Nv, cudaMemcpyHostToDevice, c->st));
+      if (lv.ccmask) {
+        // per cell: bit la + 3 lb for a constrained local node, bit 15 for an obstacle cell
+        const long long nv0 = 2 * lv.n[0] + 1;
+        lv.hccmask.assign(lv.Nc, 0);
+        for (int j = 0; j < lv.n[1]; ++j)
+          for (int i = 0; i < lv.n[0]; ++i) {
+            const long long cc = i + (long long)lv.n[0] * j;
+            unsigned m = lv.hvoid[cc] ? 0x8000u : 0u;
+            for (int lb = 0; lb < 3; ++lb)
+              for (int la = 0; la < 3; ++la)
+                if (lv.hvmask[(2 * i + la) + nv0 * (2 * j + lb)]) m |= 1u << (la + 3 * lb);
+            lv.hccmask[cc] = (uint16_t)m;
+          }
+        CK(cudaMemcpyAsync(lv.ccmask, lv.hccmask.data(), sizeof(uint16_t) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+      }
       if (lv.pmask) CK(cudaMemcpyAsync(lv.pmask, lv.hpmask.data(), lv.Np, cudaMemcpyHostToDevice, c->st));
     }
     CK(cudaStreamSynchronize(c->st));  // host staging vectors go out of scope
@@ -1243,7 +1281,7 @@ gs_status setup(gs_ctx* c) {
     CKS(c->fp32 ? autotune<float>(c) : autotune<double>(c));
   } else if (c->dim == 2) {
     for (int l = 0; l < c->L; ++l) c->lv[l].shape = c->opt.tile_autotune - 1;
-    c->saddle_shape = c->opt.tile_autotune - 1;
+    c->saddle_shape = std::min(c->opt.tile_autotune - 1, kTileHeights2D - 1);
   }
   return GS_OK;
 }
@@ -2581,6 +2619,7 @@ gs_status gs_solve_A(gs_ctx* c, const double* rhs, double* x, double tol, int* i
   c->last_rel = rel;
   if (iterations) *iterations = it;
   if (rel_residual) *rel_residual = rel;
+  CKS(check_device_error(c));
   if (st == GS_EBREAKDOWN) return fail(st, "CG breakdown (p . A p <= 0)");
   if (st == GS_ENOCONV) return fail(st, "CG did not reach the tolerance");
   return GS_OK;
@@ -2589,7 +2628,9 @@ gs_status gs_solve_A(gs_ctx* c, const double* rhs, double* x, double tol, int* i
 gs_status gs_solve(gs_ctx* c, const double* rhs, double* x, double tol, int* iterations, double* rel_residual) {
   if (!c || !rhs || !x) return fail(GS_EINVAL, "NULL argument");
   if (!(tol > 0.0)) return fail(GS_EINVAL, "tol must be > 0");
-  return fgmres(c, rhs, x, tol, iterations, rel_residual);
+  const gs_status st = fgmres(c, rhs, x, tol, iterations, rel_residual);
+  const gs_status dev = check_device_error(c);
+  return dev != GS_OK ? dev : st;
 }
 
 gs_status gs_lift_rhs(gs_ctx* c, const double* f, const double* g, double* rhs) {
@@ -2703,7 +2744,7 @@ gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
   out->schur_cc = c->cc ? 1 : 0;
   out->pressure_coarse_free = c->nfp;
   for (int l = 0; l < c->L && l < 16; ++l) out->plambda_max[l] = c->lv[l].plam_hi;
-  static const int rows[kTileShapes2D] = {16, 17, 8};
+  static const int rows[kTileShapes2D] = {16, 17, 8, 0};
   for (int l = 0; l < c->L && l < 16; ++l) out->tile_rows[l] = c->dim == 2 ? rows[c->lv[l].shape] : 0;
   out->saddle_tile_rows = c->dim == 2 ? rows[c->saddle_shape] : 0;
   out->deflation_inclusions = c->defl_ninc;

@@ -16,6 +16,8 @@ struct Geom {
   const uint8_t* vmask;  // per velocity node, 1 = constrained; NULL -> faces only
   const uint8_t* pmask;  // per pressure node, 1 = constrained; NULL -> none
   const uint8_t* cvoid;  // per cell, 1 = obstacle; NULL -> none
+  const uint16_t* ccmask;  // 2D meshes with obstacles: per cell, bit la + 3 lb = local node constrained,
+                           // bit 15 = obstacle cell; NULL -> derive from the faces
   double h[3];
 };
 

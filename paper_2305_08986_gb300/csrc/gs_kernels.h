@@ -33,10 +33,13 @@ struct TileArgs {
   T c1, c2;       // CHEB: d <- c1 d + c2 dinv r   (c1 ignored when use_d == 0)
   int use_d;
   int raw;        // 1: no constraint elimination (operator of the unconstrained forms)
+  int* err;       // device word set nonzero when a bounded wait of the kernel gave up (may be NULL)
   int tiles[3];
-  int shape;      // 2D tile height variant (0: 16, 1: 17, 2: 8 rows of evaluated cells)
+  int shape;      // 2D velocity-block variant (0 / 1 / 2: tiles of 16 / 17 / 8 rows of evaluated cells,
+                  // 3: the strip kernel of gs_strip2d.cuh; other operator blocks: 3 -> tiles of 8)
 };
-constexpr int kTileShapes2D = 3;
+constexpr int kTileShapes2D = 4;   // velocity-block variants the autotuner times
+constexpr int kTileHeights2D = 3;  // tile variants of the full saddle operator
 
 // Which blocks of the saddle operator a launch computes.
 enum TileOps { OPS_A = 1, OPS_BT = 2, OPS_B = 4 };
@@ -45,6 +48,8 @@ template <typename T>
 cudaError_t launch_tile(int dim, int mode, int ops, TileArgs<T> a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_strip2d(int mode, TileArgs<T> a, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, const T* alpha, T* out, int invert,

@@ -276,8 +276,7 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
           }
       }
       if (WA) {
-        cell_A2(0, xl, yl[0], eta, cK);
-        cell_A2(1, xl, yl[1], eta, cK);
+        cell_A2(xl, yl, eta, cK);
       }
       if (WBT) {
         T pl[4];

@@ -14,14 +14,16 @@ template cudaError_t launch_tile2d_e16<double>(int, int, const TileArgs<double>&
 
 namespace gs {
 
-// Tile height per launch: TileArgs::shape 0 -> 16 rows of evaluated cells, 1 -> 17, 2 -> 8 (every
-// mode and operator).  The result does not depend on the height: every node sums its cell
-// contributions in a fixed order.
+// Variant per launch: TileArgs::shape 0 -> tiles of 16 rows of evaluated cells, 1 -> 17, 2 -> 8,
+// 3 -> the strip kernel for the velocity block (gs_strip2d.cu; tiles of 8 rows for the other
+// blocks).  The result does not depend on the variant: every node sums its cell contributions in
+// the same fixed order.
 template <typename T>
 cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st) {
   if (mode == TILE_CHEB && ops != OPS_A) return cudaErrorInvalidValue;
+  if (a.shape == 3 && ops == OPS_A && 2 * a.g.Nv < (1LL << 31)) return launch_strip2d<T>(mode, a, st);
   if (a.shape == 1) return launch_tile2d_e17<T>(mode, ops, a, st);
-  if (a.shape == 2) return launch_tile2d_e8<T>(mode, ops, a, st);
+  if (a.shape == 2 || a.shape == 3) return launch_tile2d_e8<T>(mode, ops, a, st);
   return launch_tile2d_e16<T>(mode, ops, a, st);
 }
 template cudaError_t launch_tile2d<float>(int, int, TileArgs<float>, cudaStream_t);
