@@ -112,15 +112,19 @@ typedef struct {            /* zero-initialised = defaults */
                                   captured at its second application (default); 1: plain launches */
   int plap_degree;          /* Chebyshev degree of the pressure-Laplacian V-cycle of the
                                Cahouet-Chabard term; 0 -> 2 */
-  int krylov_fp64;          /* 0: FGMRES basis V stored as double-float pairs (hi + lo, 48-bit),
-                                  Gram-Schmidt products on the FP32 pipes (default);
-                               1: basis and Gram-Schmidt in IEEE FP64 */
+  int krylov_fp64;          /* 0 (default) or 1: FGMRES basis V and the Gram-Schmidt products and
+                                  updates in IEEE FP64;
+                               2: basis stored as double-float pairs (hi + lo, ~48 significant
+                                  bits, the same 8 bytes), Gram-Schmidt products on the FP32 pipes
+                                  with FP64 sums of the partial results */
   int tile_autotune;        /* 2D meshes: 0 -> at gs_create, time each compiled variant of the
                                   velocity-block kernel on every level (cell tiles of 32 x 16,
                                   32 x 17, 32 x 8 evaluated cells; the strip kernel, 31-cell column
                                   strips marching up row segments) and keep the fastest (default);
                                   1 / 2 / 3 -> always the 32 x 16 / 32 x 17 / 32 x 8 tile; 4 -> always
-                                  the strip kernel (the FP64 saddle operator then uses 32 x 8 tiles).
+                                  the strip kernel (the FP64 saddle operator then uses 32 x 8 tiles);
+                                  5 -> by size, the strip kernel on levels of at least 32,768 cells
+                                  and 32 x 8 tiles below (no timing at gs_create).
                                   Every variant sums a node's cell contributions in the same order,
                                   so the results do not depend on the choice. */
   int deflate;              /* 1: rigid-body deflation of stiff inclusions in the V-cycle's finest

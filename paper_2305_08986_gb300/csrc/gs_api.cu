@@ -254,8 +254,9 @@ gs_options normalize_opts(const gs_options* o) {
   r.orth = r.orth == 1 ? 1 : 0;
   r.graphs = r.graphs == 1 ? 1 : 0;
   r.plap_degree = opt_or(r.plap_degree, 2);
-  r.krylov_fp64 = r.krylov_fp64 == 1 ? 1 : 0;
-  r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 4) ? r.tile_autotune : 0;
+  // 0 (default) and 1: IEEE FP64 basis; 2: double-float basis (stored internally as 0 / 1 = double-float / FP64)
+  r.krylov_fp64 = r.krylov_fp64 == 2 ? 0 : 1;
+  r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 5) ? r.tile_autotune : 0;
   r.deflate = r.deflate == 1 ? 1 : 0;
   r.precond_kind = r.precond_kind == 1 ? 1 : 0;
   r.mono_smooth = opt_or(r.mono_smooth, 2);
@@ -1279,6 +1280,10 @@ gs_status setup(gs_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
   if (c->dim == 2 && c->opt.tile_autotune == 0) {
     CKS(c->fp32 ? autotune<float>(c) : autotune<double>(c));
+  } else if (c->dim == 2 && c->opt.tile_autotune == 5) {
+    // size rule: the strip kernel where a level has enough cells to fill the GPU, 32 x 8 tiles below
+    for (int l = 0; l < c->L; ++l) c->lv[l].shape = c->lv[l].Nc >= 32768 ? 3 : 2;
+    c->saddle_shape = 2;
   } else if (c->dim == 2) {
     for (int l = 0; l < c->L; ++l) c->lv[l].shape = c->opt.tile_autotune - 1;
     c->saddle_shape = std::min(c->opt.tile_autotune - 1, kTileHeights2D - 1);
@@ -1692,13 +1697,39 @@ gs_status norm2_host(gs_ctx* c, const double* x, double* out) {
 // CGS2 with the double-float basis (orth = 0): h1 = V^T w; w -= V h1 fused with h2 = V^T w (one
 // pass over V); w -= V h2 with the new |w|^2.  h1, h2: j + 1 entries each, nrm: |w|^2 (device).
 const int kFusedGsMax = 64;
-gs_status cgs2_fused(gs_ctx* c, const float2* Vdf, int j, double* h1, double* h2, double* nrm) {
+cudaError_t dots_strip(const float2* V, long long ldv, int k, const double* w, long long n, double* part, int G,
+                       cudaStream_t st) {
+  return launch_dots_strip_df(V, ldv, k, w, n, part, G, st);
+}
+cudaError_t dots_strip(const double* V, long long ldv, int k, const double* w, long long n, double* part, int G,
+                       cudaStream_t st) {
+  return launch_dots_strip_fp64(V, ldv, k, w, n, part, G, st);
+}
+cudaError_t multi_axpy_dots(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
+                            long long n, double* part, int G, cudaStream_t st) {
+  return launch_multi_axpy_dots_df(V, ldv, k, coef, sign, w, n, part, G, st);
+}
+cudaError_t multi_axpy_dots(const double* V, long long ldv, int k, const double* coef, double sign, double* w,
+                            long long n, double* part, int G, cudaStream_t st) {
+  return launch_multi_axpy_dots_fp64(V, ldv, k, coef, sign, w, n, part, G, st);
+}
+cudaError_t multi_axpy_norm_b(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
+                              long long n, double* part, int G, cudaStream_t st) {
+  return launch_multi_axpy_norm_df(V, ldv, k, coef, sign, w, n, part, G, st);
+}
+cudaError_t multi_axpy_norm_b(const double* V, long long ldv, int k, const double* coef, double sign, double* w,
+                              long long n, double* part, int G, cudaStream_t st) {
+  return launch_multi_axpy_norm_fp64(V, ldv, k, coef, sign, w, n, part, G, st);
+}
+// CGS2 (orth = 0) in three passes over V, for a double-float (float2) or IEEE FP64 (double) basis.
+template <typename B>
+gs_status cgs2_fused(gs_ctx* c, const B* V, int j, double* h1, double* h2, double* nrm) {
   const long long N = c->N;
-  KL(K_DOTS, launch_dots_strip_df(Vdf, N, j + 1, c->w, N, c->part, c->GF, c->st));
+  KL(K_DOTS, dots_strip(V, N, j + 1, c->w, N, c->part, c->GF, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->GF, h1, c->st));
-  KL(K_AXPY, launch_multi_axpy_dots_df(Vdf, N, j + 1, h1, -1.0, c->w, N, c->part, c->GF, c->st));
+  KL(K_AXPY, multi_axpy_dots(V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GF, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->GF, h2, c->st));
-  KL(K_AXPY, launch_multi_axpy_norm_df(Vdf, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+  KL(K_AXPY, multi_axpy_norm_b(V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
   return GS_OK;
 }
@@ -1756,9 +1787,12 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       // |w|^2 in the same pass); a second pass when |w| fell below 1/sqrt(2) of its value
       // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, orth = 0)
       double hn;
-      if (c->opt.orth == 0 && dfk && j + 1 <= kFusedGsMax) {
+      if (c->opt.orth == 0 && j + 1 <= kFusedGsMax) {
         // CGS2 with the first update fused into the second pass's dots: three passes over V
-        CKS(cgs2_fused(c, Vdf, j, h1, h2, nrm));
+        if (dfk)
+          CKS(cgs2_fused(c, (const float2*)Vdf, j, h1, h2, nrm));
+        else
+          CKS(cgs2_fused(c, (const double*)c->V, j, h1, h2, nrm));
         CK(cudaMemcpyAsync(c->hpin, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(c->hpin + (j + 1), h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(c->hpin + 2 * (j + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -2275,8 +2309,11 @@ gs_status slot_record_post(gs_ctx* c, double* gather_dev) {
       double* nrm = sl_nrm(c);
       CKS(c->fp32 ? sl_cast_out<float>(c, v, Zj) : sl_cast_out<double>(c, v, Zj));
       CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
-      if (dfk && j + 1 <= kFusedGsMax) {
-        CKS(cgs2_fused(c, Vdf, j, h1, h2, nrm));
+      if (j + 1 <= kFusedGsMax) {
+        if (dfk)
+          CKS(cgs2_fused(c, (const float2*)Vdf, j, h1, h2, nrm));
+        else
+          CKS(cgs2_fused(c, (const double*)c->V, j, h1, h2, nrm));
       } else {
         if (dfk)
           KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 1, c->st));

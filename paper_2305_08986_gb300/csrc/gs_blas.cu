@@ -316,40 +316,61 @@ cudaError_t launch_dots_partial_df(const float2* V, long long ldv, int k, const 
   return submit<DotsDfK<8>>({V, ldv, k, w, n, part, self_dot}, G, 0, st);
 }
 
-// part[i * nblk + blk] = partial sums of V[i] . w (i < k <= 64), double-float products: a block
-// stages a 256-element strip of w in shared memory as double-float, and warp q dots basis rows
-// q, q + 8, q + 16, ... against it (coalesced rows, eight loads in flight per thread); every
-// row and w are read once.  The dot-only counterpart of MultiAxpyDotsDfK's second phase.
-struct DotsStripDfK {
+// Arithmetic of a Krylov basis element: double-float pairs (float2, products on the FP32 pipes)
+// or IEEE doubles (FP64 fused multiply-add).  The fused CGS2 kernels below are written once for both.
+template <typename B>
+struct BasisOps;
+template <>
+struct BasisOps<float2> {
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ float2 split(double a) { return df_split(a); }
+  static __device__ __forceinline__ double join(float2 v) { return df_join(v); }
+  static __device__ __forceinline__ void fma(float2& acc, float2 a, float2 b) { df_fma(acc, a, b); }
+};
+template <>
+struct BasisOps<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double split(double a) { return a; }
+  static __device__ __forceinline__ double join(double v) { return v; }
+  static __device__ __forceinline__ void fma(double& acc, double a, double b) { acc = ::fma(a, b, acc); }
+};
+
+// part[i * nblk + blk] = partial sums of V[i] . w (i < k <= 64): a block stages a 256-element strip
+// of w in shared memory (in the basis arithmetic), and warp q dots basis rows q, q + 8, q + 16, ...
+// against it (coalesced rows, eight loads in flight per thread); every row and w are read once.
+// The dot-only counterpart of MultiAxpyDotsK's second phase.
+template <typename B>
+struct DotsStripK {
+  using O = BasisOps<B>;
   static constexpr int KW = 8;  // basis vectors per warp
-  struct Args { const float2* V; long long ldv; int k; const double* w; long long n; double* part; };
+  struct Args { const B* V; long long ldv; int k; const double* w; long long n; double* part; };
   static constexpr int THREADS = TPB, MINB = 4;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
-    __shared__ float2 wt[TPB];
-    const float2* __restrict__ V = a.V;
+    __shared__ B wt[TPB];
+    const B* __restrict__ V = a.V;
     const long long ldv = a.ldv, n = a.n;
     const int k = a.k;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    float2 acc[KW];
+    B acc[KW];
 #pragma unroll
-    for (int q = 0; q < KW; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < KW; ++q) acc[q] = O::zero();
     for (long long base = (long long)blk * TPB; base < n; base += (long long)nblk * TPB) {
       const long long e = base + tid;
-      wt[tid] = e < n ? df_split(a.w[e]) : make_float2(0.f, 0.f);
+      wt[tid] = e < n ? O::split(a.w[e]) : O::zero();
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < KW; ++q) {
         const int i = wid + 8 * q;
         if (i < k) {
-          const float2* Vi = V + i * ldv + base;
-          float2 v[8];
+          const B* Vi = V + i * ldv + base;
+          B v[8];
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const int el = lane + 32 * t;
-            v[t] = base + el < n ? Vi[el] : make_float2(0.f, 0.f);
+            v[t] = base + el < n ? Vi[el] : O::zero();
           }
 #pragma unroll
-          for (int t = 0; t < 8; ++t) df_fma(acc[q], v[t], wt[lane + 32 * t]);
+          for (int t = 0; t < 8; ++t) O::fma(acc[q], v[t], wt[lane + 32 * t]);
         }
       }
       __syncthreads();
@@ -358,7 +379,7 @@ struct DotsStripDfK {
     for (int q = 0; q < KW; ++q) {
       const int i = wid + 8 * q;
       if (i < k) {
-        double v = df_join(acc[q]);
+        double v = O::join(acc[q]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) a.part[(long long)i * nblk + blk] = v;
@@ -366,39 +387,51 @@ struct DotsStripDfK {
     }
   }
 };
+template <typename B>
+cudaError_t launch_dots_strip(const B* V, long long ldv, int k, const double* w, long long n, double* part, int G,
+                              cudaStream_t st) {
+  if (k > 8 * DotsStripK<B>::KW) return cudaErrorInvalidValue;
+  return submit<DotsStripK<B>>({V, ldv, k, w, n, part}, G, 0, st);
+}
 cudaError_t launch_dots_strip_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
                                  int G, cudaStream_t st) {
-  if (k > 8 * DotsStripDfK::KW) return cudaErrorInvalidValue;
-  return submit<DotsStripDfK>({V, ldv, k, w, n, part}, G, 0, st);
+  return launch_dots_strip<float2>(V, ldv, k, w, n, part, G, st);
+}
+cudaError_t launch_dots_strip_fp64(const double* V, long long ldv, int k, const double* w, long long n, double* part,
+                                   int G, cudaStream_t st) {
+  return launch_dots_strip<double>(V, ldv, k, w, n, part, G, st);
 }
 
-// w <- w + sign * sum_i coef[i] V[i] (sum carried in double-float), partial sums of the new |w|^2
-struct MultiAxpyNormDfK {
-  struct Args { const float2* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
+// w <- w + sign * sum_i coef[i] V[i] (sum carried in the basis arithmetic), partial sums of |w|^2
+template <typename B>
+struct MultiAxpyNormBK {
+  using O = BasisOps<B>;
+  struct Args { const B* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
   static constexpr int THREADS = TPB, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
-    extern __shared__ float2 cs2[];
+    extern __shared__ __align__(16) unsigned char cs_raw[];
+    B* cs2 = reinterpret_cast<B*>(cs_raw);
     __shared__ double sh[32];
-    const float2* __restrict__ V = a.V;
+    const B* __restrict__ V = a.V;
     double* __restrict__ w = a.w;
     const long long ldv = a.ldv;
     const int k = a.k;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) cs2[i] = df_split(a.sign * a.coef[i]);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cs2[i] = O::split(a.sign * a.coef[i]);
     __syncthreads();
     double s = 0.0;
     GS_FOR(e, a.n) {
       const double we = w[e];
-      float2 acc = make_float2(0.f, 0.f);
+      B acc = O::zero();
       int i = 0;
       for (; i + 8 <= k; i += 8) {  // eight basis loads in flight per thread
-        float2 v[8];
+        B v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = V[(i + u) * ldv + e];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) df_fma(acc, cs2[i + u], v[u]);
+        for (int u = 0; u < 8; ++u) O::fma(acc, cs2[i + u], v[u]);
       }
-      for (; i < k; ++i) df_fma(acc, cs2[i], V[i * ldv + e]);
-      const double r = we + df_join(acc);
+      for (; i < k; ++i) O::fma(acc, cs2[i], V[i * ldv + e]);
+      const double r = we + O::join(acc);
       w[e] = r;
       s += r * r;
     }
@@ -416,50 +449,57 @@ struct MultiAxpyNormDfK {
 };
 cudaError_t launch_multi_axpy_norm_df(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
                                       long long n, double* part, int G, cudaStream_t st) {
-  return submit<MultiAxpyNormDfK>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(float2) * (k > 0 ? k : 1), st);
+  return submit<MultiAxpyNormBK<float2>>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(float2) * (k > 0 ? k : 1), st);
+}
+cudaError_t launch_multi_axpy_norm_fp64(const double* V, long long ldv, int k, const double* coef, double sign,
+                                        double* w, long long n, double* part, int G, cudaStream_t st) {
+  return submit<MultiAxpyNormBK<double>>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(double) * (k > 0 ? k : 1), st);
 }
 
-// First CGS2 update fused with the second pass's dot products (double-float basis):
-//   w <- w + sign * sum_i coef[i] V[i]            (double-float sum, FP64 result)
+// First CGS2 update fused with the second pass's dot products:
+//   w <- w + sign * sum_i coef[i] V[i]            (sum in the basis arithmetic, FP64 result)
 //   part[i * nblk + blk] = sum over the block's elements of V[i] . w_new
 // The block walks its elements in rounds of 256: every thread updates one element and keeps the
-// new value (double-float) in shared memory, then warp q accumulates the dot products of basis
-// vectors q, q + 8, q + 16, ... over the round's 256 elements (coalesced rows; the rows were just
-// read by the update, so they come from L1/L2).  One pass over V from HBM instead of two.
-struct MultiAxpyDotsDfK {
+// new value in shared memory, then warp q accumulates the dot products of basis vectors q, q + 8,
+// q + 16, ... over the round's 256 elements (coalesced rows; the rows were just read by the update,
+// so they come from L1/L2).  One pass over V from HBM instead of two.
+template <typename B>
+struct MultiAxpyDotsK {
+  using O = BasisOps<B>;
   static constexpr int KW = 8;  // basis vectors per warp (k <= 64)
-  struct Args { const float2* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
+  struct Args { const B* V; long long ldv; int k; const double* coef; double sign; double* w; long long n; double* part; };
   static constexpr int THREADS = TPB, MINB = 4;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
-    extern __shared__ float2 cs2[];
-    __shared__ float2 wt[TPB];
-    const float2* __restrict__ V = a.V;
+    extern __shared__ __align__(16) unsigned char cs_raw[];
+    B* cs2 = reinterpret_cast<B*>(cs_raw);
+    __shared__ B wt[TPB];
+    const B* __restrict__ V = a.V;
     double* __restrict__ w = a.w;
     const long long ldv = a.ldv, n = a.n;
     const int k = a.k;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int i = tid; i < k; i += blockDim.x) cs2[i] = df_split(a.sign * a.coef[i]);
-    float2 acc[KW];
+    for (int i = tid; i < k; i += blockDim.x) cs2[i] = O::split(a.sign * a.coef[i]);
+    B acc[KW];
 #pragma unroll
-    for (int q = 0; q < KW; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < KW; ++q) acc[q] = O::zero();
     __syncthreads();
     for (long long base = (long long)blk * TPB; base < n; base += (long long)nblk * TPB) {
       const long long e = base + tid;
-      float2 wdf = make_float2(0.f, 0.f);
+      B wdf = O::zero();
       if (e < n) {
-        float2 s = make_float2(0.f, 0.f);
+        B s = O::zero();
         int i = 0;
         for (; i + 8 <= k; i += 8) {
-          float2 v[8];
+          B v[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) v[u] = V[(i + u) * ldv + e];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) df_fma(s, cs2[i + u], v[u]);
+          for (int u = 0; u < 8; ++u) O::fma(s, cs2[i + u], v[u]);
         }
-        for (; i < k; ++i) df_fma(s, cs2[i], V[i * ldv + e]);
-        const double r = w[e] + df_join(s);
+        for (; i < k; ++i) O::fma(s, cs2[i], V[i * ldv + e]);
+        const double r = w[e] + O::join(s);
         w[e] = r;
-        wdf = df_split(r);
+        wdf = O::split(r);
       }
       wt[tid] = wdf;
       __syncthreads();
@@ -467,15 +507,15 @@ struct MultiAxpyDotsDfK {
       for (int q = 0; q < KW; ++q) {
         const int i = wid + 8 * q;
         if (i < k) {
-          const float2* Vi = V + i * ldv + base;
-          float2 v[8];
+          const B* Vi = V + i * ldv + base;
+          B v[8];
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const int el = lane + 32 * t;
-            v[t] = base + el < n ? Vi[el] : make_float2(0.f, 0.f);
+            v[t] = base + el < n ? Vi[el] : O::zero();
           }
 #pragma unroll
-          for (int t = 0; t < 8; ++t) df_fma(acc[q], v[t], wt[lane + 32 * t]);
+          for (int t = 0; t < 8; ++t) O::fma(acc[q], v[t], wt[lane + 32 * t]);
         }
       }
       __syncthreads();
@@ -484,7 +524,7 @@ struct MultiAxpyDotsDfK {
     for (int q = 0; q < KW; ++q) {
       const int i = wid + 8 * q;
       if (i < k) {
-        double v = df_join(acc[q]);
+        double v = O::join(acc[q]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) a.part[(long long)i * nblk + blk] = v;
@@ -494,8 +534,13 @@ struct MultiAxpyDotsDfK {
 };
 cudaError_t launch_multi_axpy_dots_df(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
                                       long long n, double* part, int G, cudaStream_t st) {
-  if (k > 8 * MultiAxpyDotsDfK::KW) return cudaErrorInvalidValue;
-  return submit<MultiAxpyDotsDfK>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(float2) * (k > 0 ? k : 1), st);
+  if (k > 8 * MultiAxpyDotsK<float2>::KW) return cudaErrorInvalidValue;
+  return submit<MultiAxpyDotsK<float2>>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(float2) * (k > 0 ? k : 1), st);
+}
+cudaError_t launch_multi_axpy_dots_fp64(const double* V, long long ldv, int k, const double* coef, double sign,
+                                        double* w, long long n, double* part, int G, cudaStream_t st) {
+  if (k > 8 * MultiAxpyDotsK<double>::KW) return cudaErrorInvalidValue;
+  return submit<MultiAxpyDotsK<double>>({V, ldv, k, coef, sign, w, n, part}, G, sizeof(double) * (k > 0 ? k : 1), st);
 }
 
 // v_df <- w / sqrt(nrm2) in double-float form, and the same vector as double in vd

@@ -186,6 +186,13 @@ cudaError_t launch_multi_axpy_dots_df(const float2* V, long long ldv, int k, con
                                       double* w, long long n, double* part, int G, cudaStream_t st);
 cudaError_t launch_scale_by_rnorm_df(const double* w, const double* nrm2, float2* v, double* vd, long long n,
                                      cudaStream_t st);
+// the same three fused CGS2 passes on an IEEE FP64 basis (FP64 products and sums)
+cudaError_t launch_dots_strip_fp64(const double* V, long long ldv, int k, const double* w, long long n, double* part,
+                                   int G, cudaStream_t st);
+cudaError_t launch_multi_axpy_dots_fp64(const double* V, long long ldv, int k, const double* coef, double sign,
+                                        double* w, long long n, double* part, int G, cudaStream_t st);
+cudaError_t launch_multi_axpy_norm_fp64(const double* V, long long ldv, int k, const double* coef, double sign,
+                                        double* w, long long n, double* part, int G, cudaStream_t st);
 // w <- w + sign * sum_i coef[i] V[i]   (coef on device)
 cudaError_t launch_multi_axpy(const double* V, long long ldv, int k, const double* coef, double sign,
                               double* w, long long n, cudaStream_t st);

@@ -146,7 +146,7 @@ def test_engine_options_in_one_batch():
     """FP64 multigrid, the FP64 Krylov basis and the mass-only Schur term next to the defaults."""
     from paper_2305_08986_gb300 import gs
     probs = _problems()[:3]
-    opts = [dict(mg_precision=64), dict(krylov_fp64=1), dict(schur_kind=1, max_iter=3000)]
+    opts = [dict(mg_precision=64), dict(krylov_fp64=2), dict(schur_kind=1, max_iter=3000)]
     refs = [_engine_alone(p, **o) for p, o in zip(probs, opts)]
     setups = [_setup(p, **o) for p, o in zip(probs, opts)]
     eng = gs.Engine(4)

@@ -221,9 +221,9 @@ def test_graph_replay_matches_plain_launches(name):
     assert out[0][0] == out[1][0] and torch.equal(out[0][1], out[1][1])
 
 
-@pytest.mark.parametrize("krylov_fp64", [0, 1])
+@pytest.mark.parametrize("krylov_fp64", [0, 1, 2])
 def test_krylov_basis_arithmetic(krylov_fp64):
-    """Double-float (default) and IEEE FP64 Krylov bases both reach the oracle's solution."""
+    """IEEE FP64 (default, 0 and 1) and double-float (2) Krylov bases both reach the oracle's solution."""
     import torch
     from paper_2305_08986_gb300 import gs
     p = PROBLEMS["channel_small"]()
