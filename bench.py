@@ -869,6 +869,58 @@ def run_spheres(args):
 
 
 # --------------------------------------------------------------------------------------------
+# corrector stage (Sec. 3.1.2, Eq. "v_star"): the channel with the predictor solution as v°
+# --------------------------------------------------------------------------------------------
+def run_corrector(args):
+    """Solve the predictor system of the channel, then the corrector system with that velocity as
+    the convective field v° (rho = 1): FGMRES with the block-triangular preconditioner built on the
+    non-symmetric block (FP32 and FP64 multigrid), L2 flushed before every timed solve."""
+    import torch
+    from paper_2305_08986_gb300 import build as gsbuild
+    gsbuild.build(verbose=False)
+    from paper_2305_08986_gb300 import gs, inputs
+    dev = torch.device("cuda", 0)
+    p = inputs.config_channel(**WORKLOAD)
+    f = torch.tensor(p.f, device=dev)
+    g = torch.tensor(p.g, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+    out = {"workload": f"corrector stage, channel {WORKLOAD['nx']}x{WORKLOAD['ny']} Q2-Q1, v° = the predictor "
+                       "solution, rho 1, alpha 1e3, convection + streamline diffusion (Eq. a_stab), "
+                       f"{WORKLOAD['levels']} MG levels, FGMRES({args.restart}) FP64, rel-res 1e-8",
+           "l2": "flushed (256 MiB write) before every timed solve"}
+    for prec in (32, 64):
+        s = gs.Solver.from_problem(p, device=dev, mg_precision=prec, corrector=1, restart=args.restart,
+                                   max_iter=4000, tile_autotune=args.tile_autotune)
+        b = torch.empty_like(f)
+        s.lift_rhs(f, g, b)
+        x = torch.zeros_like(b)
+        it_p, _, _ = s.solve(b, x, tol=1e-10, allow_noconv=True)
+        vcirc = x[:s.n_u].cpu().numpy()
+        t0 = time.perf_counter()
+        s.set_corrector(vcirc, 1.0)
+        t_set = time.perf_counter() - t0
+        s.lift_rhs(f, g, b)
+        x.zero_()
+        s.solve(b, x, tol=TOL, allow_noconv=True)  # warm-up (graph capture)
+        ts = []
+        for _ in range(max(1, min(args.steps, 5))):
+            x.zero_()
+            flush.fill_(1.0)
+            a_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(st)
+            it, rr, _ = s.solve(b, x, tol=TOL, allow_noconv=True)
+            e_.record(st)
+            e_.synchronize()
+            ts.append(a_.elapsed_time(e_))
+        out["fp32_multigrid" if prec == 32 else "fp64_multigrid"] = {
+            "time_to_solve_ms": statistics.median(ts), "iterations": it, "rel_residual": rr,
+            "predictor_iterations": it_p, "set_corrector_s": t_set, "unknowns": s.n_total}
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------------------------
 # one solve inside an NVTX range (the command the committed launch-list summaries were taken with)
 # --------------------------------------------------------------------------------------------
 def run_solve_once(args):
@@ -994,7 +1046,8 @@ def main():
     ap.add_argument("--mesh", default="1280x224", help="--workload op: channel mesh")
     ap.add_argument("--dim3", type=int, default=0, help="--workload op: 3D sphere mesh n^3 instead")
     ap.add_argument("--workload", default="channel",
-                    choices=["channel", "batched", "serving", "spheres", "extension", "op", "solve_once"],
+                    choices=["channel", "batched", "serving", "spheres", "extension", "op", "solve_once",
+                             "corrector"],
                     help="channel: the contract line; batched / serving: the engine workloads; spheres: the 3D "
                          "64^3 inclusion workload (extra lines)")
     ap.add_argument("--instances", type=int, default=256)
@@ -1016,6 +1069,8 @@ def main():
         return run_op(args)
     if args.workload == "solve_once" and args.impl == "gs":
         return run_solve_once(args)
+    if args.workload == "corrector" and args.impl == "gs":
+        return run_corrector(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -150,6 +150,8 @@ typedef struct {            /* zero-initialised = defaults */
                                   schur_*, plap_degree and deflate do not apply. */
   int mono_smooth;          /* m of precond_kind 1; 0 -> 2 (Table NS-solver-parameters-1) */
   int mono_cycles;          /* n of precond_kind 1; 0 -> 1 */
+  int corrector;            /* 1: reserve the per-level fields of the corrector stage (2D; see
+                               gs_set_corrector); 0 -> none */
 } gs_options;
 
 /* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */
@@ -217,6 +219,25 @@ gs_status gs_solve_A(gs_ctx* ctx, const double* rhs, double* x, double tol, int*
  * constrained entries are used).  K_raw is the saddle matrix without constraint elimination.
  * All pointers device, length N; rhs must not alias f or g. */
 gs_status gs_lift_rhs(gs_ctx* ctx, const double* f, const double* g, double* rhs);
+
+/* Switch the context to the corrector stage of the time step (Sec. 3.1.2, Eq. "v_star"): the
+ * convective velocity is the unknown and v° = v# - w# is given, so the velocity block becomes
+ *   A_c = alpha M + 2 eta eps:eps + rho C(v°) + rho S(v°, r),
+ *   C: (phi_i, (v° . grad) phi_j) on each component,  S: the streamline diffusion of Eq. "a_stab",
+ *   sum_K r_K ((v° . grad) phi_i, (v° . grad) phi_j)_K with the Brooks-Hughes parameter
+ *   r_K = h_K / (2 |v°|_K p1) (coth Pe_K - 1 / Pe_K), Pe_K = rho |v°|_K h_K / (2 eta_K p1), p1 = 2,
+ *   |v°|_K at the cell centre, h_K the cell diameter, r_K = 0 where Pe_K < 1;
+ * both integrated with the 3 x 3 Gauss rule.  Every later gs_vmult / gs_vmult_A / gs_solve /
+ * gs_vcycle / gs_lift_rhs uses A_c (non-symmetric; B and B^T unchanged): the V-cycle smooths with
+ * A_c, its Chebyshev bounds come from 12 Lanczos steps on the symmetric part (A_c + A_c^T) / 2, the
+ * coarse levels take v° by injection (coarse node I = fine node 2 I) and the dense coarse solve
+ * factors A_c,0 (Gauss-Jordan; its symmetric part is positive definite).
+ * vcirc: host, d N_v doubles of the finest level (component-blocked, like a velocity vector);
+ * NULL switches back to the predictor stage (rho ignored).  rho >= 0.  2D meshes, contexts created
+ * with gs_options.corrector = 1 and the block-triangular preconditioner; synchronises the context
+ * stream (setup work: diagonals, Lanczos, coarse factorisation).  Not while the context is in a
+ * batching engine. */
+gs_status gs_set_corrector(gs_ctx* ctx, const double* vcirc, double rho);
 
 /* Solve `count` independent systems; ctxs[i] with rhs[i] -> x[i] (device pointers).
  * iterations / rel_residuals: host arrays of `count` entries or NULL.  Returns the first

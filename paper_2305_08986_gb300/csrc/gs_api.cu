@@ -81,6 +81,14 @@ struct Level {
   void *xA = nullptr, *xB = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
   double lam_hi = 0.0;
   int* errw = nullptr;  // the context's device error word (bounded waits that gave up)
+  // corrector stage (option corrector, 2D): v° on this level (injected), r_K per cell
+  std::vector<double> hvc, hrk;
+  double* vc64 = nullptr;
+  float* vc32 = nullptr;
+  double* rk64 = nullptr;
+  float* rk32 = nullptr;
+  int conv = 0;         // 1 while the context is in the corrector stage
+  double rho = 0.0;
   // pressure Laplacian level (Cahouet-Chabard term): constraint mask, MG vectors, bound
   std::vector<uint8_t> hpc;
   uint8_t* pcmask = nullptr;
@@ -257,6 +265,7 @@ gs_options normalize_opts(const gs_options* o) {
   // 0 (default) and 1: IEEE FP64 basis; 2: double-float basis (stored internally as 0 / 1 = double-float / FP64)
   r.krylov_fp64 = r.krylov_fp64 == 2 ? 0 : 1;
   r.tile_autotune = (r.tile_autotune >= 1 && r.tile_autotune <= 5) ? r.tile_autotune : 0;
+  r.corrector = r.corrector == 1 ? 1 : 0;
   r.deflate = r.deflate == 1 ? 1 : 0;
   r.precond_kind = r.precond_kind == 1 ? 1 : 0;
   r.mono_smooth = opt_or(r.mono_smooth, 2);
@@ -456,6 +465,8 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c, const doub
   c->mono = c->opt.precond_kind == 1;
   c->hmfree.clear();
   if (c->mono && c->opt.deflate == 1) return fail(GS_EINVAL, "deflation applies to the block-triangular preconditioner");
+  if (c->opt.corrector && (dim != 2 || c->mono || c->opt.deflate == 1))
+    return fail(GS_EINVAL, "the corrector stage is built for 2D meshes with the block-triangular preconditioner");
   if (c->mono && c->opt.coarse_mode != 1) {
     c->hmfree = c->hfree;
     for (long long q = 0; q < C0.Np; ++q)
@@ -627,6 +638,12 @@ void layout(gs_ctx* c, Arena& ar) {
       lv.pmask = ar.take<uint8_t>(lv.Np);
       if (c->dim == 2) lv.ccmask = ar.take<uint16_t>(lv.Nc);
     }
+    if (c->opt.corrector) {  // both precisions: FP32 applies are allowed on an FP64-multigrid context
+      lv.vc64 = ar.take<double>(lv.nu);
+      lv.rk64 = ar.take<double>(lv.Nc);
+      lv.vc32 = ar.take<float>(lv.nu);
+      lv.rk32 = ar.take<float>(lv.Nc);
+    }
     lv.xA = takeT(lv.nu);
     lv.xB = takeT(lv.nu);
     lv.b = takeT(lv.nu);
@@ -782,6 +799,15 @@ TileArgs<T> tile_args(const Level& lv) {
   a.alpha = alphap<T>(lv);
   a.shape = lv.shape;
   a.err = lv.errw;
+  if (lv.conv) {
+    a.conv = 1;
+    a.vc = sizeof(T) == 8 ? (const T*)lv.vc64 : (const T*)lv.vc32;
+    a.rk = sizeof(T) == 8 ? (const T*)lv.rk64 : (const T*)lv.rk32;
+    a.rho = (T)lv.rho;
+    a.ihx = (T)(1.0 / lv.h[0]);
+    a.ihy = (T)(1.0 / lv.h[1]);
+    a.wq = (T)(lv.h[0] * lv.h[1]);
+  }
   return a;
 }
 
@@ -898,6 +924,7 @@ gs_status lanczos(gs_ctx* c, int l) {
         TileArgs<T> a = tile_args<T>(lv);
         a.xu = x;
         a.yu = y;
+        if (a.conv) a.conv = 2;  // corrector stage: bounds of the symmetric part of the block
         return launch_tile<T>(c->dim, TILE_APPLY, OPS_A, a, c->st);
       },
       &lv.lam_hi);
@@ -930,6 +957,45 @@ gs_status plap_lanczos(gs_ctx* c, int l) {
 }
 
 // host assembly of the dense coarse matrix on its free unknowns (same closed-form 1D matrices)
+// Corrector stage: the cell's rho (C + S) block (component-diagonal, 9 x 9 per component) added to
+// the dense coarse matrix, by the 3 x 3 Gauss rule of the kernels (host copy of the 1D matrices).
+void add_conv_cell(const Level& lv, int i, int j, const std::vector<int>& map, int nf, std::vector<double>& A) {
+  const double s = 0.38729833462074168852;
+  const double Phi[3][3] = {{0.3 + s, 0.4, 0.3 - s}, {0.0, 1.0, 0.0}, {0.3 - s, 0.4, 0.3 + s}};
+  const double Dq[3][3] = {{-1.0 - 4.0 * s, 8.0 * s, 1.0 - 4.0 * s}, {-1.0, 0.0, 1.0}, {-1.0 + 4.0 * s, -8.0 * s, 1.0 + 4.0 * s}};
+  const double w[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  const double hx = lv.h[0], hy = lv.h[1];
+  const long long nv0 = 2 * lv.n[0] + 1;
+  const long long cc = i + (long long)lv.n[0] * j;
+  long long gn[9];
+  for (int q = 0; q < 9; ++q) gn[q] = (2 * i + q % 3) + nv0 * (2 * j + q / 3);
+  double vx[9] = {0}, vy[9] = {0};
+  for (int q = 0; q < 9; ++q)
+    for (int jn = 0; jn < 9; ++jn) {
+      const double ph = Phi[q % 3][jn % 3] * Phi[q / 3][jn / 3];
+      vx[q] += ph * lv.hvc[gn[jn]];
+      vy[q] += ph * lv.hvc[lv.Nv + gn[jn]];
+    }
+  const double r = lv.hrk[cc];
+  for (int p = 0; p < 9; ++p)
+    for (int qn = 0; qn < 9; ++qn) {
+      double v = 0.0;
+      for (int q = 0; q < 9; ++q) {
+        const int qa = q % 3, qb = q / 3;
+        const double W = w[qa] * w[qb] * hx * hy;
+        const double phi_p = Phi[qa][p % 3] * Phi[qb][p / 3];
+        const double adv_p = vx[q] * Dq[qa][p % 3] * Phi[qb][p / 3] / hx + vy[q] * Phi[qa][p % 3] * Dq[qb][p / 3] / hy;
+        const double adv_q = vx[q] * Dq[qa][qn % 3] * Phi[qb][qn / 3] / hx + vy[q] * Phi[qa][qn % 3] * Dq[qb][qn / 3] / hy;
+        v += W * (phi_p * adv_q + r * adv_p * adv_q);
+      }
+      v *= lv.rho;
+      for (int a = 0; a < 2; ++a) {
+        const int row = map[a * lv.Nv + gn[p]], col = map[a * lv.Nv + gn[qn]];
+        if (row >= 0 && col >= 0) A[(size_t)row * nf + col] += v;
+      }
+    }
+}
+
 void assemble_coarse(gs_ctx* c, std::vector<double>& A) {
   const Level& lv = c->lv[0];
   const int dim = c->dim;
@@ -993,6 +1059,7 @@ void assemble_coarse(gs_ctx* c, std::vector<double>& A) {
                 A[(size_t)row * nf + col] += v;
               }
             }
+        if (lv.conv) add_conv_cell(lv, i, j, map, nf, A);
       }
 }
 
@@ -1917,6 +1984,12 @@ gs_status apply_level_T(gs_ctx* c, int l, gs_op op, const void* xv, void* yv, co
       return GS_OK;
     }
     case GS_OP_DIAG_A:
+      if (lv.conv) {  // corrector stage: diag(A_c) = diag(A) + diag(rho (C + S)), formed in FP64
+        CK(launch_diagA<double>(lv.g, lv.c64, lv.eta64, lv.alpha64, c->t1, 0, c->st));
+        CK(launch_diag_conv(lv.g, lv.vc64, lv.rk64, lv.rho, c->t1, c->st));
+        CK(launch_cast<double, T>(c->t1, y, lv.nu, (T)1, c->st));
+        return GS_OK;
+      }
       CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), alphap<T>(lv), y, 0, c->st));
       return GS_OK;
     case GS_OP_SMOOTH: {
@@ -2679,6 +2752,7 @@ gs_status gs_lift_rhs(gs_ctx* c, const double* f, const double* g, double* rhs) 
     TileArgs<double> a = tile_args<double>(F);
     a.c = make_coef<double>(c->dim, F.h, 1.0);
     a.c.eta_scale = 0.0;
+    a.conv = 0;  // the load is the plain mass (the corrector terms belong to the operator)
     a.xu = f; a.yu = c->t1; a.raw = 1;
     CK(launch_tile<double>(c->dim, TILE_APPLY, OPS_A, a, c->st));
     PMassArgs<double> p{};
@@ -2690,6 +2764,108 @@ gs_status gs_lift_rhs(gs_ctx* c, const double* f, const double* g, double* rhs) 
   CK(launch_copy_constrained(g, c->w, F.g, c->st));
   CKS(saddle(c, TILE_APPLY, c->w, c->t2, nullptr, 1));
   CK(launch_combine_lift(c->t1, c->t2, g, F.vmask, F.pmask, F.g, rhs, c->st));
+  return GS_OK;
+}
+
+}  // extern "C"
+
+// ---- corrector stage (Sec. 3.1.2, Eq. "v_star" and Eq. "a_stab") ------------------------------
+namespace {
+// Brooks-Hughes streamline parameter r_K per cell: |v°| at the cell's centre node, h_K the cell
+// diameter, Pe = rho |v°| h_K / (2 eta_K p1), r_K = h_K / (2 |v°| p1) (coth Pe - 1 / Pe), p1 = 2,
+// and r_K = 0 where Pe < 1.
+void streamline_parameters(Level& lv, double rho) {
+  const long long nv0 = 2 * lv.n[0] + 1;
+  const double hK = std::sqrt(lv.h[0] * lv.h[0] + lv.h[1] * lv.h[1]);
+  lv.hrk.assign(lv.Nc, 0.0);
+  for (int j = 0; j < lv.n[1]; ++j)
+    for (int i = 0; i < lv.n[0]; ++i) {
+      const long long cc = i + (long long)lv.n[0] * j;
+      const long long ctr = (2 * i + 1) + nv0 * (2 * j + 1);
+      const double vn = std::sqrt(lv.hvc[ctr] * lv.hvc[ctr] + lv.hvc[lv.Nv + ctr] * lv.hvc[lv.Nv + ctr]);
+      const double eta = lv.heta[cc];
+      if (!(vn > 0.0) || !(eta > 0.0)) continue;
+      const double pe = rho * vn * hK / (2.0 * eta * 2.0);
+      if (pe >= 1.0) lv.hrk[cc] = hK / (2.0 * vn * 2.0) * (1.0 / std::tanh(pe) - 1.0 / pe);
+    }
+}
+
+template <typename T>
+gs_status corrector_setup_T(gs_ctx* c) {
+  for (int l = 0; l < c->L; ++l) {
+    Level& lv = c->lv[l];
+    if (lv.conv) {
+      CK(launch_diagA<double>(lv.g, lv.c64, lv.eta64, lv.alpha64, c->t1, 0, c->st));
+      CK(launch_diag_conv(lv.g, lv.vc64, lv.rk64, lv.rho, c->t1, c->st));
+      CK(launch_reciprocal<T>(c->t1, (T*)lv.dinv, lv.nu, c->st));
+    } else {
+      CK(launch_diagA<T>(lv.g, coef<T>(lv), etap<T>(lv), alphap<T>(lv), (T*)lv.dinv, 1, c->st));
+    }
+  }
+  for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(lanczos<T>(c, l));
+  return GS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gs_status gs_set_corrector(gs_ctx* c, const double* vcirc, double rho) {
+  if (!c) return fail(GS_EINVAL, "NULL argument");
+  if (!c->opt.corrector) return fail(GS_EINVAL, "the context was created without gs_options.corrector = 1");
+  if (c->dim != 2) return fail(GS_EINVAL, "the corrector stage is built for 2D meshes");
+  if (vcirc && !(rho >= 0.0 && std::isfinite(rho))) return fail(GS_EINVAL, "rho must be finite and >= 0");
+  const int L = c->L;
+  if (vcirc) {
+    Level& F = c->lv[L - 1];
+    for (long long i = 0; i < F.nu; ++i)
+      if (!std::isfinite(vcirc[i])) return fail(GS_EINVAL, "v° is not finite");
+    F.hvc.assign(vcirc, vcirc + F.nu);
+    for (int l = L - 2; l >= 0; --l) {  // injection: coarse node (I, J) takes fine node (2 I, 2 J)
+      Level& cl = c->lv[l];
+      const Level& fl = c->lv[l + 1];
+      const long long cnv0 = 2 * cl.n[0] + 1, fnv0 = 2 * fl.n[0] + 1;
+      cl.hvc.assign(cl.nu, 0.0);
+      for (int a = 0; a < 2; ++a)
+        for (long long J = 0; J < 2 * cl.n[1] + 1; ++J)
+          for (long long I = 0; I < cnv0; ++I)
+            cl.hvc[a * cl.Nv + I + cnv0 * J] = fl.hvc[a * fl.Nv + 2 * I + fnv0 * (2 * J)];
+    }
+    for (int l = 0; l < L; ++l) {
+      Level& lv = c->lv[l];
+      streamline_parameters(lv, rho);
+      lv.conv = 1;
+      lv.rho = rho;
+      CK(cudaMemcpyAsync(lv.vc64, lv.hvc.data(), sizeof(double) * lv.nu, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(lv.rk64, lv.hrk.data(), sizeof(double) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+      {
+        std::vector<float> v32(lv.hvc.begin(), lv.hvc.end()), r32(lv.hrk.begin(), lv.hrk.end());
+        CK(cudaMemcpyAsync(lv.vc32, v32.data(), sizeof(float) * lv.nu, cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(lv.rk32, r32.data(), sizeof(float) * lv.Nc, cudaMemcpyHostToDevice, c->st));
+        CK(cudaStreamSynchronize(c->st));  // the staging vectors go out of scope
+      }
+    }
+  } else {
+    for (int l = 0; l < L; ++l) c->lv[l].conv = 0;
+  }
+  // Jacobi diagonals and Chebyshev bounds (symmetric part) of every level, dense coarse inverse
+  CKS(c->fp32 ? corrector_setup_T<float>(c) : corrector_setup_T<double>(c));
+  if (c->nf > 0) {
+    std::vector<double> A;
+    assemble_coarse(c, A);
+    CK(cudaMemcpyAsync(c->Ainv, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, c->st));
+    for (int k = 0; k < c->nf; ++k) {
+      CK(launch_gj_save(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
+      CK(launch_gj_update(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
+    }
+  }
+  CK(cudaStreamSynchronize(c->st));
+  // the captured preconditioner and the engine's recorded body hold the old operators
+  if (c->pgraph) {
+    cudaGraphExecDestroy(c->pgraph);
+    c->pgraph = nullptr;
+  }
+  c->pcalls = 0;
+  c->ks.body_ok = false;
   return GS_OK;
 }
 

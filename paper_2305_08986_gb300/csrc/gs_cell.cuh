@@ -227,6 +227,103 @@ __device__ __forceinline__ void cell_A2(const T (&x)[2][9], T (&y)[2][9], T eta,
   }
 }
 
+// ---- corrector stage: convection by a given field and streamline diffusion (2D) -----------------
+// In the corrector stage (Sec. 3.1.2, Eq. "v_star") the velocity block gains
+//   rho ((v° . grad) u, w)                                   (convection by the given Q2 field v°)
+//   rho r_K ((v° . grad) u, (v° . grad) w)_K                 (streamline diffusion, Eq. "a_stab")
+// on every velocity component alike.  Both are evaluated at the 3 x 3 Gauss points of the cell
+// (the rule of every other cell integral) by sum factorisation with the 1D matrices
+//   Phi[q][j] = phi_j(g_q),  Dq[q][j] = phi_j'(g_q)  (g = 1/2 -+ sqrt(3/5)/2, 1/2 on [0, 1]),
+// i.e. v° and grad u are interpolated to the Gauss points, combined pointwise, weighted and swept
+// back with the transposed matrices.  With s = sqrt(3/5) / 2:
+//   Phi = [0.3+s 0.4 0.3-s; 0 1 0; 0.3-s 0.4 0.3+s],
+//   Dq  = [-1-4s 8s 1-4s; -1 0 1; -1+4s -8s 1+4s].
+struct GaussQ2 {
+  static constexpr double s = 0.38729833462074168852;   // sqrt(3/5) / 2
+  __host__ __device__ static constexpr double phi(int q, int j) {
+    return q == 1 ? (j == 1 ? 1.0 : 0.0) : (j == 1 ? 0.4 : (((q == 0) == (j == 0)) ? 0.3 + s : 0.3 - s));
+  }
+  __host__ __device__ static constexpr double dq(int q, int j) {
+    return q == 1 ? (j == 0 ? -1.0 : (j == 1 ? 0.0 : 1.0))
+                  : (j == 1 ? (q == 0 ? 8.0 * s : -8.0 * s) : (j == 0 ? -1.0 : 1.0) + (q == 0 ? -4.0 * s : 4.0 * s));
+  }
+  __host__ __device__ static constexpr double w(int q) { return q == 1 ? 8.0 / 18.0 : 5.0 / 18.0; }
+};
+
+// out[along axis AX] = M in (TR: M^T in), M one of the 3 x 3 Gauss matrices; arrays 3 x 3, x fastest.
+template <int AX, bool TR, bool DER, typename T>
+__device__ __forceinline__ void gsweep(const T* __restrict__ in, T* __restrict__ out) {
+#pragma unroll
+  for (int o = 0; o < 3; ++o)      // the other axis
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {  // output index along AX
+      T acc = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double m = TR ? (DER ? GaussQ2::dq(q, p) : GaussQ2::phi(q, p)) : (DER ? GaussQ2::dq(p, q) : GaussQ2::phi(p, q));
+        if (m == 0.0) continue;
+        const int ii = AX == 0 ? q : o, jj = AX == 0 ? o : q;
+        acc += T(m) * in[ii + 3 * jj];
+      }
+      const int io = AX == 0 ? p : o, jo = AX == 0 ? o : p;
+      out[io + 3 * jo] = acc;
+    }
+}
+
+// y += rho (C + S) u   (CONV = 1)   or   y += rho (S + (C + C^T) / 2) u   (CONV = 2, the symmetric
+// part, for the Chebyshev bounds of the non-symmetric block), for both components of u.
+// vc: the cell's nodal v° (two components), rK: the cell's streamline parameter, ihx = 1 / h_x,
+// ihy = 1 / h_y, wq = h_x h_y (the Jacobian of the Gauss weights).
+template <int CONV, typename T>
+__device__ __forceinline__ void cell_conv2(const T (&u)[2][9], const T (&vc)[2][9], T rho, T rK, T ihx, T ihy, T wq,
+                                           T (&y)[2][9]) {
+  T t[9], vx[9], vy[9], W[9];
+  gsweep<0, false, false>(vc[0], t);
+  gsweep<1, false, false>(t, vx);              // v°_x at the Gauss points
+  gsweep<0, false, false>(vc[1], t);
+  gsweep<1, false, false>(t, vy);              // v°_y at the Gauss points
+#pragma unroll
+  for (int qb = 0; qb < 3; ++qb)
+#pragma unroll
+    for (int qa = 0; qa < 3; ++qa) W[qa + 3 * qb] = T(GaussQ2::w(qa) * GaussQ2::w(qb)) * wq;
+  const T kc = CONV == 1 ? rho : T(0.5) * rho;  // weight of C u
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    T px[9], gx[9], gy[9], c[9], g[9], back[9];
+    gsweep<0, false, true>(u[a], t);
+    gsweep<1, false, false>(t, gx);             // d u / d x (reference), / h_x below
+    gsweep<0, false, false>(u[a], px);
+    gsweep<1, false, true>(px, gy);             // d u / d y (reference), / h_y below
+    T uq[9];
+    if (CONV == 2) gsweep<1, false, false>(px, uq);  // u at the Gauss points
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const T adv = vx[q] * gx[q] * ihx + vy[q] * gy[q] * ihy;  // v° . grad u
+      c[q] = kc * W[q] * adv;
+      g[q] = rho * rK * W[q] * adv;                            // streamline source
+      if (CONV == 2) g[q] += T(0.5) * rho * W[q] * uq[q];      // C^T u
+    }
+    // C u: (Phi^T x Phi^T) c
+    gsweep<0, true, false>(c, t);
+    gsweep<1, true, false>(t, back);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) y[a][i] += back[i];
+    // (v° . grad phi_i) terms: (Dq^T x Phi^T)(v°_x g) / h_x + (Phi^T x Dq^T)(v°_y g) / h_y
+#pragma unroll
+    for (int q = 0; q < 9; ++q) c[q] = vx[q] * g[q] * ihx;
+    gsweep<0, true, true>(c, t);
+    gsweep<1, true, false>(t, back);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) y[a][i] += back[i];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) c[q] = vy[q] * g[q] * ihy;
+    gsweep<0, true, false>(c, t);
+    gsweep<1, true, true>(t, back);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) y[a][i] += back[i];
+  }
+}
+
 // ---- 3D cell operators reading their input nodes from a shared-memory window ----------------------
 // x_a points to the cell's local node (0, 0, 0) of component a in the window; local node (i, j, k)
 // sits at x_a[i + ro[j] + po[k]] (row and plane offsets of the cell, which absorb any skew of the

@@ -34,6 +34,11 @@ struct TileArgs {
   int use_d;
   int raw;        // 1: no constraint elimination (operator of the unconstrained forms)
   int* err;       // device word set nonzero when a bounded wait of the kernel gave up (may be NULL)
+  // corrector stage (2D): conv = 1 adds rho (C + S) to A, conv = 2 the symmetric part of that term
+  int conv;
+  const T* vc;    // the convective field v° on this level (d N_v entries, component-blocked)
+  const T* rk;    // streamline parameter r_K per cell
+  T rho, ihx, ihy, wq;  // density, 1 / h_x, 1 / h_y, h_x h_y
   int tiles[3];
   int shape;      // 2D velocity-block variant (0 / 1 / 2: tiles of 16 / 17 / 8 rows of evaluated cells,
                   // 3: the strip kernel of gs_strip2d.cuh; other operator blocks: 3 -> tiles of 8)
@@ -50,6 +55,15 @@ template <typename T>
 cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_strip2d(int mode, TileArgs<T> a, cudaStream_t st);
+// the same operators with the corrector-stage terms (TileArgs::conv != 0), 32 x 8 tiles
+template <typename T>
+cudaError_t launch_tile2d_conv(int mode, int ops, const TileArgs<T>& a, cudaStream_t st);
+// diag += diag(rho (C + S)) on every free velocity node (both components); FP64
+cudaError_t launch_diag_conv(const Geom& g, const double* vc, const double* rk, double rho, double* diag,
+                             cudaStream_t st);
+// out[i] = 1 / in[i]
+template <typename T>
+cudaError_t launch_reciprocal(const double* in, T* out, long long n, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, const T* alpha, T* out, int invert,

@@ -564,4 +564,71 @@ INSTP(float)
 INSTP(double)
 #undef INSTP
 
+// ---- corrector stage: diagonal of rho (C + S) (setup, FP64) ----------------------------------
+// diag_i += rho sum_q W_q phi_i(q) (v° . grad phi_i)(q) + rho r_K sum_q W_q (v° . grad phi_i)(q)^2
+// summed over the active cells around free velocity node i (the same value for both components).
+__global__ void k_diag_conv(Geom g, const double* __restrict__ vc, const double* __restrict__ rk, double rho,
+                            double* __restrict__ diag) {
+  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= g.Nv) return;
+  const int I = (int)(node % g.nv[0]), J = (int)(node / g.nv[0]);
+  if (g.vmask ? g.vmask[node] != 0 : face_constrained(g, I, J, 0)) return;
+  const double hx = g.h[0], hy = g.h[1];
+  double acc = 0.0;
+  for (int cb = 0; cb < 2; ++cb)
+    for (int ca = 0; ca < 2; ++ca) {
+      // cells containing the node: column (I - 1) / 2 or I / 2 (both for an even, interior I)
+      const int c0 = (I % 2 == 0) ? (ca == 0 ? I / 2 : I / 2 - 1) : (ca == 0 ? I / 2 : -1);
+      const int c1 = (J % 2 == 0) ? (cb == 0 ? J / 2 : J / 2 - 1) : (cb == 0 ? J / 2 : -1);
+      if (c0 < 0 || c0 >= g.n[0] || c1 < 0 || c1 >= g.n[1]) continue;
+      const long long cell = c0 + (long long)g.n[0] * c1;
+      if (cell_void(g, cell)) continue;
+      const int la = I - 2 * c0, lb = J - 2 * c1;
+      double vx[9], vy[9];
+      for (int q = 0; q < 9; ++q) vx[q] = vy[q] = 0.0;
+      for (int jb = 0; jb < 3; ++jb)
+        for (int ja = 0; ja < 3; ++ja) {
+          const long long nd = (2 * c0 + ja) + (long long)g.nv[0] * (2 * c1 + jb);
+          const double v0 = vc[nd], v1 = vc[g.Nv + nd];
+          for (int qb = 0; qb < 3; ++qb)
+            for (int qa = 0; qa < 3; ++qa) {
+              const double ph = GaussQ2::phi(qa, ja) * GaussQ2::phi(qb, jb);
+              vx[qa + 3 * qb] += ph * v0;
+              vy[qa + 3 * qb] += ph * v1;
+            }
+        }
+      const double r = rk[cell];
+      for (int qb = 0; qb < 3; ++qb)
+        for (int qa = 0; qa < 3; ++qa) {
+          const int q = qa + 3 * qb;
+          const double W = GaussQ2::w(qa) * GaussQ2::w(qb) * hx * hy;
+          const double phi = GaussQ2::phi(qa, la) * GaussQ2::phi(qb, lb);
+          const double adv = vx[q] * GaussQ2::dq(qa, la) * GaussQ2::phi(qb, lb) / hx +
+                             vy[q] * GaussQ2::phi(qa, la) * GaussQ2::dq(qb, lb) / hy;
+          acc += W * (phi * adv + r * adv * adv);
+        }
+    }
+  diag[node] += rho * acc;
+  diag[g.Nv + node] += rho * acc;
+}
+cudaError_t launch_diag_conv(const Geom& g, const double* vc, const double* rk, double rho, double* diag,
+                             cudaStream_t st) {
+  if (g.dim != 2) return cudaErrorInvalidValue;
+  k_diag_conv<<<nblk(g.Nv), TPB, 0, st>>>(g, vc, rk, rho, diag);
+  return launched(cudaGetLastError(), 1);
+}
+
+template <typename T>
+__global__ void k_reciprocal(const double* __restrict__ in, T* __restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (T)(1.0 / in[i]);
+}
+template <typename T>
+cudaError_t launch_reciprocal(const double* in, T* out, long long n, cudaStream_t st) {
+  k_reciprocal<T><<<nblk(n), TPB, 0, st>>>(in, out, n);
+  return launched(cudaGetLastError(), 1);
+}
+template cudaError_t launch_reciprocal<float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_reciprocal<double>(const double*, double*, long long, cudaStream_t);
+
 }  // namespace gs

@@ -56,7 +56,7 @@ struct Shape2 {
   (void)PI0; (void)PI1; (void)VP0; (void)VP1; (void)OWN; (void)PP0; (void)PP1; (void)POWN;    \
   (void)ROWS; (void)IROWS; (void)CROWS
 
-template <int EY, int MODE, bool NEED_U, bool WBT, bool WU, bool WB>
+template <int EY, int MODE, bool NEED_U, bool WBT, bool WU, bool WB, int CONV = 0>
 struct Smem2 {
   static constexpr int NIN = Shape2<EY>::NIN, PI0 = Shape2<EY>::PI0, PI1 = Shape2<EY>::PI1;
   static constexpr int NCELL = Shape2<EY>::NCELL, OWN = Shape2<EY>::OWN, POWN = Shape2<EY>::POWN;
@@ -67,7 +67,8 @@ struct Smem2 {
   static constexpr int SB = (WU && MODE != TILE_APPLY) ? 2 * OWN : 0;   // b (residual / Chebyshev)
   static constexpr int SD = (WU && MODE == TILE_CHEB) ? 2 * OWN : 0;    // d and D^-1 (Chebyshev)
   static constexpr int SBP = (WB && MODE == TILE_RESID) ? POWN : 0;     // pressure b (residual)
-  static constexpr int TOTAL = SX + SP + RU + RP + SB + 2 * SD + SBP;   // elements of T
+  static constexpr int SV = CONV ? 2 * NIN : 0;                         // v° window (corrector stage)
+  static constexpr int TOTAL = SX + SP + RU + RP + SB + 2 * SD + SBP + SV;  // elements of T
   static constexpr int FLAGS = NEED_U ? NIN : 0;                        // bytes: constrained nodes
 };
 
@@ -117,12 +118,12 @@ __device__ __forceinline__ void gather2(const T* ru, int i0, int i1, T& s0, T& s
     }
   }
 }
-template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB, int CONV = 0>
 __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
   GS_SHAPE2_NAMES(EY);
   constexpr bool NEED_U = WA || WB;
   constexpr bool WU = WA || WBT;
-  using SM = Smem2<EY, MODE, NEED_U, WBT, WU, WB>;
+  using SM = Smem2<EY, MODE, NEED_U, WBT, WU, WB, CONV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sx = reinterpret_cast<T*>(smem_raw);
   T* sp = sx + SM::SX;
@@ -132,7 +133,8 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
   T* sd = sb + SM::SB;
   T* sdi = sd + SM::SD;
   T* sbp = sdi + SM::SD;
-  uint8_t* scon = reinterpret_cast<uint8_t*>(sbp + SM::SBP);
+  T* sv = sbp + SM::SBP;  // v° window (CONV)
+  uint8_t* scon = reinterpret_cast<uint8_t*>(sv + SM::SV);
   const Geom& g = A.g;
   const OpCoef<T>& c = A.c;
   const bool raw = A.raw != 0;
@@ -167,6 +169,10 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
           const int s = ix + IN0 * iy;
           cp_async_el(sx + s, A.xu + node, inr && !fcon);
           cp_async_el(sx + NIN + s, A.xu + Nv + node, inr && !fcon);
+          if (CONV) {
+            cp_async_el(sv + s, A.vc + node, inr);
+            cp_async_el(sv + NIN + s, A.vc + Nv + node, inr);
+          }
           mk[3 * r + q] = (vmasked && inr) ? g.vmask[node] : (fcon ? 1 : 0);
         }
       }
@@ -277,6 +283,18 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
       }
       if (WA) {
         cell_A2(xl, yl, eta, cK);
+        if (CONV) {
+          T vl[2][9];
+          const T* v0p = sv + 2 * e0 + IN0 * 2 * e1;
+#pragma unroll
+          for (int lb = 0; lb < 3; ++lb)
+#pragma unroll
+            for (int la = 0; la < 3; ++la) {
+              vl[0][la + 3 * lb] = v0p[la + IN0 * lb];
+              vl[1][la + 3 * lb] = v0p[NIN + la + IN0 * lb];
+            }
+          cell_conv2<CONV>(xl, vl, A.rho, A.rk[cell], A.ihx, A.ihy, A.wq, yl);
+        }
       }
       if (WBT) {
         T pl[4];
@@ -370,24 +388,44 @@ __device__ __forceinline__ void tile2d_body(const TileArgs<T>& A, int bid) {
   }
 }
 
-template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB, int CONV = 0>
 struct Tile2dK {
   using Args = TileArgs<T>;
-  static constexpr int THREADS = NT, MINB = 2;
+  static constexpr int THREADS = NT, MINB = CONV ? 1 : 2;
   static __device__ __forceinline__ void body(const Args& a, int blk, int) {
-    tile2d_body<T, EY, MODE, WA, WBT, WB>(a, blk);
+    tile2d_body<T, EY, MODE, WA, WBT, WB, CONV>(a, blk);
   }
 };
 
-template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int EY, int MODE, bool WA, bool WBT, bool WB, int CONV = 0>
 cudaError_t launch2(TileArgs<T> a, cudaStream_t st) {
   using S2 = Shape2<EY>;
-  using SM = Smem2<EY, MODE, WA || WB, WBT, WA || WBT, WB>;
+  using SM = Smem2<EY, MODE, WA || WB, WBT, WA || WBT, WB, CONV>;
   a.tiles[0] = (a.g.n[0] + S2::TO0 - 1) / S2::TO0;
   a.tiles[1] = (a.g.n[1] + S2::TO1 - 1) / S2::TO1;
   a.tiles[2] = 1;
   const size_t smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
-  return submit<Tile2dK<T, EY, MODE, WA, WBT, WB>>(a, (long long)a.tiles[0] * a.tiles[1], smem, st);
+  return submit<Tile2dK<T, EY, MODE, WA, WBT, WB, CONV>>(a, (long long)a.tiles[0] * a.tiles[1], smem, st);
+}
+
+// Velocity block and saddle operator with the corrector-stage terms (cell_conv2): conv = 1 adds
+// rho (C + S), conv = 2 the symmetric part rho (S + (C + C^T) / 2) (velocity block only).
+template <typename T, int EY>
+cudaError_t launch_conv_shape(int mode, int ops, const TileArgs<T>& a, cudaStream_t st) {
+  if (ops == OPS_A) {
+    if (a.conv == 2) {
+      if (mode == TILE_APPLY) return launch2<T, EY, TILE_APPLY, true, false, false, 2>(a, st);
+      return cudaErrorInvalidValue;
+    }
+    if (mode == TILE_APPLY) return launch2<T, EY, TILE_APPLY, true, false, false, 1>(a, st);
+    if (mode == TILE_RESID) return launch2<T, EY, TILE_RESID, true, false, false, 1>(a, st);
+    return launch2<T, EY, TILE_CHEB, true, false, false, 1>(a, st);
+  }
+  if (ops == (OPS_A | OPS_BT | OPS_B) && a.conv == 1) {
+    return mode == TILE_APPLY ? launch2<T, EY, TILE_APPLY, true, true, true, 1>(a, st)
+                              : launch2<T, EY, TILE_RESID, true, true, true, 1>(a, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 // Launch one tile height.  FULL: every mode / operator combination is compiled; otherwise only

@@ -21,6 +21,9 @@ namespace gs {
 template <typename T>
 cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st) {
   if (mode == TILE_CHEB && ops != OPS_A) return cudaErrorInvalidValue;
+  // corrector stage: launches that include the velocity block take the convection terms (32 x 8
+  // tiles); B and B^T alone are unchanged
+  if (a.conv && (ops & OPS_A)) return launch_tile2d_conv<T>(mode, ops, a, st);
   if (a.shape == 3 && ops == OPS_A && 2 * a.g.Nv < (1LL << 31)) return launch_strip2d<T>(mode, a, st);
   if (a.shape == 1) return launch_tile2d_e17<T>(mode, ops, a, st);
   if (a.shape == 2 || a.shape == 3) return launch_tile2d_e8<T>(mode, ops, a, st);

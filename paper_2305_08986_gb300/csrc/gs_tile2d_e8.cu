@@ -10,4 +10,11 @@ cudaError_t launch_tile2d_e8(int mode, int ops, const TileArgs<T>& a, cudaStream
 template cudaError_t launch_tile2d_e8<float>(int, int, const TileArgs<float>&, cudaStream_t);
 template cudaError_t launch_tile2d_e8<double>(int, int, const TileArgs<double>&, cudaStream_t);
 
+template <typename T>
+cudaError_t launch_tile2d_conv(int mode, int ops, const TileArgs<T>& a, cudaStream_t st) {
+  return tile2d::launch_conv_shape<T, 8>(mode, ops, a, st);
+}
+template cudaError_t launch_tile2d_conv<float>(int, int, const TileArgs<float>&, cudaStream_t);
+template cudaError_t launch_tile2d_conv<double>(int, int, const TileArgs<double>&, cudaStream_t);
+
 }  // namespace gs

@@ -39,7 +39,7 @@ class GsOptions(ctypes.Structure):
                 ("schur_kind", ctypes.c_int), ("orth", ctypes.c_int), ("graphs", ctypes.c_int),
                 ("plap_degree", ctypes.c_int), ("krylov_fp64", ctypes.c_int), ("tile_autotune", ctypes.c_int),
                 ("deflate", ctypes.c_int), ("precond_kind", ctypes.c_int), ("mono_smooth", ctypes.c_int),
-                ("mono_cycles", ctypes.c_int)]
+                ("mono_cycles", ctypes.c_int), ("corrector", ctypes.c_int)]
 
 
 class GsInfo(ctypes.Structure):
@@ -96,6 +96,8 @@ _lib.gs_profile_read.restype = ctypes.c_int
 _lib.gs_profile_read.argtypes = [_vp, ctypes.POINTER(GsKernelStat), ctypes.c_int]
 _lib.gs_profile_read_level.restype = ctypes.c_int
 _lib.gs_profile_read_level.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(GsKernelStat), ctypes.c_int]
+_lib.gs_set_corrector.restype = ctypes.c_int
+_lib.gs_set_corrector.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.c_double]
 _lib.gs_coarse_solve_noalloc.restype = ctypes.c_int
 _lib.gs_coarse_solve_noalloc.argtypes = [_vp, _vp, _vp]
 _lib.gs_set_stream.restype = ctypes.c_int
@@ -138,6 +140,7 @@ EXPORTED = ["gs_footprint_bytes", "gs_create", "gs_create_ex", "gs_vmult", "gs_v
             "gs_lift_rhs",
             "gs_batch_solve", "gs_apply_level", "gs_get_info", "gs_set_stream", "gs_destroy", "gs_strerror",
             "gs_last_error", "gs_profile", "gs_profile_read", "gs_profile_read_level", "gs_coarse_solve_noalloc",
+            "gs_set_corrector",
             "gs_engine_create",
             "gs_engine_add", "gs_engine_step", "gs_engine_poll", "gs_engine_active", "gs_engine_get_stats",
             "gs_engine_destroy"]
@@ -311,6 +314,18 @@ class Solver:
         else:
             n = _lib.gs_profile_read_level(self.ctx, int(level), arr, 32)
         return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n)}
+
+    def set_corrector(self, vcirc=None, rho=0.0):
+        """Corrector stage with the given convective field v° (numpy, d N_v entries of the finest
+        level); None returns to the predictor stage (gs_set_corrector)."""
+        if vcirc is None:
+            _check(_lib.gs_set_corrector(self.ctx, None, 0.0), "gs_set_corrector")
+            return
+        v = np.ascontiguousarray(np.asarray(vcirc, dtype=np.float64))
+        if v.shape != (self.n_u,):
+            raise ValueError(f"vcirc: expected {self.n_u} entries, got {v.shape}")
+        _check(_lib.gs_set_corrector(self.ctx, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(rho)),
+               "gs_set_corrector")
 
     def set_stream(self, stream):
         self.stream = stream
