@@ -275,7 +275,7 @@ typedef enum {
   GS_OP_SADDLE_VCYCLE = 19, /* y = V_l(x): one saddle-point V-cycle on level l, level vectors */
   GS_OP_SADDLE_COARSE = 20, /* y = M_0^{-1} x: dense saddle solve of level 0 (FP64 level
                             vectors, free unknowns; constrained entries of y are 0) */
-  GS_OP_CHEB_STEP = 21   /* one fused Chebyshev-Jacobi step on the caller's vectors (the kernel
+  GS_OP_CHEB_STEP = 21,  /* one fused Chebyshev-Jacobi step on the caller's vectors (the kernel
                             the smoother of Sec. 4 launches k_A - 1 times per call): with
                             aux = [b | d | D^-1] (3 x d N_v,l contiguous entries), r = b - A_l x,
                             d <- c1 d + c2 D^-1 r (in place in aux), y = x + d, where c1, c2 are
@@ -284,6 +284,11 @@ typedef enum {
                             levels with Chebyshev bounds only (not level 0 with the dense
                             coarse solve).  Lets a caller time the step on vectors of its own,
                             e.g. several copies that together exceed L2. */
+  GS_OP_WAIT_PROBE = 22  /* fault-path check (no paper counterpart): one CTA waits, with the
+                            bounded wait of the staged kernels, on an mbarrier phase that nothing
+                            completes; after about a second it gives up and sets the context's
+                            error word, so the next gs_solve / gs_solve_A returns GS_ETIMEOUT (and
+                            clears it).  x, y, aux ignored (y must be non-NULL). */
 } gs_op;
 
 /* Apply one operator of level `level` (0 = coarsest).  prec = 64: x, y, aux are double*;

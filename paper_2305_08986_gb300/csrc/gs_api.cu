@@ -2926,6 +2926,10 @@ gs_status gs_apply_level(gs_ctx* c, int level, gs_op op, int prec, const void* x
                                    c->st));
     return GS_OK;
   }
+  if (op == GS_OP_WAIT_PROBE) {
+    CK(launch_wait_probe(c->errw, c->st));
+    return GS_OK;
+  }
   if (op == GS_OP_PRECOND) {
     if (level != c->L - 1 || !x) return fail(GS_EINVAL, "preconditioner: finest level, x required");
     return precond(c, (const double*)x, (double*)y);

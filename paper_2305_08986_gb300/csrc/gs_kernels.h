@@ -55,6 +55,8 @@ template <typename T>
 cudaError_t launch_tile2d(int mode, int ops, TileArgs<T> a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_strip2d(int mode, TileArgs<T> a, cudaStream_t st);
+// one CTA whose bounded mbarrier wait runs out (about a second) and sets *err
+cudaError_t launch_wait_probe(int* err, cudaStream_t st);
 // the same operators with the corrector-stage terms (TileArgs::conv != 0), 32 x 8 tiles
 template <typename T>
 cudaError_t launch_tile2d_conv(int mode, int ops, const TileArgs<T>& a, cudaStream_t st);

@@ -89,4 +89,17 @@ cudaError_t launch_strip2d(int mode, TileArgs<T> a, cudaStream_t st) {
 template cudaError_t launch_strip2d<float>(int, TileArgs<float>, cudaStream_t);
 template cudaError_t launch_strip2d<double>(int, TileArgs<double>, cudaStream_t);
 
+// Fault-path probe: waits on a phase of an mbarrier that nothing completes (count 1, no arrival),
+// through the same bounded wait as the strip kernel, which gives up and sets *err.
+__global__ void k_wait_probe(int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) strip2d::mbar_init(&bar, 1);
+  __syncthreads();
+  strip2d::mbar_wait(&bar, 0u, err);
+}
+cudaError_t launch_wait_probe(int* err, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(err);
+  return launched(cudaGetLastError(), 1);
+}
+
 }  // namespace gs

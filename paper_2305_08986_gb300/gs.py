@@ -24,7 +24,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 GS_OK, GS_EINVAL, GS_ENOMEM, GS_ECUDA, GS_ENOCONV, GS_EBREAKDOWN, GS_ETIMEOUT, GS_EBUSY = range(8)
 (OP_A, OP_RESIDUAL_A, OP_DIAG_A, OP_SMOOTH, OP_RESTRICT, OP_PROLONGATE, OP_B, OP_BT,
  OP_SCHUR_MASS, OP_SCHUR_INV, OP_COARSE, OP_PRECOND, OP_A_RAW, OP_PLAP, OP_PLAP_INV, OP_PRESTRICT,
- OP_PPROLONGATE, OP_SCHUR_DIAG, OP_SADDLE_SMOOTH, OP_SADDLE_VCYCLE, OP_SADDLE_COARSE, OP_CHEB_STEP) = range(22)
+ OP_PPROLONGATE, OP_SCHUR_DIAG, OP_SADDLE_SMOOTH, OP_SADDLE_VCYCLE, OP_SADDLE_COARSE, OP_CHEB_STEP,
+ OP_WAIT_PROBE) = range(23)
 
 
 class GsMesh(ctypes.Structure):

@@ -322,3 +322,28 @@ def test_non_finite_input_reports_breakdown():
     x = torch.zeros_like(b)
     it, rr, st = s.solve(b, x, tol=1e-8)
     assert st == gs.GS_OK and rr <= 1e-8
+
+
+def test_bounded_wait_reports_timeout_and_the_context_recovers():
+    """A wait that runs out (an mbarrier phase nothing completes, GS_OP_WAIT_PROBE) sets the error
+    word after about a second; the next solve reports GS_ETIMEOUT and clears it, and the solve after
+    that succeeds: no hang, no fault, the context stays usable."""
+    import time
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS["disc16"]()
+    s = gs.Solver.from_problem(p)
+    b = torch.empty(s.n_total, dtype=torch.float64, device="cuda")
+    s.lift_rhs(torch.tensor(p.f, device="cuda"), torch.tensor(p.g, device="cuda"), b)
+    dummy = torch.empty(1, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    s.apply_level(p.levels - 1, gs.OP_WAIT_PROBE, None, dummy)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 30.0
+    x = torch.zeros_like(b)
+    with pytest.raises(gs.GsError) as e:
+        s.solve(b, x, tol=1e-8)
+    assert e.value.status == gs.GS_ETIMEOUT
+    x = torch.zeros_like(b)
+    it, rr, st = s.solve(b, x, tol=1e-8)
+    assert st == gs.GS_OK and rr <= 1e-8
