@@ -233,10 +233,12 @@ gs_status gs_lift_rhs(gs_ctx* ctx, const double* f, const double* g, double* rhs
  * coarse levels take v° by injection (coarse node I = fine node 2 I) and the dense coarse solve
  * factors A_c,0 (Gauss-Jordan; its symmetric part is positive definite).
  * vcirc: host, d N_v doubles of the finest level (component-blocked, like a velocity vector);
+ * With the saddle-point multigrid (precond_kind = 1) every level's velocity block is A_c and the
+ * Schur solve of the block smoother is ChebBiCGStab(1, 1) (one BiCGStab step preconditioned by
+ * diag(B diag(A_c)^-1 B^T)^-1, shadow residual = the right-hand side) in place of ChebMINRES.
  * NULL switches back to the predictor stage (rho ignored).  rho >= 0.  2D meshes, contexts created
- * with gs_options.corrector = 1 and the block-triangular preconditioner; synchronises the context
- * stream (setup work: diagonals, Lanczos, coarse factorisation).  Not while the context is in a
- * batching engine. */
+ * with gs_options.corrector = 1, no deflation; synchronises the context stream (setup work:
+ * diagonals, Lanczos, coarse factorisations).  Not while the context is in a batching engine. */
 gs_status gs_set_corrector(gs_ctx* ctx, const double* vcirc, double rho);
 
 /* Solve `count` independent systems; ctxs[i] with rhs[i] -> x[i] (device pointers).

@@ -100,6 +100,7 @@ struct Level {
   // mr, residual mres), the first Ahat solve mwt, Schur work vectors mz / mq, the inverse Schur
   // diagonal dsinv and the pressure constraint mask mpm (all zero without obstacle cells)
   void *ms = nullptr, *mr = nullptr, *mres = nullptr, *mwt = nullptr, *mz = nullptr, *mq = nullptr;
+  void *my1 = nullptr, *mz2 = nullptr;  // corrector stage: the second BiCGStab direction (y1, z2)
   void* dsinv = nullptr;
   uint8_t* mpm = nullptr;
 };
@@ -162,7 +163,7 @@ struct gs_ctx {
   std::vector<int> hmfree;
   double* MAinv = nullptr;
   int* mcfree = nullptr;
-  double *mctmp = nullptr, *msc = nullptr;
+  double *mctmp = nullptr, *msc = nullptr, *msc2 = nullptr;
   void *mb = nullptr, *mx = nullptr;
   // Krylov (FP64)
   double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *t1 = nullptr, *t2 = nullptr;
@@ -465,8 +466,8 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c, const doub
   c->mono = c->opt.precond_kind == 1;
   c->hmfree.clear();
   if (c->mono && c->opt.deflate == 1) return fail(GS_EINVAL, "deflation applies to the block-triangular preconditioner");
-  if (c->opt.corrector && (dim != 2 || c->mono || c->opt.deflate == 1))
-    return fail(GS_EINVAL, "the corrector stage is built for 2D meshes with the block-triangular preconditioner");
+  if (c->opt.corrector && (dim != 2 || c->opt.deflate == 1))
+    return fail(GS_EINVAL, "the corrector stage is built for 2D meshes without deflation");
   if (c->mono && c->opt.coarse_mode != 1) {
     c->hmfree = c->hfree;
     for (long long q = 0; q < C0.Np; ++q)
@@ -691,11 +692,16 @@ void layout(gs_ctx* c, Arena& ar) {
       lv.mq = takeT(lv.Np);
       lv.dsinv = takeT(lv.Np);
       lv.mpm = ar.take<uint8_t>(lv.Np);
+      if (c->opt.corrector) {
+        lv.my1 = takeT(lv.nu);
+        lv.mz2 = takeT(lv.Np);
+      }
     }
     c->MAinv = ar.take<double>((long long)c->nmf * c->nmf);
     c->mcfree = ar.take<int>(c->nmf);
     c->mctmp = ar.take<double>(c->nmf);
     c->msc = ar.take<double>(2);
+    c->msc2 = ar.take<double>(2);
     if (c->opt.mono_cycles > 1) {
       c->mb = takeT(F.nu + F.Np);
       c->mx = takeT(F.nu + F.Np);
@@ -1566,6 +1572,34 @@ gs_status mono_smooth_step(gs_ctx* c, int l, bool zero) {
     KL(K_MONO, launch_tile<T>(c->dim, TILE_APPLY, OPS_BT, a, c->st));
   }
   CKS(cheb<T>(c, l, (const T*)lv.b, true));  // y = Ahat^{-1} B^T z in lv.xA
+  if (lv.conv) {  // corrector stage: ChebBiCGStab(1, 1) on the negated right-hand side q
+    T* y1 = (T*)lv.my1;
+    T* v = (T*)lv.mres + lv.nu;  // v, then s (the residual is consumed)
+    T* z2 = (T*)lv.mz2;
+    KL(K_MONO, launch_cast<T, T>((const T*)lv.xA, y1, lv.nu, (T)1, c->st));  // y1 = Ahat^{-1} B^T z1
+    {  // v = S z1 = B y1
+      TileArgs<T> a = tile_args<T>(lv);
+      a.xu = y1; a.yp = v;
+      KL(K_MONO, launch_tile<T>(c->dim, TILE_APPLY, OPS_B, a, c->st));
+    }
+    KL(K_MONO, launch_dot2<T>(q, q, q, v, lv.Np, c->part, c->G, c->msc, c->st));  // q . q, q . v
+    KL(K_MONO, launch_bicg_s<T>(q, v, (const T*)lv.dsinv, z2, c->msc, lv.Np, c->st));  // s, z2 = P s
+    {  // lv.b = B^T z2
+      TileArgs<T> a = tile_args<T>(lv);
+      a.xp = z2; a.yu = (T*)lv.b;
+      KL(K_MONO, launch_tile<T>(c->dim, TILE_APPLY, OPS_BT, a, c->st));
+    }
+    CKS(cheb<T>(c, l, (const T*)lv.b, true));  // y2 = Ahat^{-1} B^T z2 in lv.xA
+    {  // t = S z2 = B y2 (into q)
+      TileArgs<T> a = tile_args<T>(lv);
+      a.xu = (const T*)lv.xA; a.yp = q;
+      KL(K_MONO, launch_tile<T>(c->dim, TILE_APPLY, OPS_B, a, c->st));
+    }
+    KL(K_MONO, launch_dot2<T>(q, (const T*)v, q, q, lv.Np, c->part, c->G, c->msc2, c->st));  // t . s, t . t
+    KL(K_MONO, launch_mono_update2<T>(x, x + lv.nu, wt, y1, (const T*)lv.xA, z, z2, c->msc, c->msc2, lv.nu, lv.Np,
+                                      zero ? 1 : 0, c->st));
+    return GS_OK;
+  }
   {  // q = B y = S z
     TileArgs<T> a = tile_args<T>(lv);
     a.xu = (const T*)lv.xA; a.yp = q;
@@ -2803,6 +2837,11 @@ gs_status corrector_setup_T(gs_ctx* c) {
     }
   }
   for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) CKS(lanczos<T>(c, l));
+  if (c->mono)  // diag(B diag(A_c)^{-1} B^T) of the saddle-point smoother
+    for (int l = (c->opt.coarse_mode == 1 ? 0 : 1); l < c->L; ++l) {
+      Level& lv = c->lv[l];
+      CK(launch_schur_diag<T>(lv.g, lv.c64, (const T*)lv.dinv, (T*)lv.dsinv, 1, c->st));
+    }
   return GS_OK;
 }
 }  // namespace
@@ -2856,6 +2895,15 @@ gs_status gs_set_corrector(gs_ctx* c, const double* vcirc, double rho) {
     for (int k = 0; k < c->nf; ++k) {
       CK(launch_gj_save(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
       CK(launch_gj_update(c->Ainv, c->nf, k, c->gjrow, c->gjcol, c->st));
+    }
+  }
+  if (c->mono && c->nmf > 0) {  // dense coarse saddle matrix with the corrector block
+    std::vector<double> M;
+    assemble_coarse_saddle(c, M);
+    CK(cudaMemcpyAsync(c->MAinv, M.data(), sizeof(double) * M.size(), cudaMemcpyHostToDevice, c->st));
+    for (int k = 0; k < c->nmf; ++k) {
+      CK(launch_gj_save(c->MAinv, c->nmf, k, c->gjrow, c->gjcol, c->st));
+      CK(launch_gj_update(c->MAinv, c->nmf, k, c->gjrow, c->gjcol, c->st));
     }
   }
   CK(cudaStreamSynchronize(c->st));

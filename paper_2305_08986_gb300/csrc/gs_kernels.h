@@ -273,6 +273,17 @@ cudaError_t launch_schur_dots(const T* z, const T* q, const T* dsinv, long long 
 template <typename T>
 cudaError_t launch_mono_update(T* xu, T* xp, const T* wt, const T* y, const T* z, const double* s, long long nu,
                                long long np, int zero, cudaStream_t st);
+// ChebBiCGStab(1, 1) pieces (corrector stage): out[0] = a . b, out[1] = c . d; s = q - alpha v (in
+// v) and z2 = dsinv s with alpha = s1[0] / s1[1]; the smoother update with alpha and omega = s2[0] / s2[1]
+template <typename T>
+cudaError_t launch_dot2(const T* a, const T* b, const T* c, const T* d, long long n, double* part, int G,
+                        double* out, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bicg_s(const T* q, T* v, const T* dsinv, T* z2, const double* s1, long long n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mono_update2(T* xu, T* xp, const T* wt, const T* y1, const T* y2, const T* z1, const T* z2,
+                                const double* s1, const double* s2, long long nu, long long np, int zero,
+                                cudaStream_t st);
 template <typename T>
 cudaError_t launch_mul(const T* a, const T* b, T* out, long long n, cudaStream_t st);  // out = a * b
 template <typename T>

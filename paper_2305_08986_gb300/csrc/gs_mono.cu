@@ -200,6 +200,110 @@ cudaError_t launch_add(const T* x, T* y, long long n, cudaStream_t st) {
   return submit<AddK<T>>({x, y, n}, nblk(n), 0, st);
 }
 
+// ---- ChebBiCGStab(1, 1): one preconditioned BiCGStab step for S w = q from zero (van der Vorst;
+// shadow residual = q, preconditioner P = D_S^{-1}), the Schur solve of the saddle-point smoother
+// when the velocity block is not symmetric (corrector stage):
+//   z1 = P q, v = S z1, alpha = (q . q) / (q . v), s = q - alpha v, z2 = P s, t = S z2,
+//   omega = (t . s) / (t . t), w = alpha z1 + omega z2;
+// alpha = 0 and omega = 0 when q . v = 0 (the iteration stops at w = 0), omega = 0 when t = 0.
+
+// part[blk] = sum a . b, part[nblk + blk] = sum c . d over the block's entries (FP64 sums)
+template <typename T>
+struct Dot2K {
+  struct Args { const T* a; const T* b; const T* c; const T* d; long long n; double* part; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ double sh[TPB / 32];
+    double s0 = 0.0, s1 = 0.0;
+    GS_FOR(i, a.n) {
+      s0 += (double)a.a[i] * (double)a.b[i];
+      s1 += (double)a.c[i] * (double)a.d[i];
+    }
+    s0 = block_sum(s0, sh);
+    s1 = block_sum(s1, sh);
+    if (threadIdx.x == 0) {
+      a.part[blk] = s0;
+      a.part[nblk + blk] = s1;
+    }
+  }
+};
+
+// s = q - alpha v (in place of v), z2 = P s, with alpha = s1[0] / s1[1] (0 when s1[1] = 0)
+template <typename T>
+struct BicgSK {
+  struct Args { const T* q; T* v; const T* dsinv; T* z2; const double* s1; long long n; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ double sal;
+    if (threadIdx.x == 0) sal = a.s1[1] != 0.0 ? a.s1[0] / a.s1[1] : 0.0;
+    __syncthreads();
+    const T al = (T)sal;
+    GS_FOR(i, a.n) {
+      const T sv = a.q[i] - al * a.v[i];
+      a.v[i] = sv;
+      a.z2[i] = a.dsinv[i] * sv;
+    }
+  }
+};
+
+// x_u (+)= wt + alpha y1 + omega y2,  x_p (+)= -(alpha z1 + omega z2)   (the step works on the
+// negated right-hand side q = r_p - B wt; zero: the iterate starts from zero)
+template <typename T>
+struct MonoUpdate2K {
+  struct Args {
+    T* xu; T* xp; const T* wt; const T* y1; const T* y2; const T* z1; const T* z2; const double* s1;
+    const double* s2; long long nu, np; int zero;
+  };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ double sal, som;
+    if (threadIdx.x == 0) {
+      const bool ok = a.s1[1] != 0.0;
+      sal = ok ? a.s1[0] / a.s1[1] : 0.0;
+      som = (ok && a.s2[1] > 0.0) ? a.s2[0] / a.s2[1] : 0.0;
+    }
+    __syncthreads();
+    const T al = (T)sal, om = (T)som;
+    GS_FOR(i, a.nu + a.np) {
+      if (i < a.nu) {
+        const T v = a.wt[i] + al * a.y1[i] + om * a.y2[i];
+        a.xu[i] = a.zero ? v : a.xu[i] + v;
+      } else {
+        const long long k = i - a.nu;
+        const T v = -(al * a.z1[k] + om * a.z2[k]);
+        a.xp[k] = a.zero ? v : a.xp[k] + v;
+      }
+    }
+  }
+};
+
+template <typename T>
+cudaError_t launch_dot2(const T* a, const T* b, const T* c, const T* d, long long n, double* part, int G,
+                        double* out, cudaStream_t st) {
+  cudaError_t e = submit<Dot2K<T>>({a, b, c, d, n, part}, G, 0, st);
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(part, 2, G, out, st);
+}
+template <typename T>
+cudaError_t launch_bicg_s(const T* q, T* v, const T* dsinv, T* z2, const double* s1, long long n, cudaStream_t st) {
+  return submit<BicgSK<T>>({q, v, dsinv, z2, s1, n}, nblk(n), 0, st);
+}
+template <typename T>
+cudaError_t launch_mono_update2(T* xu, T* xp, const T* wt, const T* y1, const T* y2, const T* z1, const T* z2,
+                                const double* s1, const double* s2, long long nu, long long np, int zero,
+                                cudaStream_t st) {
+  return submit<MonoUpdate2K<T>>({xu, xp, wt, y1, y2, z1, z2, s1, s2, nu, np, zero}, nblk(nu + np), 0, st);
+}
+#define INSTB(T)                                                                                                   \
+  template cudaError_t launch_dot2<T>(const T*, const T*, const T*, const T*, long long, double*, int, double*,    \
+                                      cudaStream_t);                                                               \
+  template cudaError_t launch_bicg_s<T>(const T*, T*, const T*, T*, const double*, long long, cudaStream_t);       \
+  template cudaError_t launch_mono_update2<T>(T*, T*, const T*, const T*, const T*, const T*, const T*,            \
+                                              const double*, const double*, long long, long long, int, cudaStream_t);
+INSTB(float)
+INSTB(double)
+#undef INSTB
+
 #define INSTM(T)                                                                                                  \
   template cudaError_t launch_schur_diag<T>(const Geom&, const OpCoef<double>&, const T*, T*, int, cudaStream_t); \
   template cudaError_t launch_schur_dots<T>(const T*, const T*, const T*, long long, double*, int, double*,       \
