@@ -439,7 +439,7 @@ def run_gpu(args, rank, world):
         ach = fl / (ms / nl * 1e-3) / 1e12
         saddle = {"bound": "alu", "achieved": ach, "peak": args.fp64_peak_tflops, "unit": "TFLOP/s",
                   "frac": ach / args.fp64_peak_tflops, "launches": nl, "avg_launch_us": 1e3 * ms / nl,
-                  "peak_source": "FP64 FMA microbenchmark on a GB300 of this pool (profiles/alu_peaks_gb300.md)"}
+                  "peak_source": "nominal FP64 peak: 2 DFMA per SM per clock x 152 SMs x 2.07 GHz (ncu peak_sustained)"}
 
     # the line's roofline is the class with the most device time in the profiled solve
     dominant = roof
@@ -1033,7 +1033,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--restart", type=int, default=50)
-    ap.add_argument("--fp64-peak-tflops", type=float, default=1.01)
+    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25,
+                    help="FP64 peak of ALU-bound rooflines: 2 DFMA per SM per clock (ncu peak_sustained) x 152 SMs x 2 "
+                         "flops x 2.07 GHz = 1.26 TFLOP/s, the nominal 1.25 TFLOP/s")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-mono", action="store_true", help="skip the Sec. 4 saddle-point multigrid comparison")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
