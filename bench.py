@@ -259,7 +259,7 @@ def run_reference(args, rank, world):
 # fused Chebyshev step at the 1280 x 224 workload (the strip kernel the autotuner picks there), from
 # one ncu --set full capture of the kernel as built now (profiles/strip2d_cheb_fp32_channel1280x224.md).
 # The writes (d, x') stay in L2 within the capture, so the figure is the read traffic.
-NCU_TRAFFIC_BYTES = {"cheb_step": 38.566912e6 + 9.728e3, "saddle_fp64": None}
+NCU_TRAFFIC_BYTES = {"cheb_step": 38.566912e6 + 9.728e3, "saddle_fp64": 24.761088e6 + 512.0}
 
 
 def tile_step_bytes(n_u: int, n_cells: int, elem: int, kind: str) -> int:
@@ -421,7 +421,7 @@ def run_gpu(args, rank, world):
     roof = None
     if cheb_roof is not None:
         tr = NCU_TRAFFIC_BYTES.get("cheb_step")
-        roof = {"bound": "hbm", "kernel": "cheb_step (fused Chebyshev step, FP32 tile kernel, all MG levels)",
+        roof = {"bound": "hbm", "kernel": "cheb_step (fused Chebyshev step, FP32, all MG levels: strip kernel where a level has a 0 tile height, cell tiles elsewhere)",
                 "achieved": cheb_roof["achieved"], "peak": peak_gbs, "unit": "GB/s", "frac": cheb_roof["frac"],
                 "traffic": tr, "traffic_over_algorithmic": (tr / tile_step_bytes(n_u, n_cells, 4, "cheb_step")
                                                             if tr else None),
@@ -441,11 +441,26 @@ def run_gpu(args, rank, world):
                   "frac": ach / args.fp64_peak_tflops, "launches": nl, "avg_launch_us": 1e3 * ms / nl,
                   "peak_source": "nominal FP64 peak: 2 DFMA per SM per clock x 152 SMs x 2.07 GHz (ncu peak_sustained)"}
 
-    # the line's roofline is the class with the most device time in the profiled solve
+    # the line's roofline is the kernel with the most device time in the profiled solve: the FP64
+    # saddle operator, or the Chebyshev step on the levels of one kernel variant (strip kernel where
+    # tile_rows reports 0, cell tiles elsewhere)
+    rows_l = [solver.info().tile_rows[l] for l in range(p.levels)]
+    cheb_by_kernel = {}
+    for l in range(p.levels):
+        st_ = per_level.get(l, {}).get("cheb_step")
+        if st_ and st_[0]:
+            key = "strip" if rows_l[l] == 0 else "tile"
+            cheb_by_kernel[key] = cheb_by_kernel.get(key, 0.0) + st_[1]
     dominant = roof
-    if saddle is not None and (roof is None or prof["saddle_fp64"][1] > cheb_roof["ms"]):
-        dominant = dict(saddle, kernel="saddle_fp64 (FP64 saddle operator of the FGMRES matvec)",
-                        traffic=NCU_TRAFFIC_BYTES.get("saddle_fp64"))
+    cheb_max = max(cheb_by_kernel.values()) if cheb_by_kernel else 0.0
+    if saddle is not None and (roof is None or prof["saddle_fp64"][1] > cheb_max):
+        fl = n_cells * (534 + 2 * 75)
+        tr = NCU_TRAFFIC_BYTES.get("saddle_fp64")
+        dominant = dict(saddle, kernel="saddle_fp64 (FP64 saddle operator of the FGMRES matvec, 32 x 8 cell tiles)",
+                        traffic=tr, traffic_over_algorithmic=tr / (8 * 2 * N + 8 * n_cells) if tr else None,
+                        flops_per_launch=fl, cheb_step_ms_by_kernel=cheb_by_kernel,
+                        how="algorithmic flops (684 per cell: the sum-factorised A, B and B^T) / average device "
+                            "time per launch in the profiled solve; the FP64 pipe is the binding unit")
 
     krylov_table = None
     try:  # secondary figures: never let them break the bench line
