@@ -638,11 +638,11 @@ def run_batched(args):
     gsbuild.build(verbose=False)
     from paper_2305_08986_gb300 import gs, inputs
     dev = torch.device("cuda", 0)
-    probs = inputs.batch_instances(args.instances, seed=0)
+    probs = inputs.batch_instances(args.instances, seed=0, align_coarse=not args.unaligned)
     t0 = time.perf_counter()
     solvers, rhs, xs = [], [], []
     for p in probs:
-        s = gs.Solver.from_problem(p, device=dev)
+        s = gs.Solver.from_problem(p, device=dev, deflate=args.deflate, max_iter=args.max_iter)
         f = torch.tensor(p.f, device=dev)
         g = torch.tensor(p.g, device=dev)
         b = torch.empty_like(f)
@@ -672,7 +672,7 @@ def run_batched(args):
     def sequential_run():
         its = []
         for s, b, x in zip(solvers, rhs, xs):
-            it, rr, _ = s.solve(b, x, tol=TOL)
+            it, rr, _ = s.solve(b, x, tol=TOL, allow_noconv=True)
             its.append(it)
         return its
 
@@ -698,14 +698,18 @@ def run_batched(args):
     stats = eng.stats()
     eng.close()
     n2 = sum(1 for p in probs if p.dim == 2)
+    boxes = "unaligned box inclusion (as drawn)" if args.unaligned else "box inclusion aligned with the coarsest mesh"
     line = {"workload": f"batched: {len(probs)} instances ({n2} 2D in 16^2..256^2, {len(probs) - n2} 3D in 8^3..32^3), "
-                        "box inclusion contrast U(1e2,1e6), alpha U(1,1e3), FP32 MG / FP64 FGMRES(50), rel-res 1e-8",
+                        f"{boxes}, contrast U(1e2,1e6), alpha U(1,1e3), FP32 MG / FP64 FGMRES(50), rel-res 1e-8"
+                        + (", rigid-body deflation of the inclusion" if args.deflate else "")
+                        + f", at most {args.max_iter} iterations",
             "metric": "solve throughput", "unit": "GDoF/s", "unknowns": unknowns,
             "value": unknowns / (statistics.median(eng_ms) * 1e-3) / 1e9,
             "engine_ms": {"p50": statistics.median(eng_ms), "max": max(eng_ms)},
             "sequential_ms": statistics.median(seq_ms),
             "speedup_vs_sequential": statistics.median(seq_ms) / statistics.median(eng_ms),
             "iterations": {"mean": statistics.fmean(its), "max": max(its)},
+            "not_converged_count": len(failed),
             "not_converged": [{"i": i, "dim": probs[i].dim, "n": probs[i].n[0], "levels": probs[i].levels,
                                "alpha": probs[i].alpha, "its": its[i], "rel": rels[i]} for i in failed],
             "solution_rel_diff_engine_vs_sequential": diff,
@@ -717,6 +721,7 @@ def run_batched(args):
 # serving: Poisson arrivals through the continuous-batching server vs sequential plain FP64
 # --------------------------------------------------------------------------------------------
 def run_serving(args):
+    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     import numpy as np
     import torch
     from paper_2305_08986_gb300 import build as gsbuild
@@ -724,48 +729,64 @@ def run_serving(args):
     from paper_2305_08986_gb300 import gs, inputs, serving
     dev = torch.device("cuda", 0)
     rates = [float(r) for r in args.rates.split(",")]
-    base = inputs.serving_stream(1.0, args.requests, seed=1)
-    problems = [p for _, p in base]
-    # sequential plain FP64 baseline: service time of each request alone (setup + solve + copy back)
+    specs = inputs.serving_specs(args.requests, seed=1)
+    fps = [serving.request_footprint(sp) for sp in specs]
+    # sequential plain FP64 baseline: service time of each of the first requests alone (problem arrays,
+    # setup, FP64-multigrid solve, copy back), then the same arrivals through one FIFO server
+    nb = min(args.baseline_requests, len(specs))
     svc = []
-    for i, p in enumerate(problems):
+    for sp in specs[:nb]:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        p = sp.build()
         s = gs.Solver.from_problem(p, device=dev, mg_precision=64)
         f = torch.tensor(p.f, device=dev)
         g = torch.tensor(p.g, device=dev)
         b = torch.empty_like(f)
         s.lift_rhs(f, g, b)
         x = torch.zeros_like(b)
-        s.solve(b, x, tol=TOL)
+        s.solve(b, x, tol=TOL, allow_noconv=True)
         x.cpu()
         s.close()
+        del s, f, g, b, x
         svc.append(time.perf_counter() - t0)
-    out = {"workload": f"serving: {args.requests} requests per rate, 3D 8^3..48^3 and 2D 32^2..512^2 log-uniform, "
-                       "random-inclusion contrast up to 1e6, rel-res 1e-8, HBM cap "
-                       f"{args.hbm_cap_gb:g} GB, continuous batching (FP32 MG / FP64 FGMRES)",
-           "unknowns_total": int(sum(len(p.f) for p in problems)), "rates": {}}
+    out = {"workload": f"serving: up to {args.requests} requests or {args.rate_seconds:g} s of arrivals per rate, "
+                       "2D 32^2..1536^2 and 3D 8^3..96^3 log-uniform, box inclusion contrast log-uniform in [1, 1e6], "
+                       f"rel-res 1e-8, HBM admission cap {args.hbm_cap_gb:g} GB, continuous batching "
+                       "(FP32 MG / FP64 FGMRES)",
+           "footprint_gb": {"mean": statistics.fmean(fps) / 1e9, "max": max(fps) / 1e9,
+                            "p50": statistics.median(fps) / 1e9},
+           "baseline": f"sequential plain FP64 (FP64 multigrid): each of the first {nb} requests run alone "
+                       "(arrays + setup + solve + copy back), then replayed through one FIFO server with the "
+                       "same arrival times",
+           "rates": {}}
     for rate in rates:
+        count = int(min(len(specs), max(1, math.ceil(rate * args.rate_seconds))))
         rng = np.random.default_rng(int(rate * 1000) + 7)
-        offs = np.cumsum(rng.exponential(1.0 / rate, size=len(problems)))
-        stream = [(float(o), serving.Request(i, p, tol=TOL)) for i, (o, p) in enumerate(zip(offs, problems))]
-        srv = serving.StokesServer(hbm_cap_bytes=args.hbm_cap_gb * 1e9, max_slots=256, setup_workers=4)
-        t0 = serving.run_stream(srv, stream)
+        offs = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        stream = [(float(o), serving.Request(i, sp, tol=TOL)) for i, (o, sp) in enumerate(zip(offs, specs[:count]))]
+        srv = serving.StokesServer(hbm_cap_bytes=args.hbm_cap_gb * 1e9, max_slots=256, setup_workers=8)
+        t0 = serving.run_stream(srv, stream, timeout_s=1200.0)
         summ = serving.summarize(srv.results, t0)
+        summ["arrival_span_s"] = float(offs[-1])
         summ["peak_running"] = srv.peak_running
         summ["peak_admitted_gb"] = srv.peak_used / 1e9
+        summ["cap_bound"] = srv.cap_waits > 0
+        summ["admissions_held_by_cap"] = srv.cap_waits
         summ["engine_steps"] = srv.engine.stats()["steps"]
         srv.close()
-        # same arrivals through one FIFO server with the measured FP64 service times
+        del srv
+        torch.cuda.empty_cache()
+        k = min(nb, count)
         tfree, lat = 0.0, []
-        for o, d in zip(offs, svc):
+        for o, d in zip(offs[:k], svc[:k]):
             start = max(o, tfree)
             tfree = start + d
             lat.append(tfree - o)
         lat.sort()
         q = lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))]
-        summ["sequential_fp64"] = {"p50_ms": 1e3 * q(0.5), "p99_ms": 1e3 * q(0.99),
-                                   "solves_per_s": len(lat) / (tfree - offs[0] + svc[0])}
+        summ["sequential_fp64"] = {"requests": k, "p50_ms": 1e3 * q(0.5), "p99_ms": 1e3 * q(0.99),
+                                   "solves_per_s": k / (tfree - offs[0] + svc[0])}
         out["rates"][f"{rate:g}"] = summ
         print(json.dumps({"rate": rate, **summ}), file=sys.stderr, flush=True)
     print(json.dumps(out), flush=True)
@@ -1068,7 +1089,13 @@ def main():
                     help="channel: the contract line; batched / serving: the engine workloads; spheres: the 3D "
                          "64^3 inclusion workload (extra lines)")
     ap.add_argument("--instances", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--unaligned", action="store_true", help="--workload batched: boxes as drawn, not snapped")
+    ap.add_argument("--deflate", type=int, default=0, choices=[0, 1], help="--workload batched: deflation option")
+    ap.add_argument("--max-iter", type=int, default=1000, help="--workload batched: FGMRES iteration limit")
+    ap.add_argument("--requests", type=int, default=2000, help="--workload serving: requests per rate at most")
+    ap.add_argument("--rate-seconds", type=float, default=60.0, help="--workload serving: arrival span per rate")
+    ap.add_argument("--baseline-requests", type=int, default=100,
+                    help="--workload serving: requests timed alone for the sequential FP64 baseline")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--hbm-cap-gb", type=float, default=150.0)
     args = ap.parse_args()

@@ -319,10 +319,12 @@ def config_random_field(dim: int, n: Sequence[int], levels: int = 1, seed: int =
                    float(alpha), all_faces(dim) if faces is None else faces, void, f, g)
 
 
-def batch_instances(count: int = 256, seed: int = 0, max2d: int = 256, max3d: int = 32) -> List[Problem]:
+def batch_instances(count: int = 256, seed: int = 0, max2d: int = 256, max3d: int = 32,
+                    align_coarse: bool = True) -> List[Problem]:
     """Batched workload: sizes drawn from 2D {16..256}^2 and 3D {8..32}^3 (coarsest level at most
-    7 cells (2D) or 4 cells (3D) per axis), contrast U(1e2, 1e6) in a random box aligned with the
-    coarsest mesh, alpha U(1, 1e3)."""
+    7 cells (2D) or 4 cells (3D) per axis), contrast U(1e2, 1e6) in a random box, alpha U(1, 1e3).
+    align_coarse: snap each box to the coarsest mesh (default); False keeps the box as drawn.  The
+    random draws do not depend on align_coarse, so both forms hold the same instances."""
     sizes2 = [s for s in (16, 24, 32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 192, 224, 256) if s <= max2d]
     sizes3 = [s for s in (8, 12, 16, 24, 32) if s <= max3d]
     rng = np.random.default_rng(seed)
@@ -333,7 +335,7 @@ def batch_instances(count: int = 256, seed: int = 0, max2d: int = 256, max3d: in
         contrast = float(rng.uniform(1e2, 1e6))
         alpha = float(rng.uniform(1.0, 1e3))
         out.append(config_box_inclusion(dim, (s,) * dim, levels_for(s, dim), contrast, alpha,
-                                        seed=int(rng.integers(1 << 31)), align_coarse=True))
+                                        seed=int(rng.integers(1 << 31)), align_coarse=align_coarse))
     return out
 
 
@@ -366,6 +368,55 @@ def serving_stream(rate: float, count: int, seed: int = 0, n2=(32, 512), n3=(8, 
                                  seed=int(rng.integers(1 << 31)), align_coarse=True)
         reqs.append((t, p))
     return reqs
+
+
+@dataclasses.dataclass
+class ProblemSpec:
+    """A box-inclusion instance described by its draws alone (no arrays): the serving workload
+    holds thousands of these and builds each one's arrays only when its setup starts."""
+
+    dim: int
+    n: tuple
+    levels: int
+    contrast: float
+    alpha: float
+    seed: int
+    length: tuple = ()
+    dirichlet_faces: int = -1
+    void: None = None
+
+    def __post_init__(self):
+        if not self.length:
+            self.length = (1.0,) * self.dim
+        if self.dirichlet_faces < 0:
+            self.dirichlet_faces = all_faces(self.dim)
+
+    @property
+    def n_total(self) -> int:
+        return self.dim * int(np.prod([2 * k + 1 for k in self.n])) + int(np.prod([k + 1 for k in self.n]))
+
+    def build(self) -> Problem:
+        return config_box_inclusion(self.dim, self.n, self.levels, self.contrast, self.alpha, seed=self.seed,
+                                    length=self.length, faces=self.dirichlet_faces, align_coarse=True)
+
+
+def serving_specs(count: int, seed: int = 0, n2=(32, 1536), n3=(8, 96)) -> List[ProblemSpec]:
+    """Request mix of the serving workload: dimension 2 or 3 with probability 1/2, size
+    log-uniform in n2 (2D) or n3 (3D) rounded to c * 2^k with a small coarse c, box inclusion
+    aligned with the coarsest mesh with contrast log-uniform in [1, 1e6], alpha U(1, 1e3).  The
+    default ranges put the mean device footprint near 2.5 GB (largest ~20 GB), so that at high
+    request rates a 150 GB admission cap binds."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        dim = 2 if rng.uniform() < 0.5 else 3
+        lo, hi = n2 if dim == 2 else n3
+        s = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        s = _round_pow2_mult(s, 7 if dim == 2 else 4)
+        contrast = float(math.exp(rng.uniform(0.0, math.log(1e6))))
+        alpha = float(rng.uniform(1.0, 1e3))
+        out.append(ProblemSpec(dim, (s,) * dim, levels_for(s, dim), contrast, alpha, int(rng.integers(1 << 31))))
+    return out
 
 
 def _round_pow2_mult(s: int, cmax: int) -> int:

@@ -28,7 +28,9 @@ from . import gs
 @dataclass
 class Request:
     rid: int
-    problem: Any            # inputs.Problem (dim, n, length, levels, eta, alpha, dirichlet_faces, void, f, g)
+    problem: Any            # inputs.Problem (dim, n, length, levels, eta, alpha, dirichlet_faces, void, f, g),
+                            # or a description with the same mesh fields and a build() that returns one
+                            # (its arrays are then made on the setup thread)
     t_arrival: float = 0.0  # seconds on the server clock (time.perf_counter())
     tol: float = 1e-8
     opts: Dict[str, int] = field(default_factory=dict)
@@ -56,8 +58,7 @@ def request_footprint(p, opts=None) -> int:
     Dirichlet data, right-hand side and solution vectors."""
     opts = opts or {}
     ws = gs.footprint_bytes(p.dim, p.n, p.length, p.levels, p.void, p.dirichlet_faces, **opts)
-    n_total = len(p.f)
-    return int(ws + 4 * 8 * n_total + 4096)
+    return int(ws + 4 * 8 * p.n_total + 4096)
 
 
 class StokesServer:
@@ -78,6 +79,8 @@ class StokesServer:
         self.running: Dict[int, tuple] = {}  # rid -> (request, footprint, t_admitted, t_ready, solver, b, x)
         self.used = 0
         self.peak_used = 0
+        self.cap_waits = 0                # requests that waited at the head of the queue for memory
+        self._held = None
         self.peak_running = 0
         self.results: List[Result] = []
 
@@ -93,7 +96,7 @@ class StokesServer:
         st = getattr(self._tls, "stream", None)
         if st is None:
             st = self._tls.stream = torch.cuda.Stream(self.device)
-        p = req.problem
+        p = req.problem.build() if hasattr(req.problem, "build") else req.problem
         with torch.cuda.device(self.device), torch.cuda.stream(st):
             s = gs.Solver.from_problem(p, stream=st, **req.opts)
             f = torch.as_tensor(p.f, dtype=torch.float64).pin_memory().to(self.device, non_blocking=True)
@@ -118,7 +121,12 @@ class StokesServer:
                 self.queue.popleft()
                 self.results.append(Result(req.rid, gs.GS_ENOMEM, 0, float("nan"), req.t_arrival, now(), now(), now()))
                 continue
-            if self.used + fp > self.cap or len(self.setups) + len(self.running) >= self.max_slots:
+            if self.used + fp > self.cap:
+                if self._held != req.rid:
+                    self._held = req.rid
+                    self.cap_waits += 1
+                break
+            if len(self.setups) + len(self.running) >= self.max_slots:
                 break
             self.queue.popleft()
             self.used += fp

@@ -52,6 +52,7 @@ def test_serving_alone_vs_in_the_mix():
     t0 = serving.run_stream(srv, stream, timeout_s=300)
     assert len(srv.results) == len(probs)
     assert srv.peak_used <= cap and srv.peak_running <= 3
+    assert srv.cap_waits > 0  # the cap, not only the slot count, held requests back
     for r in srv.results:
         xa, ita, rra = alone[r.rid]
         assert r.status == 0 and r.rel_residual <= TOL
@@ -69,4 +70,21 @@ def test_serving_rejects_requests_above_the_cap():
     srv = serving.StokesServer(hbm_cap_bytes=serving.request_footprint(p) // 2, max_slots=2)
     serving.run_stream(srv, [(0.0, serving.Request(0, p))], timeout_s=60)
     assert [r.status for r in srv.results] == [gs.GS_ENOMEM]
+    srv.close()
+
+
+def test_described_requests_build_on_the_setup_thread():
+    """A request given as a description (inputs.ProblemSpec) is built by the setup worker and
+    solves to the same bits as the same request given with its arrays."""
+    import torch
+    from paper_2305_08986_gb300 import serving
+    sp = inputs.serving_specs(3, seed=4, n2=(24, 48), n3=(8, 12))
+    srv = serving.StokesServer(hbm_cap_bytes=64e9, max_slots=4, setup_workers=2, keep_solutions=True)
+    stream = [(0.01 * i, serving.Request(i, s, tol=TOL)) for i, s in enumerate(sp)]
+    serving.run_stream(srv, stream, timeout_s=300)
+    assert sorted(r.rid for r in srv.results) == [0, 1, 2]
+    for r in srv.results:
+        xa, ita, rra = _alone(sp[r.rid].build())
+        assert r.status == 0 and (r.iterations, r.rel_residual) == (ita, rra)
+        assert torch.equal(r.x, xa)
     srv.close()
