@@ -125,6 +125,9 @@ typedef struct {            /* zero-initialised = defaults */
                                   the strip kernel (the FP64 saddle operator then uses 32 x 8 tiles);
                                   5 -> by size, the strip kernel on levels of at least 32,768 cells
                                   and 32 x 8 tiles below (no timing at gs_create).
+                               3D meshes: 0 -> time the cell tiles of 8 x 8 x 8 and 8 x 8 x 4
+                                  evaluated cells per level and keep the faster (default);
+                                  2 -> always 8 x 8 x 4; any other value -> always 8 x 8 x 8.
                                   Every variant sums a node's cell contributions in the same order,
                                   so the results do not depend on the choice. */
   int deflate;              /* 1: rigid-body deflation of stiff inclusions in the V-cycle's finest
@@ -318,8 +321,9 @@ typedef struct {
   int pressure_coarse_free;/* unknowns of the dense coarse pressure-Laplacian solve */
   double plambda_max[16];  /* Chebyshev upper bound of the pressure Laplacian per level */
   int tile_rows[16];       /* 2D: evaluated cell rows per tile chosen for each level's multigrid kernels
-                              (0: the strip kernel) */
-  int saddle_tile_rows;    /* 2D: the same for the FP64 saddle operator (0 in 3D) */
+                              (0: the strip kernel); 3D: evaluated cell layers along z per 8 x 8 x k
+                              tile (8 or 4) */
+  int saddle_tile_rows;    /* the same for the FP64 saddle operator */
   int deflation_inclusions;/* stiff inclusions in the deflation space (option deflate) */
   int deflation_modes;     /* rigid modes kept (modes vanishing on unconstrained nodes dropped) */
   int precond_kind;        /* the preconditioner in use (gs_options.precond_kind) */

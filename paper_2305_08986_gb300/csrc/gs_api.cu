@@ -1211,11 +1211,14 @@ gs_status time_launches(gs_ctx* c, F&& launch, int reps, double* us) {
   return GS_OK;
 }
 
-// Per level, time the fused Chebyshev step with each compiled tile height on the level's own
-// (scratch) vectors and keep the fastest; then the same for the FP64 saddle operator on the
-// finest level.  A height must beat the current choice by 2 % to replace it.
+// Per level, time the fused Chebyshev step with each compiled kernel variant (2D: tile heights
+// and the strip kernel; 3D: tile depths) on the level's own (scratch) vectors and keep the
+// fastest; then the same for the FP64 saddle operator on the finest level.  A variant must beat
+// the current choice by 2 % to replace it.
 template <typename T>
 gs_status autotune(gs_ctx* c) {
+  const int nshape = c->dim == 2 ? kTileShapes2D : kTileShapes3D;
+  const int nsaddle = c->dim == 2 ? kTileHeights2D : kTileShapes3D;
   for (int l = 0; l < c->L; ++l) {
     Level& lv = c->lv[l];
     CK(cudaMemsetAsync(lv.xA, 0, sizeof(T) * lv.nu, c->st));
@@ -1223,13 +1226,13 @@ gs_status autotune(gs_ctx* c) {
     CK(cudaMemsetAsync(lv.d, 0, sizeof(T) * lv.nu, c->st));
     double best_us = 0.0;
     int best = 0;
-    for (int s = 0; s < kTileShapes2D; ++s) {
+    for (int s = 0; s < nshape; ++s) {
       TileArgs<T> a = tile_args<T>(lv);
       a.shape = s;
       a.xu = (const T*)lv.xA; a.bu = (const T*)lv.b; a.d = (T*)lv.d; a.dinv = (const T*)lv.dinv;
       a.xout = (T*)lv.xB; a.c1 = (T)0.5; a.c2 = (T)1; a.use_d = 1;
       double us;
-      CKS(time_launches(c, [&]() { return launch_tile<T>(2, TILE_CHEB, OPS_A, a, c->st); }, 4, &us));
+      CKS(time_launches(c, [&]() { return launch_tile<T>(c->dim, TILE_CHEB, OPS_A, a, c->st); }, 4, &us));
       if (s == 0 || us < 0.98 * best_us) { best_us = us; best = s; }
     }
     lv.shape = best;
@@ -1237,7 +1240,7 @@ gs_status autotune(gs_ctx* c) {
   CK(cudaMemsetAsync(c->r, 0, sizeof(double) * c->N, c->st));
   double best_us = 0.0;
   int best = 0;
-  for (int s = 0; s < kTileHeights2D; ++s) {
+  for (int s = 0; s < nsaddle; ++s) {
     c->saddle_shape = s;
     double us;
     CKS(time_launches(c, [&]() -> cudaError_t {
@@ -1351,8 +1354,11 @@ gs_status setup(gs_ctx* c) {
   }
   if (c->fp32) CKS(setup_T<float>(c)); else CKS(setup_T<double>(c));
   CK(cudaStreamSynchronize(c->st));
-  if (c->dim == 2 && c->opt.tile_autotune == 0) {
+  if (c->opt.tile_autotune == 0) {
     CKS(c->fp32 ? autotune<float>(c) : autotune<double>(c));
+  } else if (c->dim == 3) {
+    for (int l = 0; l < c->L; ++l) c->lv[l].shape = c->opt.tile_autotune == 2 ? 1 : 0;
+    c->saddle_shape = c->opt.tile_autotune == 2 ? 1 : 0;
   } else if (c->dim == 2 && c->opt.tile_autotune == 5) {
     // size rule: the strip kernel where a level has enough cells to fill the GPU, 32 x 8 tiles below
     for (int l = 0; l < c->L; ++l) c->lv[l].shape = c->lv[l].Nc >= 32768 ? 3 : 2;
@@ -3010,8 +3016,9 @@ gs_status gs_get_info(const gs_ctx* c, gs_info* out) {
   out->pressure_coarse_free = c->nfp;
   for (int l = 0; l < c->L && l < 16; ++l) out->plambda_max[l] = c->lv[l].plam_hi;
   static const int rows[kTileShapes2D] = {16, 17, 8, 0};
-  for (int l = 0; l < c->L && l < 16; ++l) out->tile_rows[l] = c->dim == 2 ? rows[c->lv[l].shape] : 0;
-  out->saddle_tile_rows = c->dim == 2 ? rows[c->saddle_shape] : 0;
+  for (int l = 0; l < c->L && l < 16; ++l)
+    out->tile_rows[l] = c->dim == 2 ? rows[c->lv[l].shape] : tile3d_depth(c->lv[l].shape);
+  out->saddle_tile_rows = c->dim == 2 ? rows[c->saddle_shape] : tile3d_depth(c->saddle_shape);
   out->deflation_inclusions = c->defl_ninc;
   out->deflation_modes = c->defl_m;
   out->precond_kind = c->mono ? 1 : 0;

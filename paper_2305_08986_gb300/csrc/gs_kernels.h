@@ -41,10 +41,15 @@ struct TileArgs {
   T rho, ihx, ihy, wq;  // density, 1 / h_x, 1 / h_y, h_x h_y
   int tiles[3];
   int shape;      // 2D velocity-block variant (0 / 1 / 2: tiles of 16 / 17 / 8 rows of evaluated cells,
-                  // 3: the strip kernel of gs_strip2d.cuh; other operator blocks: 3 -> tiles of 8)
+                  // 3: the strip kernel of gs_strip2d.cuh; other operator blocks: 3 -> tiles of 8);
+                  // 3D: 0 / 1 -> tiles of 8 x 8 x 8 / 8 x 8 x 4 evaluated cells
 };
 constexpr int kTileShapes2D = 4;   // velocity-block variants the autotuner times
 constexpr int kTileHeights2D = 3;  // tile variants of the full saddle operator
+// 3D cell tiles (TileArgs::shape): 0 -> 8 x 8 x 8, 1 -> 8 x 8 x 4 evaluated cells; every variant
+// sums a node's cell contributions in the same order, so the choice does not change any result
+constexpr int kTileShapes3D = 2;
+constexpr int tile3d_depth(int shape) { return shape == 1 ? 4 : 8; }
 
 // Which blocks of the saddle operator a launch computes.
 enum TileOps { OPS_A = 1, OPS_BT = 2, OPS_B = 4 };

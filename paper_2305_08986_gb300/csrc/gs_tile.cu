@@ -2,43 +2,38 @@
 // operator (Eq. "stokes-discrete-block"), matrix-free on Cartesian Q2-Q1 hexahedra (3D; the 2D
 // path is gs_tile2d.cu).
 //
-// Work decomposition.  A CTA owns a box of TO^d cells and the velocity / pressure nodes whose
-// global index lies in [2 cs, 2 (cs + TO)) (resp. [cs, cs + TO)) per axis, plus the last node
-// of the mesh when the box touches the upper boundary.  To complete the sums at its owned
-// nodes it also evaluates the layer of cells just below the box (halo cells at local index
+// Work decomposition.  A CTA owns a box of TO_0 x TO_1 x TO_2 cells and the velocity / pressure
+// nodes whose global index lies in [2 cs, 2 (cs + TO)) (resp. [cs, cs + TO)) per axis, plus the
+// last node of the mesh when the box touches the upper boundary.  To complete the sums at its
+// owned nodes it also evaluates the layer of cells just below the box (halo cells at local index
 // -1), so no two CTAs write the same output and no atomics are needed.  Inside the CTA the
-// (TO+1)^d evaluated cells are split in 2^d parity classes; cells of one class share no node,
-// so each phase adds its cell results into the shared-memory node tile with plain
-// read-modify-writes, and the fixed phase order makes the result deterministic.  The owned
-// nodes are then written once, coalesced, with the mode's epilogue (plain apply, residual, or
-// a fused Chebyshev update).
+// evaluated cells are split in 8 classes by the parity of their global cell index along each
+// axis; cells of one class share no node, so each phase adds its cell results into the
+// shared-memory node tile with plain read-modify-writes.  The phases run in the order of the
+// global parity class, so every node sums its cells' contributions in one order that depends on
+// the node alone: tiles of any shape or position give the same bits, and the autotuner may pick
+// the tile shape per level.  The owned nodes are then written once, coalesced, with the mode's
+// epilogue (plain apply, residual, or a fused Chebyshev update).
 #include "gs_cell.cuh"
 #include "gs_kernels.h"
 
 namespace gs {
 
-template <int DIM>
-struct TileShape;
-template <>
-struct TileShape<3> {  // 8^3 evaluated cells, 7^3 owned; one thread per (2x2x2 group, component)
-  static constexpr int TC0 = 8, TC1 = 8, TC2 = 8;
-  static constexpr int G0 = 4, G1 = 4, G2 = 4;
+// Tile shapes: TC0 x TC1 x TC2 evaluated cells ((TC - 1) owned per axis), one thread per
+// (2 x 2 x 2 group, output component).  The skewed shared-memory layouts below assume TC0 = TC1 =
+// 8; TC2 may be 8 or 4 (a warp then covers the same group pattern).
+template <int C2>
+struct TileShape3 {
+  static_assert(C2 == 8 || C2 == 4, "3D tile depth");
+  static constexpr int TC0 = 8, TC1 = 8, TC2 = C2;
+  static constexpr int G0 = TC0 / 2, G1 = TC1 / 2, G2 = TC2 / 2;
   static constexpr int SPLIT = 3;
-};
-
-template <int DIM>
-struct TileDims {
-  using S = TileShape<DIM>;
-  static constexpr int NG = S::G0 * S::G1 * S::G2;
-  static constexpr int THREADS = NG * S::SPLIT;
-  static constexpr int VE0 = 2 * (S::TC0 - 1) + 1;
-  static constexpr int VE1 = 2 * (S::TC1 - 1) + 1;
-  static constexpr int VE2 = DIM == 3 ? 2 * (S::TC2 - 1) + 1 : 1;
-  static constexpr int VSZ = VE0 * VE1 * VE2;
-  static constexpr int PE0 = S::TC0, PE1 = S::TC1, PE2 = DIM == 3 ? S::TC2 : 1;
+  static constexpr int NG = G0 * G1 * G2;
+  static constexpr int THREADS = NG * SPLIT;
+  static constexpr int VE0 = 2 * (TC0 - 1) + 1, VE1 = 2 * (TC1 - 1) + 1, VE2 = 2 * (TC2 - 1) + 1;
+  static constexpr int PE0 = TC0, PE1 = TC1, PE2 = TC2;
   static constexpr int PSZ = PE0 * PE1 * PE2;
 };
-
 __device__ __forceinline__ int owned_v_ext(int cs, int TO, int n) {
   return (cs + TO >= n) ? (2 * n + 1 - 2 * cs) : 2 * TO;
 }
@@ -76,33 +71,37 @@ struct Skew3 {
   static constexpr int OA = 1, OB = F ? 0 : 3, OP = F ? 236 : 229;  // output tile (VE = 15)
 };
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int MODE, bool WA, bool WBT, bool WB, class S>
 struct Smem3 {
-  using S = TileShape<3>;
-  using D = TileDims<3>;
   using K = Skew3<T>;
   static constexpr bool NEED_U = WA || WB, WU = WA || WBT;
-  static constexpr int W = 2 * S::TC0 + 1, WV = W * W * W;  // staged velocity window
-  static constexpr int WVA = (W - 1) * (1 + W + K::WP) + (K::WA + K::WB) * ((W - 1) >> 2) + 1;  // skewed window
-  static constexpr int VSZA = (D::VE0 - 1) + (D::VE1 - 1) * D::VE0 + (D::VE2 - 1) * K::OP +
-                              K::OA * ((D::VE1 - 1) >> 2) + K::OB * ((D::VE2 - 1) >> 2) + 1;
-  static constexpr int PW = S::TC0 + 1, PWV = PW * PW * PW; // staged pressure window
+  static constexpr int W0 = 2 * S::TC0 + 1, W1 = 2 * S::TC1 + 1, W2 = 2 * S::TC2 + 1;  // staged velocity window
+  static constexpr int W = W0, WV = W0 * W1 * W2;
+  static constexpr int WVA = (W0 - 1) + (W1 - 1) * W + (W2 - 1) * K::WP + K::WA * ((W1 - 1) >> 2) +
+                             K::WB * ((W2 - 1) >> 2) + 1;  // skewed window
+  static constexpr int VSZA = (S::VE0 - 1) + (S::VE1 - 1) * S::VE0 + (S::VE2 - 1) * K::OP +
+                              K::OA * ((S::VE1 - 1) >> 2) + K::OB * ((S::VE2 - 1) >> 2) + 1;
+  static constexpr int PW0 = S::TC0 + 1, PW1 = S::TC1 + 1, PW2 = S::TC2 + 1;
+  static constexpr int PWV = PW0 * PW1 * PW2;               // staged pressure window
   static constexpr int SU = WU ? 3 * VSZA : 0;              // velocity outputs
-  static constexpr int SP = WB ? D::PSZ : 0;                // pressure outputs
+  static constexpr int SP = WB ? S::PSZ : 0;                // pressure outputs
   static constexpr int SX = NEED_U ? 3 * WVA : 0;
   static constexpr int SPW = WBT ? PWV : 0;
   static constexpr int TOTAL = SU + SP + SX + SPW;           // elements of T
   static constexpr int FLAGS = NEED_U ? WV : 0;              // bytes
+  static_assert(S::TC0 == 8 && S::TC1 == 8, "the skewed layouts assume 8 x 8 cells in x and y");
+  static_assert(K::WP >= W * W1 + K::WA * ((W1 - 1) >> 2) && K::OP >= S::VE0 * S::VE1 + K::OA * ((S::VE1 - 1) >> 2),
+                "planes of the skewed layouts must not overlap");
 };
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int MODE, bool WA, bool WBT, bool WB, class S>
 __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
-  using S = TileShape<3>;
-  using D = TileDims<3>;
-  using SM = Smem3<T, MODE, WA, WBT, WB>;
+  using D = S;
+  using SM = Smem3<T, MODE, WA, WBT, WB, S>;
   using K = Skew3<T>;
   constexpr bool NEED_U = SM::NEED_U, WU = SM::WU;
-  constexpr int W = SM::W, WW = W * W, WV = SM::WV, WVA = SM::WVA, VSZA = SM::VSZA, PW = SM::PW;
+  constexpr int W = SM::W, WW = W * SM::W1, WV = SM::WV, WVA = SM::WVA, VSZA = SM::VSZA;
+  constexpr int PW0 = SM::PW0, PW01 = SM::PW0 * SM::PW1;
   auto widx = [](int i0, int i1, int i2) { return i0 + W * i1 + K::WP * i2 + K::WA * (i1 >> 2) + K::WB * (i2 >> 2); };
   auto oidx = [](int i0, int i1, int i2) {
     return i0 + D::VE0 * i1 + K::OP * i2 + K::OA * (i1 >> 2) + K::OB * (i2 >> 2);
@@ -137,7 +136,7 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   if (NEED_U) {
     const int I0 = 2 * (cs0 - 1), J0 = 2 * (cs1 - 1), K0 = 2 * (cs2 - 1);
     for (int i = tid; i < WV; i += D::THREADS) {
-      const int a = i % W, b = (i / W) % W, k = i / WW;
+      const int a = i % W, b = (i / W) % SM::W1, k = i / WW;
       const int I = I0 + a, J = J0 + b, K = K0 + k;
       const bool inr = I >= 0 && I < g.nv[0] && J >= 0 && J < g.nv[1] && K >= 0 && K < g.nv[2];
       const long long node = inr ? I + (long long)g.nv[0] * (J + (long long)g.nv[1] * K) : 0;
@@ -151,7 +150,7 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   if (WBT) {
     const int P0 = cs0 - 1, Q0 = cs1 - 1, R0 = cs2 - 1;
     for (int i = tid; i < SM::PWV; i += D::THREADS) {
-      const int P = P0 + i % PW, Q = Q0 + (i / PW) % PW, R = R0 + i / (PW * PW);
+      const int P = P0 + i % PW0, Q = Q0 + (i / PW0) % SM::PW1, R = R0 + i / PW01;
       const bool inr = P >= 0 && P < g.npn[0] && Q >= 0 && Q < g.npn[1] && R >= 0 && R < g.npn[2];
       const long long q = inr ? P + (long long)g.npn[0] * (Q + (long long)g.npn[1] * R) : 0;
       const bool con = inr && !raw && pnode_constrained(g, q);
@@ -164,7 +163,7 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   if (NEED_U && vmasked) {
     for (int i = tid; i < WV; i += D::THREADS)
       if (sflag[i]) {
-        const int wi = widx(i % W, (i / W) % W, i / WW);
+        const int wi = widx(i % W, (i / W) % SM::W1, i / WW);
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) sx[cc * WVA + wi] = T(0);
       }
@@ -191,9 +190,13 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   auto fo = [](int ax, int i) {
     return ax == 0 ? i : (ax == 1 ? D::VE0 * i + K::OA * (i >> 2) : K::OP * i + K::OB * (i >> 2));
   };
-  auto fp = [](int ax, int i) { return ax == 0 ? i : (ax == 1 ? PW * i : PW * PW * i); };
+  auto fp = [](int ax, int i) { return ax == 0 ? i : (ax == 1 ? PW0 * i : PW01 * i); };
+  // phase pc = the global parity class (c0 & 1) + 2 (c1 & 1) + 4 (c2 & 1) of its cells; the local
+  // index of the first evaluated cell, cs - 1, fixes which local parity that is
+  const int opar = ((cs0 - 1) & 1) | (((cs1 - 1) & 1) << 1) | (((cs2 - 1) & 1) << 2);
 #pragma unroll 1
-  for (int ph = 0; ph < 8; ++ph) {
+  for (int pc = 0; pc < 8; ++pc) {
+    const int ph = pc ^ opar;
     const int lp[3] = {2 * g0 + (ph & 1), 2 * g1 + ((ph >> 1) & 1), 2 * g2 + ((ph >> 2) & 1)};
     const int c0 = cs0 - 1 + lp[0], c1 = cs1 - 1 + lp[1], c2 = cs2 - 1 + lp[2];
     bool active = c0 >= 0 && c0 < g.n[0] && c1 >= 0 && c1 < g.n[1] && c2 >= 0 && c2 < g.n[2];
@@ -323,30 +326,33 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   }
 }
 
-template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
+template <typename T, int MODE, bool WA, bool WBT, bool WB, int C2>
 struct TileK {
   using Args = TileArgs<T>;
-  static constexpr int THREADS = TileDims<DIM>::THREADS, MINB = 1;
-  static_assert(DIM == 3, "2D launches use the tiles of gs_tile2d.cuh");
+  using S = TileShape3<C2>;
+  static constexpr int THREADS = S::THREADS, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int) {
-    tile3d_body<T, MODE, WA, WBT, WB>(a, blk);
+    tile3d_body<T, MODE, WA, WBT, WB, S>(a, blk);
   }
 };
 
-template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
-static cudaError_t launch_one(TileArgs<T> a, cudaStream_t st) {
-  using S = TileShape<DIM>;
-  using D = TileDims<DIM>;
+template <typename T, int MODE, bool WA, bool WBT, bool WB, int C2>
+static cudaError_t launch_shape(TileArgs<T> a, cudaStream_t st) {
+  using S = TileShape3<C2>;
+  using SM = Smem3<T, MODE, WA, WBT, WB, S>;
   a.tiles[0] = (a.g.n[0] + S::TC0 - 2) / (S::TC0 - 1);
   a.tiles[1] = (a.g.n[1] + S::TC1 - 2) / (S::TC1 - 1);
-  a.tiles[2] = DIM == 3 ? (a.g.n[2] + S::TC2 - 2) / (S::TC2 - 1) : 1;
-  size_t smem = sizeof(T) * (((WA || WBT) ? DIM * D::VSZ : 0) + (WB ? D::PSZ : 0));
-  if (DIM == 3) {
-    using SM = Smem3<T, MODE, WA, WBT, WB>;
-    smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
-  }
+  a.tiles[2] = (a.g.n[2] + S::TC2 - 2) / (S::TC2 - 1);
+  const size_t smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
   const long long nblocks = (long long)a.tiles[0] * a.tiles[1] * a.tiles[2];
-  return submit<TileK<T, DIM, MODE, WA, WBT, WB>>(a, nblocks, smem, st);
+  return submit<TileK<T, MODE, WA, WBT, WB, C2>>(a, nblocks, smem, st);
+}
+
+template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
+static cudaError_t launch_one(TileArgs<T> a, cudaStream_t st) {
+  static_assert(DIM == 3, "2D launches use the kernels of gs_tile2d.cuh and gs_strip2d.cuh");
+  if (a.shape == 1) return launch_shape<T, MODE, WA, WBT, WB, 4>(a, st);
+  return launch_shape<T, MODE, WA, WBT, WB, 8>(a, st);
 }
 
 template <typename T, int DIM, int MODE>

@@ -290,6 +290,55 @@ def test_tile_heights_give_identical_solves(name):
         assert (it, rr) == outs[0][1:] and torch.equal(x, outs[0][0])
 
 
+TILE_DEPTH_CASES_3D = {
+    "box_3d": lambda: inputs.config_box_inclusion(3, (24, 16, 20), 3, 1e5, 20.0, seed=6, align_coarse=True),
+    "ragged_void_3d": lambda: inputs.config_random_field(3, (13, 9, 11), levels=1, seed=8, contrast=1e6, alpha=3.0,
+                                                         faces=inputs.FACE_XM | inputs.FACE_ZP, void_fraction=0.1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(TILE_DEPTH_CASES_3D))
+def test_3d_tile_depths_give_identical_results(name):
+    """The 3D cell tile of 8 x 8 x 8 or 8 x 8 x 4 evaluated cells (forced or autotuned): every node
+    sums its cells' contributions in the order of their global parity class, so A x, the saddle
+    operator and the whole solve are bitwise the same."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = TILE_DEPTH_CASES_3D[name]()
+    rng = np.random.default_rng(5)
+    outs = []
+    for mode in (1, 2, 0):
+        s = gs.Solver.from_problem(p, tile_autotune=mode, coarse_mode=1 if p.levels == 1 else 0)
+        inf = s.info()
+        depths = [inf.tile_rows[l] for l in range(p.levels)]
+        if mode:
+            assert depths == [(8, 4)[mode - 1]] * p.levels and inf.saddle_tile_rows == (8, 4)[mode - 1]
+        else:
+            assert all(dd in (8, 4) for dd in depths) and inf.saddle_tile_rows in (8, 4)
+        xk = torch.tensor(rng.standard_normal(s.n_total) if not outs else outs[0][0], device="cuda")
+        yk = torch.empty_like(xk)
+        s.vmult(xk, yk)
+        xa32 = xk[:s.n_u].float().contiguous()
+        ya32 = torch.empty_like(xa32)
+        s32 = gs.Solver.from_problem(p, tile_autotune=mode, mg_precision=32, coarse_mode=1 if p.levels == 1 else 0)
+        s32.vmult_A(xa32, ya32)
+        if p.levels > 1:
+            f = torch.tensor(p.f, device="cuda")
+            g = torch.tensor(p.g, device="cuda")
+            b = torch.empty_like(f)
+            s.lift_rhs(f, g, b)
+            x = torch.zeros_like(b)
+            it, rr, _ = s.solve(b, x, tol=1e-9)
+            sol = (x.cpu(), it, rr)
+        else:
+            sol = None
+        outs.append((xk.cpu().numpy(), yk.cpu(), ya32.cpu(), sol))
+    for _, y, y32, sol in outs[1:]:
+        assert torch.equal(y, outs[0][1]) and torch.equal(y32, outs[0][2])
+        if sol is not None:
+            assert sol[1:] == outs[0][3][1:] and torch.equal(sol[0], outs[0][3][0])
+
+
 @pytest.mark.parametrize("case", CASES[:2] + [dict(dim=2, n=(20, 6), levels=1, void=0.1, faces=inputs.FACE_YM)])
 @pytest.mark.parametrize("variant", [1, 4])
 def test_velocity_kernel_variants_bitwise(case, variant):
