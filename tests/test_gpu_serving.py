@@ -45,7 +45,7 @@ def test_serving_alone_vs_in_the_mix():
     probs = _requests()
     alone = [_alone(p) for p in probs]
     fps = [serving.request_footprint(p) for p in probs]
-    cap = 2.2 * max(fps)  # forces queueing on the footprint
+    cap = 1.2 * max(fps)  # the largest request cannot join the first three: queueing on the footprint
     srv = serving.StokesServer(hbm_cap_bytes=cap, max_slots=3, setup_workers=2, keep_solutions=True)
     # all arrive at once, then two more bursts while the first ones run
     stream = [(0.0 if i < 4 else 0.05 * (i - 3), serving.Request(i, p, tol=TOL)) for i, p in enumerate(probs)]
