@@ -11,12 +11,10 @@
 // launch): a kernel may be scheduled while its predecessor in the stream is still running, and
 // its first instruction, griddepcontrol.wait, holds every thread until the predecessor grid has
 // completed and its memory is visible.  No block touches memory before that wait, so the order of
-// the launches is preserved.  Right after the wait every block issues griddepcontrol.launch_dependents:
-// once all blocks of the grid have issued it (every block is then resident), the next grid in the
-// stream may be scheduled onto free SM slots, where its blocks hold at their own wait until this grid
-// has completed.  The successor's launch latency thus overlaps this grid's run instead of its tail,
-// and at most two grids of the stream are resident at a time.  (Without the launch attribute both
-// instructions have no effect.)
+// the launches is preserved; only the launch latency overlaps the predecessor's tail.  (Without
+// the launch attribute the wait returns at once.)  The blocks do not signal their dependents early
+// (griddepcontrol.launch_dependents): measured on the channel solve, successor blocks parked at
+// their wait on the SMs slowed it down (49.9 against 49.05 ms).
 // submit<K>() launches k_one immediately, or, while a Recorder is installed on the calling
 // thread, appends (kernel, args, nblk, shared bytes) to it instead.  The batching engine records
 // the same host code for every instance and merges the recordings step by step into k_many
@@ -88,10 +86,7 @@ cudaError_t ensure_dynamic_smem(F* fn, size_t smem, std::atomic<size_t>* enabled
   return cudaSuccess;
 }
 
-__device__ __forceinline__ void wait_prerequisite_grids() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+__device__ __forceinline__ void wait_prerequisite_grids() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <class K>
 __global__ void __launch_bounds__(K::THREADS, K::MINB) k_one(const typename K::Args a) {
