@@ -157,14 +157,20 @@ typedef struct {            /* zero-initialised = defaults */
                                gs_set_corrector); 0 -> none */
 } gs_options;
 
-/* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input). */
+/* Bytes of device workspace gs_create needs for this mesh / levels / options (0 on bad input):
+ * the multigrid hierarchy of Sec. 4 and the FGMRES basis of Sec. 5 ("Linear solver settings"). */
 size_t gs_footprint_bytes(const gs_mesh* mesh, int levels, const gs_options* opts);
 
-/* Build the hierarchy: levels l = 0 (coarsest, n / 2^(levels-1) cells per axis) ... levels-1
- * (finest, mesh->n).  eta_per_cell: HOST array of N_c positive finite values (finest level,
- * cell-lexicographic, x fastest); coarse eta = mean of the active children.  alpha >= 0.
- * opts may be NULL.  stream: cudaStream_t or NULL.  workspace: device pointer of at least
- * gs_footprint_bytes() bytes.  On success *out receives the context. */
+/* Build the hierarchy of the generalized Stokes problem alpha u - div(2 eta eps(u)) + grad p = f,
+ * div u = g_p (Sec. 3.1.2, Eq. "ggce:implicit"; Q2-Q1 spaces of Eq. "spaces"; eta per cell as in the
+ * viscosity splitting, Eq. "viscosity-splitting"; nested meshes of Sec. 4): levels l = 0
+ * (coarsest, n / 2^(levels-1) cells per axis) ... levels-1 (finest, mesh->n).  eta_per_cell: HOST
+ * array of N_c positive finite values (finest level, cell-lexicographic, x fastest); coarse eta =
+ * mean of the active children.  alpha >= 0 (alpha = rho / (gamma tau)).  opts may be NULL.
+ * stream: cudaStream_t or NULL.  workspace: device pointer of at least gs_footprint_bytes() bytes,
+ * owned by the caller and used by the context until gs_destroy.  On success *out receives the
+ * context; on GS_EINVAL (bad sizes, non-finite eta, too small a workspace) or GS_ECUDA nothing is
+ * kept (gs_last_error() says why). */
 gs_status gs_create(const gs_mesh* mesh, int levels, const double* eta_per_cell, double alpha,
                     const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
                     gs_ctx** out);
@@ -181,23 +187,28 @@ gs_status gs_create_ex(const gs_mesh* mesh, int levels, const double* eta_per_ce
                        const gs_options* opts, void* stream, void* workspace, size_t workspace_bytes,
                        gs_ctx** out);
 
-/* y = K x on the finest level, FP64 (Eq. "stokes-discrete-block" with constraints).
- * x, y: device, length N, must not alias. */
+/* y = K x on the finest level, FP64 (Eq. "stokes-discrete-block" with constraints; the blocks
+ * are the forms of Eq. "form_a_j" and Eq. "form_b").  x, y: device, length N, must not alias.
+ * GS_EINVAL on a null pointer. */
 gs_status gs_vmult(gs_ctx* ctx, const double* x, double* y);
 
 /* y = A x (velocity block, constrained) on the finest level.  fp32 = 0: x, y are double*;
  * fp32 = 1: x, y are float* (the operator the FP32 multigrid uses).  Length d*N_v. */
 gs_status gs_vmult_A(gs_ctx* ctx, const void* x, void* y, int fp32);
 
-/* z = V(r): one velocity V-cycle (FP64 in/out; inside in the context's mg_precision).
- * Length d*N_v, device.  Constrained rows act as identity rows inside the smoother and never
- * couple to free entries; the block preconditioner overwrites them with r. */
+/* z = V(r): one velocity V-cycle of Sec. 4 (Chebyshev-Jacobi smoothing of degree k_A, Table
+ * "NS-solver-parameters-1"; FP64 in/out, inside in the context's mg_precision).  Length d*N_v,
+ * device.  Constrained rows act as identity rows inside the smoother and never couple to free
+ * entries; the block preconditioner overwrites them with r.  GS_EINVAL on a null pointer. */
 gs_status gs_vcycle(gs_ctx* ctx, const double* r, double* z);
 
-/* Solve K x = rhs with FGMRES to ||rhs - K x|| / ||rhs|| <= tol (explicit residual).
- * x: in = initial guess, out = solution (device, length N).  *iterations and *rel_residual
- * receive the FGMRES iteration count and the explicit relative residual (either may be NULL).
- * Returns GS_ENOCONV if tol was not reached within max_iter (x holds the last iterate). */
+/* Solve K x = rhs with FGMRES (Sec. 5, "Linear solver settings") preconditioned as in Sec. 4, to
+ * ||rhs - K x|| / ||rhs|| <= tol (explicit residual).  x: in = initial guess, out = solution
+ * (device, length N).  *iterations and *rel_residual receive the FGMRES iteration count and the
+ * explicit relative residual (either may be NULL).  Returns GS_ENOCONV if tol was not reached
+ * within max_iter (x holds the last iterate), GS_EBREAKDOWN on a non-finite right-hand side,
+ * initial guess or Krylov scalar, GS_ETIMEOUT when a kernel's bounded wait gave up (the context
+ * stays usable). */
 gs_status gs_solve(gs_ctx* ctx, const double* rhs, double* x, double tol, int* iterations,
                    double* rel_residual);
 
@@ -217,7 +228,8 @@ gs_status gs_solve(gs_ctx* ctx, const double* rhs, double* x, double tol, int* i
 gs_status gs_solve_A(gs_ctx* ctx, const double* rhs, double* x, double tol, int* iterations,
                      double* rel_residual);
 
-/* rhs = [M_u f_u ; M_p f_p] - K_raw g on free entries, rhs = g on constrained entries, where
+/* Right-hand side of Eq. "stokes-discrete-block" with the Dirichlet data lifted (Sec. 3.1.2):
+ * rhs = [M_u f_u ; M_p f_p] - K_raw g on free entries, rhs = g on constrained entries, where
  * f is a nodal load field (full layout) and g holds Dirichlet values (full layout; only its
  * constrained entries are used).  K_raw is the saddle matrix without constraint elimination.
  * All pointers device, length N; rhs must not alias f or g. */
