@@ -87,6 +87,7 @@ struct Level {
   float* vc32 = nullptr;
   double* rk64 = nullptr;
   float* rk32 = nullptr;
+  float* part3 = nullptr;  // 3D: partial sums of the FP32 halo-free tiles (shared by all levels)
   int conv = 0;         // 1 while the context is in the corrector stage
   double rho = 0.0;
   // pressure Laplacian level (Cahouet-Chabard term): constraint mask, MG vectors, bound
@@ -662,6 +663,12 @@ void layout(gs_ctx* c, Arena& ar) {
   c->ctmp = ar.take<double>(c->nf);
   c->errw = ar.take<int>(4);
   for (int l = 0; l < c->L; ++l) c->lv[l].errw = c->errw;
+  if (c->dim == 3) {  // partial sums of the FP32 halo-free tiles: the finest level needs the most
+    long long mx = 0;
+    for (int l = 0; l < c->L; ++l) mx = std::max(mx, nh3_part_elems(c->lv[l].n));
+    float* p3 = ar.take<float>(mx);
+    for (int l = 0; l < c->L; ++l) c->lv[l].part3 = p3;
+  }
   const int gjn = std::max(c->nf, std::max(c->nfp, c->nmf));
   c->gjrow = ar.take<double>(gjn);
   c->gjcol = ar.take<double>(gjn);
@@ -805,6 +812,7 @@ TileArgs<T> tile_args(const Level& lv) {
   a.alpha = alphap<T>(lv);
   a.shape = lv.shape;
   a.err = lv.errw;
+  if (sizeof(T) == 4 && lv.g.dim == 3) a.part = (T*)lv.part3;
   if (lv.conv) {
     a.conv = 1;
     a.vc = sizeof(T) == 8 ? (const T*)lv.vc64 : (const T*)lv.vc32;

@@ -40,6 +40,8 @@ struct TileArgs {
   const T* rk;    // streamline parameter r_K per cell
   T rho, ihx, ihy, wq;  // density, 1 / h_x, 1 / h_y, h_x h_y
   int tiles[3];
+  T* part;        // 3D FP32: per-tile partial sums of the nodes on shared tile faces (gs_tile.cu,
+                  // tile3nh_body; NULL: the halo tiles are used)
   int shape;      // 2D velocity-block variant (0 / 1 / 2: tiles of 16 / 17 / 8 rows of evaluated cells,
                   // 3: the strip kernel of gs_strip2d.cuh; other operator blocks: 3 -> tiles of 8);
                   // 3D: 0 / 1 -> tiles of 8 x 8 x 8 / 8 x 8 x 4 evaluated cells
@@ -49,6 +51,15 @@ constexpr int kTileHeights2D = 3;  // tile variants of the full saddle operator
 // 3D cell tiles (TileArgs::shape): 0 -> 8 x 8 x 8, 1 -> 8 x 8 x 4 evaluated cells; every variant
 // sums a node's cell contributions in the same order, so the choice does not change any result
 constexpr int kTileShapes3D = 2;
+// FP32 3D velocity block without halo cells (gs_tile.cu, tile3nh_body): tiles of 8 x 8 x 4 cells, a
+// 17 x 17 x 9 node box each; the partial-sum buffer holds 3 boxes (one per component) per tile
+constexpr int kNH3Cells0 = 8, kNH3Cells1 = 8, kNH3Cells2 = 4;
+constexpr int kNH3Box = (2 * kNH3Cells0 + 1) * (2 * kNH3Cells1 + 1) * (2 * kNH3Cells2 + 1);
+inline long long nh3_part_elems(const int n[3]) {
+  const long long t = (long long)((n[0] + kNH3Cells0 - 1) / kNH3Cells0) * ((n[1] + kNH3Cells1 - 1) / kNH3Cells1) *
+                      ((n[2] + kNH3Cells2 - 1) / kNH3Cells2);
+  return t * 3 * kNH3Box;
+}
 constexpr int tile3d_depth(int shape) { return shape == 1 ? 4 : 8; }
 
 // Which blocks of the saddle operator a launch computes.

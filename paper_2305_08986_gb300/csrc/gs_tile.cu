@@ -326,6 +326,300 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   }
 }
 
+// ---- 3D velocity block (A x, b - A x, Chebyshev step) without halo cells, FP32 ----------------------
+// The tiles above evaluate one layer of halo cells per axis; on meshes of 2^k cells per axis a tile
+// owning 7 cells per axis then evaluates ~1.95x the cells of the mesh.  Here a CTA owns and evaluates
+// exactly the cells [cs, cs + TC) (8 x 8 x 4; the last tile along an axis may be cut by the mesh).
+// Its cells touch the nodes [2 cs, 2 cs + 2 TC] per axis; the nodes strictly inside that box, and
+// those on a face at the mesh boundary, are complete after the CTA's own cells and get the mode's
+// epilogue at once.  A node on a face shared with a neighbouring tile receives contributions from
+// up to 8 tiles: each tile writes its partial sum there to a per-tile slot of the partial buffer
+// (TileArgs::part), and a second kernel (fix3nh_body) adds the partials of the sharing tiles in a
+// fixed order (tiles lexicographic, x fastest) and applies the epilogue.  Inside a tile the cells are
+// processed in 8 phases by their global parity class, as in the tiles above.  The sums are
+// deterministic; they differ in rounding from the halo tiles' (a different association at the
+// shared faces), so all FP32 applications of the 3D velocity block use this kernel.
+struct NH3 {
+  static constexpr int TC0 = kNH3Cells0, TC1 = kNH3Cells1, TC2 = kNH3Cells2;  // cells per tile
+  static constexpr int G0 = TC0 / 2, G1 = TC1 / 2, G2 = TC2 / 2, NG = G0 * G1 * G2;  // 32 groups
+  static constexpr int THREADS = NG * 3;                                // one warp per component
+  static constexpr int W0 = 2 * TC0 + 1, W1 = 2 * TC1 + 1, W2 = 2 * TC2 + 1;  // node box 17 x 17 x 9
+  static constexpr int NW = W0 * W1 * W2;                               // 2601 nodes
+  static_assert(NW == kNH3Box, "node box of the partial-sum buffer");
+  static constexpr int P0 = 2 * TC0, P1 = 2 * TC1, P2 = 2 * TC2;        // node spacing of tile faces
+};
+
+template <typename T>
+struct SmemNH3 {
+  using K = Skew3<T>;
+  // node box in the skewed window layout (row pitch 17), used for the input window and the sums
+  static constexpr int WVA = (NH3::W0 - 1) + (NH3::W1 - 1) * NH3::W0 + (NH3::W2 - 1) * K::WP +
+                             K::WA * ((NH3::W1 - 1) >> 2) + K::WB * ((NH3::W2 - 1) >> 2) + 1;
+  static constexpr int TOTAL = 6 * WVA;  // x window (3 components) + sums (3 components)
+  static constexpr int FLAGS = NH3::NW;  // bytes
+  static_assert(NH3::W0 == 17 && NH3::W1 == 17, "the skewed layout assumes a row pitch of 17");
+  static_assert(K::WP >= NH3::W0 * NH3::W1 + K::WA * ((NH3::W1 - 1) >> 2), "planes must not overlap");
+};
+
+// number of tiles of the halo-free 3D kernel along each axis
+__host__ __device__ inline int nh3_tiles(int n, int tc) { return (n + tc - 1) / tc; }
+
+template <typename T, int MODE>
+__device__ __forceinline__ void tile3nh_body(const TileArgs<T>& A, int bid) {
+  using S = NH3;
+  using SM = SmemNH3<T>;
+  using K = Skew3<T>;
+  constexpr int W = S::W0, WW = S::W0 * S::W1, WV = S::NW, WVA = SM::WVA;
+  auto widx = [](int i0, int i1, int i2) { return i0 + W * i1 + K::WP * i2 + K::WA * (i1 >> 2) + K::WB * (i2 >> 2); };
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sx = reinterpret_cast<T*>(smem_raw);
+  T* su = sx + 3 * WVA;
+  uint8_t* sflag = reinterpret_cast<uint8_t*>(su + 3 * WVA);
+  const Geom& g = A.g;
+  const OpCoef<T>& c = A.c;
+  const bool raw = A.raw != 0;
+  const bool vmasked = !raw && g.vmask != nullptr;
+  const int tid = threadIdx.x;
+  int tile = bid;
+  const int t0 = tile % A.tiles[0];
+  tile /= A.tiles[0];
+  const int t1 = tile % A.tiles[1];
+  const int t2 = tile / A.tiles[1];
+  const int cs0 = t0 * S::TC0, cs1 = t1 * S::TC1, cs2 = t2 * S::TC2;
+  const int I0 = 2 * cs0, J0 = 2 * cs1, K0 = 2 * cs2;
+  const long long Nv = g.Nv;
+
+  // ---- stage the node box of x (all copies in flight together), zero the sums ----
+  for (int i = tid; i < WV; i += S::THREADS) {
+    const int a = i % W, b = (i / W) % S::W1, k = i / WW;
+    const int I = I0 + a, J = J0 + b, Kz = K0 + k;
+    const bool inr = I < g.nv[0] && J < g.nv[1] && Kz < g.nv[2];
+    const long long node = inr ? I + (long long)g.nv[0] * (J + (long long)g.nv[1] * Kz) : 0;
+    const bool fcon = !raw && inr && !vmasked && face_constrained(g, I, J, Kz);
+    const int wi = widx(a, b, k);
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) cp_async_3d(sx + cc * WVA + wi, A.xu + cc * Nv + node, inr && !fcon);
+    sflag[i] = (vmasked && inr) ? g.vmask[node] : 0;
+  }
+  for (int i = tid; i < 3 * WVA; i += S::THREADS) su[i] = T(0);
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (vmasked) {
+    for (int i = tid; i < WV; i += S::THREADS)
+      if (sflag[i]) {
+        const int wi = widx(i % W, (i / W) % S::W1, i / WW);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) sx[cc * WVA + wi] = T(0);
+      }
+  }
+  __syncthreads();
+
+  // ---- the tile's cells in 8 phases (cs is even on every axis: local parity = global parity) ----
+  const int comp = tid / S::NG;  // warp-uniform component
+  const int grp = tid % S::NG;
+  const int g0 = grp % S::G0;
+  const int g1 = (grp / S::G0) % S::G1;
+  const int g2 = grp / (S::G0 * S::G1);
+  const int pa[3] = {comp, comp == 2 ? 0 : comp + 1, comp == 0 ? 2 : comp - 1};
+  T km_l[3], ex_l[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    km_l[q] = c.km[pa[q]];
+    ex_l[q] = c.ex[pa[q]];
+  }
+  auto fw = [](int ax, int i) { return ax == 0 ? i : (ax == 1 ? W * i + K::WA * (i >> 2) : K::WP * i + K::WB * (i >> 2)); };
+  T* sc = su + comp * WVA;
+#pragma unroll 1
+  for (int ph = 0; ph < 8; ++ph) {
+    const int lp[3] = {2 * g0 + (ph & 1), 2 * g1 + ((ph >> 1) & 1), 2 * g2 + ((ph >> 2) & 1)};
+    const int c0 = cs0 + lp[0], c1 = cs1 + lp[1], c2 = cs2 + lp[2];
+    bool active = c0 < g.n[0] && c1 < g.n[1] && c2 < g.n[2];
+    long long cell = 0;
+    if (active) {
+      cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
+      if (cell_void(g, cell)) active = false;
+    }
+    if (active) {
+      const T eta = A.eta[cell] * c.eta_scale;
+      const T mmK = A.alpha ? c.mm * A.alpha[cell] : c.mm;
+      int o[3][3];  // box offsets of the cell's nodes along each logical axis (input and sums alike)
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) o[q][t] = fw(pa[q], 2 * lp[pa[q]] + t);
+      T yl[27];
+      cell_A3p(sx + pa[0] * WVA, sx + pa[1] * WVA, sx + pa[2] * WVA, o[0], o[1], o[2], yl, eta, mmK, km_l, ex_l);
+#pragma unroll
+      for (int lc = 0; lc < 3; ++lc)
+#pragma unroll
+        for (int lb = 0; lb < 3; ++lb)
+#pragma unroll
+          for (int la = 0; la < 3; ++la) sc[o[0][la] + o[1][lb] + o[2][lc]] += yl[la + 3 * lb + 9 * lc];
+    }
+    __syncthreads();
+  }
+
+  // ---- nodes of the box: epilogue, or the partial sum of a node on a shared face ----
+  const int e0 = min(S::P0, 2 * g.n[0] - I0) + 1;
+  const int e1 = min(S::P1, 2 * g.n[1] - J0) + 1;
+  const int e2 = min(S::P2, 2 * g.n[2] - K0) + 1;
+  const bool lo0 = cs0 > 0, lo1 = cs1 > 0, lo2 = cs2 > 0;
+  const bool hi0 = cs0 + S::TC0 < g.n[0], hi1 = cs1 + S::TC1 < g.n[1], hi2 = cs2 + S::TC2 < g.n[2];
+  T* part = A.part + (long long)bid * 3 * WV;
+  const int nbox = e0 * e1 * e2;
+  for (int i = tid; i < nbox; i += S::THREADS) {
+    const int i0 = i % e0;
+    const int i1 = (i / e0) % e1;
+    const int i2 = i / (e0 * e1);
+    const int s = widx(i0, i1, i2);
+    const bool shared = (i0 == 0 && lo0) || (i0 == S::P0 && hi0) || (i1 == 0 && lo1) || (i1 == S::P1 && hi1) ||
+                        (i2 == 0 && lo2) || (i2 == S::P2 && hi2);
+    if (shared) {
+      const int li = i0 + S::W0 * (i1 + S::W1 * i2);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) part[a * WV + li] = su[a * WVA + s];
+      continue;
+    }
+    const int I = I0 + i0, J = J0 + i1, Kz = K0 + i2;
+    const long long node = I + (long long)g.nv[0] * (J + (long long)g.nv[1] * Kz);
+    const bool con = !raw && vnode_constrained(g, node, I, J, Kz);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long gi = a * Nv + node;
+      const T ax = con ? A.xu[gi] : su[a * WVA + s];
+      if (MODE == TILE_APPLY) {
+        A.yu[gi] = ax;
+      } else if (MODE == TILE_RESID) {
+        A.yu[gi] = A.bu[gi] - ax;
+      } else {
+        const T r = A.bu[gi] - ax;
+        T dn = A.c2 * A.dinv[gi] * r;
+        if (A.use_d) dn += A.c1 * A.d[gi];
+        A.d[gi] = dn;
+        const T xin = con ? A.xu[gi] : sx[a * WVA + s];
+        A.xout[gi] = xin + dn;
+      }
+    }
+  }
+}
+
+// The nodes on faces shared by tiles of tile3nh_body: one thread per node, all three components.
+// Node families: planes x = 16 k (0 < k < tiles_x), then planes y = 16 k without the nodes of an
+// x-plane, then planes z = 8 k without the nodes of an x- or y-plane, so each node is visited once.
+template <typename T, int MODE>
+__device__ __forceinline__ void fix3nh_body(const TileArgs<T>& A, int blk) {
+  using S = NH3;
+  const Geom& g = A.g;
+  const int nv0 = g.nv[0], nv1 = g.nv[1], nv2 = g.nv[2];
+  const int nb0 = A.tiles[0] - 1, nb1 = A.tiles[1] - 1, nb2 = A.tiles[2] - 1;
+  const long long nX = (long long)nb0 * nv1 * nv2, nY = (long long)nb1 * nv0 * nv2, nZ = (long long)nb2 * nv0 * nv1;
+  long long idx = (long long)blk * 256 + threadIdx.x;
+  // an interior tile face along an axis: node coordinate P k with 0 < k < tiles
+  auto face = [](int X, int P, int tiles) { return X % P == 0 && X > 0 && X / P < tiles; };
+  int I, J, Kz;
+  if (idx < nX) {
+    const long long pl = (long long)nv1 * nv2;
+    const int p = (int)(idx / pl);
+    const long long r = idx - p * pl;
+    I = S::P0 * (p + 1);
+    J = (int)(r % nv1);
+    Kz = (int)(r / nv1);
+  } else if ((idx -= nX) < nY) {
+    const long long pl = (long long)nv0 * nv2;
+    const int p = (int)(idx / pl);
+    const long long r = idx - p * pl;
+    J = S::P1 * (p + 1);
+    I = (int)(r % nv0);
+    Kz = (int)(r / nv0);
+    if (face(I, S::P0, A.tiles[0])) return;
+  } else if ((idx -= nY) < nZ) {
+    const long long pl = (long long)nv0 * nv1;
+    const int p = (int)(idx / pl);
+    const long long r = idx - p * pl;
+    Kz = S::P2 * (p + 1);
+    I = (int)(r % nv0);
+    J = (int)(r / nv0);
+    if (face(I, S::P0, A.tiles[0]) || face(J, S::P1, A.tiles[1])) return;
+  } else {
+    return;
+  }
+  // the tiles sharing the node and its local index in each (one or two per axis, lower tile first)
+  int tl[3][2], ll[3][2], nt[3];
+  const int X[3] = {I, J, Kz}, P[3] = {S::P0, S::P1, S::P2};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (face(X[ax], P[ax], A.tiles[ax])) {
+      nt[ax] = 2;
+      tl[ax][0] = X[ax] / P[ax] - 1;
+      ll[ax][0] = P[ax];
+      tl[ax][1] = X[ax] / P[ax];
+      ll[ax][1] = 0;
+    } else {
+      nt[ax] = 1;
+      tl[ax][0] = min(X[ax] / P[ax], A.tiles[ax] - 1);
+      ll[ax][0] = X[ax] - P[ax] * tl[ax][0];
+      tl[ax][1] = tl[ax][0];
+      ll[ax][1] = ll[ax][0];
+    }
+  }
+  const long long node = I + (long long)nv0 * (J + (long long)nv1 * Kz);
+  const bool con = !A.raw && vnode_constrained(g, node, I, J, Kz);
+  const long long Nv = g.Nv;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T acc = T(0);
+    for (int b2 = 0; b2 < nt[2]; ++b2)
+      for (int b1 = 0; b1 < nt[1]; ++b1)
+        for (int b0 = 0; b0 < nt[0]; ++b0) {
+          const long long t = tl[0][b0] + (long long)A.tiles[0] * (tl[1][b1] + (long long)A.tiles[1] * tl[2][b2]);
+          const int li = ll[0][b0] + S::W0 * (ll[1][b1] + S::W1 * ll[2][b2]);
+          acc += A.part[(t * 3 + a) * S::NW + li];
+        }
+    const long long gi = a * Nv + node;
+    const T ax = con ? A.xu[gi] : acc;
+    if (MODE == TILE_APPLY) {
+      A.yu[gi] = ax;
+    } else if (MODE == TILE_RESID) {
+      A.yu[gi] = A.bu[gi] - ax;
+    } else {
+      const T r = A.bu[gi] - ax;
+      T dn = A.c2 * A.dinv[gi] * r;
+      if (A.use_d) dn += A.c1 * A.d[gi];
+      A.d[gi] = dn;
+      A.xout[gi] = A.xu[gi] + dn;
+    }
+  }
+}
+
+template <typename T, int MODE>
+struct Tile3NHK {
+  using Args = TileArgs<T>;
+  static constexpr int THREADS = NH3::THREADS, MINB = 3;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) { tile3nh_body<T, MODE>(a, blk); }
+};
+
+template <typename T, int MODE>
+struct Fix3NHK {
+  using Args = TileArgs<T>;
+  static constexpr int THREADS = 256, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int) { fix3nh_body<T, MODE>(a, blk); }
+};
+
+template <typename T, int MODE>
+static cudaError_t launch_nh3(TileArgs<T> a, cudaStream_t st) {
+  a.tiles[0] = nh3_tiles(a.g.n[0], NH3::TC0);
+  a.tiles[1] = nh3_tiles(a.g.n[1], NH3::TC1);
+  a.tiles[2] = nh3_tiles(a.g.n[2], NH3::TC2);
+  const long long nblocks = (long long)a.tiles[0] * a.tiles[1] * a.tiles[2];
+  cudaError_t e = submit<Tile3NHK<T, MODE>>(a, nblocks, sizeof(T) * SmemNH3<T>::TOTAL + SmemNH3<T>::FLAGS, st);
+  if (e != cudaSuccess) return e;
+  const long long nfix = (long long)(a.tiles[0] - 1) * a.g.nv[1] * a.g.nv[2] +
+                         (long long)(a.tiles[1] - 1) * a.g.nv[0] * a.g.nv[2] +
+                         (long long)(a.tiles[2] - 1) * a.g.nv[0] * a.g.nv[1];
+  if (nfix == 0) return cudaSuccess;
+  return submit<Fix3NHK<T, MODE>>(a, (nfix + 255) / 256, 0, st);
+}
+
 template <typename T, int MODE, bool WA, bool WBT, bool WB, int C2>
 struct TileK {
   using Args = TileArgs<T>;
@@ -370,6 +664,13 @@ template <typename T>
 cudaError_t launch_tile(int dim, int mode, int ops, TileArgs<T> a, cudaStream_t st) {
   if (mode == TILE_CHEB && ops != OPS_A) return cudaErrorInvalidValue;
   if (dim == 2) return launch_tile2d<T>(mode, ops, a, st);  // gs_tile2d.cu
+  if constexpr (sizeof(T) == 4) {
+    if (ops == OPS_A && a.part != nullptr) {  // FP32 velocity block: tiles without halo cells
+      if (mode == TILE_APPLY) return launch_nh3<T, TILE_APPLY>(a, st);
+      if (mode == TILE_RESID) return launch_nh3<T, TILE_RESID>(a, st);
+      return launch_nh3<T, TILE_CHEB>(a, st);
+    }
+  }
   if (mode == TILE_APPLY) return dispatch_ops<T, 3, TILE_APPLY>(ops, a, st);
   if (mode == TILE_RESID) return dispatch_ops<T, 3, TILE_RESID>(ops, a, st);
   return launch_one<T, 3, TILE_CHEB, true, false, false>(a, st);
