@@ -255,11 +255,11 @@ def run_reference(args, rank, world):
 # --------------------------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------------------------
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the finest-level
-# fused Chebyshev step at the 1280 x 224 workload (the strip kernel the autotuner picks there), from
-# one ncu --set full capture of the kernel as built now (profiles/strip2d_cheb_fp32_channel1280x224.md).
-# The writes (d, x') stay in L2 within the capture, so the figure is the read traffic.
-NCU_TRAFFIC_BYTES = {"cheb_step": 38.566912e6 + 9.728e3, "saddle_fp64": 24.761088e6 + 512.0}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from one ncu --set full
+# capture of each kernel as built now: the finest-level fused Chebyshev step at the 1280 x 224
+# workload (strip kernel; its writes d, x' stay in L2 within the capture, so the figure is the read
+# traffic) and the FP64 saddle operator (x and eta read once; y and spilled registers written).
+NCU_TRAFFIC_BYTES = {"cheb_step": 38.566912e6 + 9.728e3, "saddle_fp64": 25.351168e6 + 7.776256e6}
 
 
 def tile_step_bytes(n_u: int, n_cells: int, elem: int, kind: str) -> int:
