@@ -554,6 +554,7 @@ def run_gpu(args, rank, world):
 
     kfp64 = krylov_variant(krylov_fp64=2) if rank == 0 else None
     korth = krylov_variant(orth=1) if rank == 0 else None
+    kgram = krylov_variant(orth=2) if rank == 0 else None
     # the Schur approximation by the 1/eta-weighted pressure mass alone (schur_kind = 1), without the
     # Cahouet-Chabard term of the default; it needs ~13x the iterations on this reaction-dominated case
     kmass = krylov_variant(schur_kind=1) if rank == 0 and not args.skip_mono else None
@@ -637,6 +638,7 @@ def run_gpu(args, rank, world):
             "krylov_rooflines": krylov_table,
             "krylov_double_float_basis": kfp64,
             "krylov_selective_reorth": korth,
+            "krylov_gram_matrix_cgs": kgram,
             "schur_mass_only": kmass,
             "kernel_profile_ms": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
             "kernel_profile_note": "one CUDA event pair per launch (lengthens short launches); sums exceed the solve time",

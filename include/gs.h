@@ -107,7 +107,13 @@ typedef struct {            /* zero-initialised = defaults */
                                   Dirichlet condition), inverted by one multigrid V-cycle */
   int orth;                 /* 0: classical Gram-Schmidt always applied twice (CGS2, default);
                                1: second pass only when the new vector's norm drops below
-                                  1/sqrt(2) of its value before the projection */
+                                  1/sqrt(2) of its value before the projection;
+                               2: CGS2 through the Gram matrix G = V^T V of the cycle: one pass
+                                  for V^T w and the newest column of G, coefficients
+                                  c = h1 + (h1 - G h1) (equal to CGS2's in exact arithmetic), one
+                                  update pass (3 instead of 4 FP64 FMAs per basis entry; up to 64
+                                  basis vectors, CGS2 beyond).  Single solves only: gs_batch_solve
+                                  and the engine take orth = 0. */
   int graphs;               /* 0: replay the preconditioner's fixed launch sequence as a CUDA graph
                                   captured at its second application (default); 1: plain launches */
   int plap_degree;          /* Chebyshev degree of the pressure-Laplacian V-cycle of the

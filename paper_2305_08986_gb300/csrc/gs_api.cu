@@ -183,6 +183,8 @@ struct gs_ctx {
   int GA = 1;  // blocks of the fused axpy + norm (G * (m + 2) >= GA partial sums)
   int GF = 1;  // blocks of the fused CGS2 update + dots (one wave, 4 CTAs per SM)
   double* dsc = nullptr;
+  double* gram = nullptr;  // orth = 2: G = V^T V of the current restart cycle, (m + 1) x (m + 1)
+  double* gsc = nullptr;   // orth = 2: [V^T w ; V^T v_j], 2 (m + 2) values
   double* hpin = nullptr;
   int last_it = 0;
   double last_rel = 0.0;
@@ -261,7 +263,7 @@ gs_options normalize_opts(const gs_options* o) {
   r.lanczos_steps = opt_or(r.lanczos_steps, 12);
   r.coarse_mode = r.coarse_mode == 1 ? 1 : 0;
   r.schur_kind = (r.schur_kind == 1 || r.schur_kind == 2) ? r.schur_kind : 0;
-  r.orth = r.orth == 1 ? 1 : 0;
+  r.orth = (r.orth == 1 || r.orth == 2) ? r.orth : 0;
   r.graphs = r.graphs == 1 ? 1 : 0;
   r.plap_degree = opt_or(r.plap_degree, 2);
   // 0 (default) and 1: IEEE FP64 basis; 2: double-float basis (stored internally as 0 / 1 = double-float / FP64)
@@ -744,8 +746,12 @@ void layout(gs_ctx* c, Arena& ar) {
   if (GF > 4 * 152) GF = 4 * 152;
   if (GF < 1) GF = 1;
   c->GF = (int)GF;
-  c->part = ar.take<double>((long long)std::max(c->G, c->GF) * (m + 2));
+  // partial-sum rows: m + 2 dots, or both dot blocks of orth = 2 (2 k rows, k <= 64)
+  const int prow = std::max(m + 2, 2 * std::min(m + 1, 64) + 2);
+  c->part = ar.take<double>((long long)std::max(c->G, c->GF) * prow);
   c->dsc = ar.take<double>(4 * (m + 4));
+  c->gram = ar.take<double>((long long)(m + 1) * (m + 1));
+  c->gsc = ar.take<double>(2 * (m + 2));
   c->footprint = ar.off + 256;
 }
 
@@ -1820,6 +1826,14 @@ cudaError_t dots_strip(const double* V, long long ldv, int k, const double* w, l
                        cudaStream_t st) {
   return launch_dots_strip_fp64(V, ldv, k, w, n, part, G, st);
 }
+cudaError_t dots_strip2(const float2* V, long long ldv, int k, const double* w, long long n, double* part, int G,
+                        cudaStream_t st) {
+  return launch_dots_strip2_df(V, ldv, k, w, n, part, G, st);
+}
+cudaError_t dots_strip2(const double* V, long long ldv, int k, const double* w, long long n, double* part, int G,
+                        cudaStream_t st) {
+  return launch_dots_strip2_fp64(V, ldv, k, w, n, part, G, st);
+}
 cudaError_t multi_axpy_dots(const float2* V, long long ldv, int k, const double* coef, double sign, double* w,
                             long long n, double* part, int G, cudaStream_t st) {
   return launch_multi_axpy_dots_df(V, ldv, k, coef, sign, w, n, part, G, st);
@@ -1845,6 +1859,24 @@ gs_status cgs2_fused(gs_ctx* c, const B* V, int j, double* h1, double* h2, doubl
   KL(K_AXPY, multi_axpy_dots(V, N, j + 1, h1, -1.0, c->w, N, c->part, c->GF, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, j + 1, c->GF, h2, c->st));
   KL(K_AXPY, multi_axpy_norm_b(V, N, j + 1, h2, -1.0, c->w, N, c->part, c->GA, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
+  return GS_OK;
+}
+
+// Classical Gram-Schmidt through the Gram matrix (orth = 2): one pass over V for d = [V^T w ;
+// V^T v_j] (the newest basis vector, one new column of G = V^T V), c = h1 + (h1 - G h1) on the
+// device, then one pass w -= V c with the new |w|^2.  In exact arithmetic c equals the CGS2
+// coefficients h1 + V^T (w - V h1): the second pass's dots are replaced by G h1, so V is read twice
+// instead of three times and the FP64 work is 3 instead of 4 FMAs per basis entry.
+template <typename B>
+gs_status cgs_gram(gs_ctx* c, const B* V, int j, double* coef, double* nrm) {
+  const long long N = c->N;
+  const int m = c->opt.restart;
+  const int g2 = std::min(c->GF, 3 * 152);  // one wave of the two-vector dots (3 CTAs per SM)
+  KL(K_DOTS, dots_strip2(V, N, j + 1, c->w, N, c->part, g2, c->st));
+  KL(K_DOTS, launch_reduce_partials(c->part, 2 * (j + 1), g2, c->gsc, c->st));
+  KL(K_DOTS, launch_gram_correct(c->gsc, c->gram, m + 1, j + 1, coef, c->st));
+  KL(K_AXPY, multi_axpy_norm_b(V, N, j + 1, coef, -1.0, c->w, N, c->part, c->GA, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
   return GS_OK;
 }
@@ -1902,7 +1934,17 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       // |w|^2 in the same pass); a second pass when |w| fell below 1/sqrt(2) of its value
       // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, orth = 0)
       double hn;
-      if (c->opt.orth == 0 && j + 1 <= kFusedGsMax) {
+      if (c->opt.orth == 2 && j + 1 <= kFusedGsMax) {
+        if (dfk)
+          CKS(cgs_gram(c, (const float2*)Vdf, j, h2, nrm));
+        else
+          CKS(cgs_gram(c, (const double*)c->V, j, h2, nrm));
+        CK(cudaMemcpyAsync(c->hpin, h2, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(c->hpin + (j + 1), nrm, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int i = 0; i <= j; ++i) Hc(i, j) = c->hpin[i];
+        hn = std::sqrt(c->hpin[j + 1]);
+      } else if (c->opt.orth != 1 && j + 1 <= kFusedGsMax) {
         // CGS2 with the first update fused into the second pass's dots: three passes over V
         if (dfk)
           CKS(cgs2_fused(c, (const float2*)Vdf, j, h1, h2, nrm));
@@ -1932,7 +1974,7 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
         for (int i = 0; i <= j; ++i) Hc(i, j) = c->hpin[i];
         const double wn0 = std::sqrt(c->hpin[j + 1]);
         hn = std::sqrt(c->hpin[m + 1]);
-        if (c->opt.orth == 0 || hn < kReorthKappa * wn0) {
+        if (c->opt.orth != 1 || hn < kReorthKappa * wn0) {
           if (dfk)
             KL(K_DOTS, launch_dots_partial_df(Vdf, N, j + 1, c->w, N, c->part, c->G, 0, c->st));
           else

@@ -387,6 +387,116 @@ struct DotsStripK {
     }
   }
 };
+// Both dot blocks of classical Gram-Schmidt evaluated through the Gram matrix (option orth = 2):
+// part[i * nblk + blk] = partials of V[i] . w and part[(k + i) * nblk + blk] = partials of V[i] . u
+// for i < k, u = V[k - 1] (the newest basis vector: one new column of G = V^T V).  Like DotsStripK,
+// with a second staged strip; every basis row is read once for both dots.
+template <typename B>
+struct DotsStrip2K {
+  using O = BasisOps<B>;
+  static constexpr int KW = 8;
+  struct Args { const B* V; long long ldv; int k; const double* w; long long n; double* part; };
+  static constexpr int THREADS = TPB, MINB = 3;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    __shared__ B wt[TPB];
+    __shared__ B ut[TPB];
+    const B* __restrict__ V = a.V;
+    const long long ldv = a.ldv, n = a.n;
+    const int k = a.k;
+    const B* __restrict__ U = V + (long long)(k - 1) * ldv;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    B accw[KW], accu[KW];
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+      accw[q] = O::zero();
+      accu[q] = O::zero();
+    }
+    for (long long base = (long long)blk * TPB; base < n; base += (long long)nblk * TPB) {
+      const long long e = base + tid;
+      wt[tid] = e < n ? O::split(a.w[e]) : O::zero();
+      ut[tid] = e < n ? U[e] : O::zero();
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < KW; ++q) {
+        const int i = wid + 8 * q;
+        if (i < k) {
+          const B* Vi = V + i * ldv + base;
+          B v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int el = lane + 32 * t;
+            v[t] = base + el < n ? Vi[el] : O::zero();
+          }
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            O::fma(accw[q], v[t], wt[lane + 32 * t]);
+            O::fma(accu[q], v[t], ut[lane + 32 * t]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+      const int i = wid + 8 * q;
+      if (i < k) {
+        double v = O::join(accw[q]), u = O::join(accu[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          v += __shfl_down_sync(0xffffffffu, v, o);
+          u += __shfl_down_sync(0xffffffffu, u, o);
+        }
+        if (lane == 0) {
+          a.part[(long long)i * nblk + blk] = v;
+          a.part[(long long)(k + i) * nblk + blk] = u;
+        }
+      }
+    }
+  }
+};
+template <typename B>
+cudaError_t launch_dots_strip2(const B* V, long long ldv, int k, const double* w, long long n, double* part, int G,
+                               cudaStream_t st) {
+  if (k < 1 || k > 8 * DotsStrip2K<B>::KW) return cudaErrorInvalidValue;
+  return submit<DotsStrip2K<B>>({V, ldv, k, w, n, part}, G, 0, st);
+}
+cudaError_t launch_dots_strip2_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
+                                  int G, cudaStream_t st) {
+  return launch_dots_strip2<float2>(V, ldv, k, w, n, part, G, st);
+}
+cudaError_t launch_dots_strip2_fp64(const double* V, long long ldv, int k, const double* w, long long n, double* part,
+                                    int G, cudaStream_t st) {
+  return launch_dots_strip2<double>(V, ldv, k, w, n, part, G, st);
+}
+
+// Gram-matrix form of the second Gram-Schmidt pass: with d = [V^T w ; V^T v_{k-1}] (2k values),
+// store column k - 1 of G = V^T V (and its mirror row), then c = h1 + (h1 - G h1), h1 = V^T w.  In
+// exact arithmetic c is the CGS2 coefficient vector h1 + V^T (w - V h1); the update w - V c follows.
+// One block; k <= 64.
+struct GramCorrK {
+  struct Args { const double* d; double* G; int ldg; int k; double* c; };
+  static constexpr int THREADS = 64, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int, int) {
+    const int i = threadIdx.x, k = a.k;
+    if (i < k) {
+      const double g = a.d[k + i];
+      a.G[(long long)i * a.ldg + (k - 1)] = g;
+      a.G[(long long)(k - 1) * a.ldg + i] = g;
+    }
+    __syncthreads();
+    if (i < k) {
+      double s = 0.0;
+      for (int l = 0; l < k; ++l) s = fma(a.G[(long long)i * a.ldg + l], a.d[l], s);
+      const double h = a.d[i];
+      a.c[i] = h + (h - s);
+    }
+  }
+};
+cudaError_t launch_gram_correct(const double* d, double* G, int ldg, int k, double* c, cudaStream_t st) {
+  if (k < 1 || k > 64) return cudaErrorInvalidValue;
+  return submit<GramCorrK>({d, G, ldg, k, c}, 1, 0, st);
+}
+
 template <typename B>
 cudaError_t launch_dots_strip(const B* V, long long ldv, int k, const double* w, long long n, double* part, int G,
                               cudaStream_t st) {

@@ -197,6 +197,13 @@ template <typename T>
 cudaError_t launch_dots_partial(const T* V, long long ldv, int k, const T* w, long long n,
                                 double* part, int G, cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* part, int k, int G, double* out, cudaStream_t st);
+// Gram-Schmidt through the Gram matrix (orth = 2): dots of the basis with w and with its newest row,
+// then the correction of the coefficients (gs_blas.cu)
+cudaError_t launch_dots_strip2_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
+                                  int G, cudaStream_t st);
+cudaError_t launch_dots_strip2_fp64(const double* V, long long ldv, int k, const double* w, long long n, double* part,
+                                    int G, cudaStream_t st);
+cudaError_t launch_gram_correct(const double* d, double* G, int ldg, int k, double* c, cudaStream_t st);
 // k dot products V[i] . w plus w . w in row k of part (rows 0..k)
 cudaError_t launch_dots_norm_partial(const double* V, long long ldv, int k, const double* w, long long n,
                                      double* part, int G, cudaStream_t st);

@@ -127,6 +127,27 @@ def test_solve_parity_selective_reorth():
     assert rel(normalize_pressure(m, o.sys, x.cpu().numpy()), normalize_pressure(m, o.sys, xo)) <= 1e-8
 
 
+@pytest.mark.parametrize("name", ["box3d", "channel_small"])
+def test_solve_parity_gram_matrix_cgs(name):
+    """Classical Gram-Schmidt through the Gram matrix (orth = 2: one pass for V^T w and the newest
+    column of V^T V, coefficients h1 + (h1 - G h1), one update pass) against the oracle's CGS2, whose
+    coefficients it equals in exact arithmetic."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS[name]()
+    m = mesh_from_problem(p)
+    o = StokesOracle(m, p.eta, p.alpha, p.levels)
+    b_ref = o.sys.lift_rhs(p.f, p.g)
+    xo, ito, relo, _ = o.solve(b_ref, tol=1e-11)
+    for krylov in (1, 2):
+        s = gs.Solver.from_problem(p, mg_precision=64, orth=2, krylov_fp64=krylov)
+        b = torch.tensor(b_ref, device="cuda")
+        x = torch.zeros_like(b)
+        it, rr, _ = s.solve(b, x, tol=1e-11)
+        assert rr <= 1e-11 and abs(it - ito) <= max(2, 0.05 * ito), (krylov, it, ito)
+        assert rel(normalize_pressure(m, o.sys, x.cpu().numpy()), normalize_pressure(m, o.sys, xo)) <= 1e-8
+
+
 def test_cahouet_chabard_iterations():
     """alpha = 1e3 channel: FP32 multigrid with the Cahouet-Chabard term stays in the tens of
     iterations (the mass-only Schur approximation needs several hundred)."""
