@@ -184,31 +184,42 @@ def cpu_baseline_entry(res, cores):
                        f"({res[0]['n_u']} rows, {res[0]['csr_nnz']} nonzeros), median of 20 per core")}
 
 
-def krylov_bytes(n: int, iterations: int, restart: int):
-    """Algorithmic HBM bytes and FP64 fused multiply-adds of the CGS2 kernels over one solve (8 B per
-    basis entry; iteration k uses the j + 1 = (k mod restart) + 1 basis rows of its cycle):
+def krylov_bytes(n: int, iterations: int, restart: int, form: str = "gram"):
+    """Algorithmic HBM bytes and FP64 fused multiply-adds of the Gram-Schmidt kernels over one solve
+    (8 B per basis entry; iteration k uses the j + 1 = (k mod restart) + 1 basis rows of its cycle).
+    form "gram" (the default, orth = 0 / 2):
+      dot pass: the j + 1 rows and w read once; 2 (j + 1) FMAs per entry (V^T w and the newest
+      column of V^T V);
+      update pass (+ norm): the rows read, w read and written; j + 2 FMAs per entry;
+    form "explicit" (orth = 3):
       first pass (strip dots): the j + 1 rows and w read once; j + 1 FMAs per entry;
       second pass (update + dots): the rows read once from HBM (again from L1/L2 for the dots), w read
       and written; 2 (j + 1) FMAs per entry;
       third pass (update + norm): the rows read, w read and written; j + 2 FMAs per entry;
-      the new basis vector: w read, v written."""
+    both: the new basis vector, w read and v written."""
     dots = axpy = 0
     fma_dots = fma_axpy = 0
     for k in range(iterations):
         rows = (k % restart) + 1
         dots += (rows + 1) * n * 8
-        axpy += 2 * (rows + 2) * n * 8 + 2 * n * 8
-        fma_dots += rows * n
-        fma_axpy += (3 * rows + 1) * n
+        if form == "gram":
+            axpy += (rows + 2) * n * 8 + 2 * n * 8
+            fma_dots += 2 * rows * n
+            fma_axpy += (rows + 1) * n
+        else:
+            axpy += 2 * (rows + 2) * n * 8 + 2 * n * 8
+            fma_dots += rows * n
+            fma_axpy += (3 * rows + 1) * n
     return dots, axpy, fma_dots, fma_axpy
 
 
-def krylov_rooflines(prof: dict, n: int, iterations: int, restart: int, peak_gbs: float, fp64_tflops: float):
+def krylov_rooflines(prof: dict, n: int, iterations: int, restart: int, peak_gbs: float, fp64_tflops: float,
+                     form: str = "gram"):
     """Achieved GB/s (fraction of the measured HBM peak) and FP64 TFLOP/s (fraction of the measured
     FP64 peak) of the Gram-Schmidt classes, from the live per-class device time of one solve (CUDA
     events, one pair per launch: slightly long).  With the FP64 basis the FMA count binds: one FP64
     FMA per 8-byte entry read needs 0.85 T FMA/s at the HBM rate, above the ~0.5 T FMA/s of GB300."""
-    dots_b, axpy_b, dots_f, axpy_f = krylov_bytes(n, iterations, restart)
+    dots_b, axpy_b, dots_f, axpy_f = krylov_bytes(n, iterations, restart, form)
     out = {}
     for cls, b, f in (("gram_schmidt_dots", dots_b, dots_f), ("krylov_axpy", axpy_b, axpy_f)):
         if cls in prof and prof[cls][1] > 0:
@@ -526,8 +537,8 @@ def run_gpu(args, rank, world):
         s64.close()
 
     # ---- the same solve with the double-float Krylov basis (krylov_fp64 = 2; the default is FP64) ----
-    # ---- Krylov variants on the same system: the double-float basis (krylov_fp64 = 2) and the
-    # selective second Gram-Schmidt pass (orth = 1, FP64 basis) ----
+    # ---- Krylov variants on the same system: the double-float basis (krylov_fp64 = 2), the
+    # selective second Gram-Schmidt pass (orth = 1) and CGS2 with an explicit second pass (orth = 3) ----
     def krylov_variant(**opts):
         try:
             sk = gs.Solver.from_problem(p, device=dev, restart=args.restart, max_iter=4000,
@@ -554,7 +565,7 @@ def run_gpu(args, rank, world):
 
     kfp64 = krylov_variant(krylov_fp64=2) if rank == 0 else None
     korth = krylov_variant(orth=1) if rank == 0 else None
-    kgram = krylov_variant(orth=2) if rank == 0 else None
+    kcgs2 = krylov_variant(orth=3) if rank == 0 else None
     # the Schur approximation by the 1/eta-weighted pressure mass alone (schur_kind = 1), without the
     # Cahouet-Chabard term of the default; it needs ~13x the iterations on this reaction-dominated case
     kmass = krylov_variant(schur_kind=1) if rank == 0 and not args.skip_mono else None
@@ -638,7 +649,7 @@ def run_gpu(args, rank, world):
             "krylov_rooflines": krylov_table,
             "krylov_double_float_basis": kfp64,
             "krylov_selective_reorth": korth,
-            "krylov_gram_matrix_cgs": kgram,
+            "krylov_explicit_cgs2": kcgs2,
             "schur_mass_only": kmass,
             "kernel_profile_ms": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
             "kernel_profile_note": "one CUDA event pair per launch (lengthens short launches); sums exceed the solve time",

@@ -105,15 +105,16 @@ typedef struct {            /* zero-initialised = defaults */
                                2: Cahouet-Chabard S^{-1} ~ M_p(1/eta)^{-1} + alpha K_p^{-1}, K_p the
                                   Q1 pressure Laplacian (p = 0 on faces without a velocity
                                   Dirichlet condition), inverted by one multigrid V-cycle */
-  int orth;                 /* 0: classical Gram-Schmidt always applied twice (CGS2, default);
+  int orth;                 /* 0 (default) or 2: CGS2 through the Gram matrix G = V^T V of the cycle:
+                                  one pass over V for h1 = V^T w and the newest column of G, the
+                                  coefficients c = h1 + (h1 - G h1) (CGS2's coefficients
+                                  h1 + V^T (w - V h1) in exact arithmetic), one update pass w -= V c;
+                                  3 instead of 4 FP64 FMAs per basis entry (up to 64 basis vectors,
+                                  the explicit form beyond);
                                1: second pass only when the new vector's norm drops below
-                                  1/sqrt(2) of its value before the projection;
-                               2: CGS2 through the Gram matrix G = V^T V of the cycle: one pass
-                                  for V^T w and the newest column of G, coefficients
-                                  c = h1 + (h1 - G h1) (equal to CGS2's in exact arithmetic), one
-                                  update pass (3 instead of 4 FP64 FMAs per basis entry; up to 64
-                                  basis vectors, CGS2 beyond).  Single solves only: gs_batch_solve
-                                  and the engine take orth = 0. */
+                                  1/sqrt(2) of its value before the projection (single solves
+                                  only: the engine needs a fixed number of passes);
+                               3: CGS2 with an explicit second pass (three passes over V) */
   int graphs;               /* 0: replay the preconditioner's fixed launch sequence as a CUDA graph
                                   captured at its second application (default); 1: plain launches */
   int plap_degree;          /* Chebyshev degree of the pressure-Laplacian V-cycle of the
@@ -264,8 +265,8 @@ gs_status gs_set_corrector(gs_ctx* ctx, const double* vcirc, double rho);
 
 /* Solve `count` independent systems; ctxs[i] with rhs[i] -> x[i] (device pointers).
  * iterations / rel_residuals: host arrays of `count` entries or NULL.  Returns the first
- * non-OK status (all systems are still attempted).  When every context uses the default
- * orthogonalisation (orth = 0) and no profiling, the systems run together through a batching
+ * non-OK status (all systems are still attempted).  When every context uses a fixed number of
+ * Gram-Schmidt passes (orth != 1) and no profiling, the systems run together through a batching
  * engine on ctxs[0]'s stream (one launch per kernel per FGMRES iteration for all of them, see
  * gs_engine_*).  Otherwise they run one after the other through gs_solve. */
 gs_status gs_batch_solve(gs_ctx* const* ctxs, int count, const double* const* rhs,
@@ -405,7 +406,7 @@ gs_status gs_coarse_solve_noalloc(gs_ctx* ctx, const double* b, double* y);
  * every context added (0: 50); stream: cudaStream_t or NULL; all engine work is enqueued there.
  * The engine allocates its own staging buffers (device and pinned host memory, a few hundred
  * bytes per slot plus the argument tables of one step).
- * gs_engine_add: ctx must use orth = 0 and no profiling and must not be in the engine already;
+ * gs_engine_add: ctx must use orth != 1 and no profiling and must not be in the engine already;
  * rhs, x: device, full length, x holds the initial guess and receives the solution; they and the
  * context stay in use until the solve is reported by gs_engine_poll.  Synchronises ctx's stream.
  * GS_EBUSY when every slot is taken.

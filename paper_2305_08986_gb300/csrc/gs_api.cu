@@ -263,7 +263,8 @@ gs_options normalize_opts(const gs_options* o) {
   r.lanczos_steps = opt_or(r.lanczos_steps, 12);
   r.coarse_mode = r.coarse_mode == 1 ? 1 : 0;
   r.schur_kind = (r.schur_kind == 1 || r.schur_kind == 2) ? r.schur_kind : 0;
-  r.orth = (r.orth == 1 || r.orth == 2) ? r.orth : 0;
+  // public 0 / 2 -> Gram-matrix CGS2 (internal 2), 1 -> selective (1), 3 -> explicit CGS2 (internal 0)
+  r.orth = r.orth == 1 ? 1 : (r.orth == 3 ? 0 : 2);
   r.graphs = r.graphs == 1 ? 1 : 0;
   r.plap_degree = opt_or(r.plap_degree, 2);
   // 0 (default) and 1: IEEE FP64 basis; 2: double-float basis (stored internally as 0 / 1 = double-float / FP64)
@@ -1815,7 +1816,7 @@ gs_status norm2_host(gs_ctx* c, const double* x, double* out) {
   return dot_host<double>(c, x, c->N, 1, x, c->N, out);
 }
 
-// CGS2 with the double-float basis (orth = 0): h1 = V^T w; w -= V h1 fused with h2 = V^T w (one
+// CGS2 with the double-float basis (explicit second pass): h1 = V^T w; w -= V h1 fused with h2 = V^T w (one
 // pass over V); w -= V h2 with the new |w|^2.  h1, h2: j + 1 entries each, nrm: |w|^2 (device).
 const int kFusedGsMax = 64;
 cudaError_t dots_strip(const float2* V, long long ldv, int k, const double* w, long long n, double* part, int G,
@@ -1850,7 +1851,7 @@ cudaError_t multi_axpy_norm_b(const double* V, long long ldv, int k, const doubl
                               long long n, double* part, int G, cudaStream_t st) {
   return launch_multi_axpy_norm_fp64(V, ldv, k, coef, sign, w, n, part, G, st);
 }
-// CGS2 (orth = 0) in three passes over V, for a double-float (float2) or IEEE FP64 (double) basis.
+// CGS2 with an explicit second pass in three passes over V, for a double-float (float2) or IEEE FP64 (double) basis.
 template <typename B>
 gs_status cgs2_fused(gs_ctx* c, const B* V, int j, double* h1, double* h2, double* nrm) {
   const long long N = c->N;
@@ -1869,13 +1870,13 @@ gs_status cgs2_fused(gs_ctx* c, const B* V, int j, double* h1, double* h2, doubl
 // coefficients h1 + V^T (w - V h1): the second pass's dots are replaced by G h1, so V is read twice
 // instead of three times and the FP64 work is 3 instead of 4 FMAs per basis entry.
 template <typename B>
-gs_status cgs_gram(gs_ctx* c, const B* V, int j, double* coef, double* nrm) {
+gs_status cgs_gram(gs_ctx* c, const B* V, int j, double* coef, double* nrm, double* zero = nullptr) {
   const long long N = c->N;
   const int m = c->opt.restart;
   const int g2 = std::min(c->GF, 3 * 152);  // one wave of the two-vector dots (3 CTAs per SM)
   KL(K_DOTS, dots_strip2(V, N, j + 1, c->w, N, c->part, g2, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, 2 * (j + 1), g2, c->gsc, c->st));
-  KL(K_DOTS, launch_gram_correct(c->gsc, c->gram, m + 1, j + 1, coef, c->st));
+  KL(K_DOTS, launch_gram_correct(c->gsc, c->gram, m + 1, j + 1, coef, zero, c->st));
   KL(K_AXPY, multi_axpy_norm_b(V, N, j + 1, coef, -1.0, c->w, N, c->part, c->GA, c->st));
   KL(K_DOTS, launch_reduce_partials(c->part, 1, c->GA, nrm, c->st));
   return GS_OK;
@@ -1932,7 +1933,7 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
       // classical Gram-Schmidt: h = V^T w (with |w|^2 in the same pass), w -= V h (with the new
       // |w|^2 in the same pass); a second pass when |w| fell below 1/sqrt(2) of its value
-      // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, orth = 0)
+      // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, explicit or through the Gram matrix)
       double hn;
       if (c->opt.orth == 2 && j + 1 <= kFusedGsMax) {
         if (dfk)
@@ -2358,7 +2359,7 @@ gs_status report(gs_status s, const std::string& why) { return fail(s, why); }
 gs_status slot_begin(gs_ctx* c, const double* b, double* x, double tol) {
   if (!c || !b || !x) return fail(GS_EINVAL, "NULL argument");
   if (!(tol > 0.0)) return fail(GS_EINVAL, "tol must be > 0");
-  if (c->opt.orth != 0) return fail(GS_EINVAL, "batched solves use classical Gram-Schmidt twice (orth = 0)");
+  if (c->opt.orth == 1) return fail(GS_EINVAL, "batched solves need a fixed number of Gram-Schmidt passes (orth != 1)");
   if (c->prof) return fail(GS_EINVAL, "kernel profiling is on for this context");
   KState& k = c->ks;
   const int m = c->opt.restart;
@@ -2472,7 +2473,12 @@ gs_status slot_record_post(gs_ctx* c, double* gather_dev) {
       double* nrm = sl_nrm(c);
       CKS(c->fp32 ? sl_cast_out<float>(c, v, Zj) : sl_cast_out<double>(c, v, Zj));
       CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
-      if (j + 1 <= kFusedGsMax) {
+      if (c->opt.orth == 2 && j + 1 <= kFusedGsMax) {  // coefficients in h1, zeros in h2
+        if (dfk)
+          CKS(cgs_gram(c, (const float2*)Vdf, j, h1, nrm, h2));
+        else
+          CKS(cgs_gram(c, (const double*)c->V, j, h1, nrm, h2));
+      } else if (j + 1 <= kFusedGsMax) {
         if (dfk)
           CKS(cgs2_fused(c, (const float2*)Vdf, j, h1, h2, nrm));
         else
@@ -2980,7 +2986,7 @@ gs_status gs_batch_solve(gs_ctx* const* ctxs, int count, const double* const* rh
   bool engine_ok = count > 1;
   int max_restart = 1;
   for (int i = 0; i < count && engine_ok; ++i) {
-    if (!ctxs[i] || ctxs[i]->opt.orth != 0 || ctxs[i]->prof) engine_ok = false;
+    if (!ctxs[i] || ctxs[i]->opt.orth == 1 || ctxs[i]->prof) engine_ok = false;
     for (int q = 0; q < i && engine_ok; ++q) engine_ok = ctxs[q] != ctxs[i];
     if (engine_ok) max_restart = std::max(max_restart, ctxs[i]->opt.restart);
   }

@@ -474,7 +474,7 @@ cudaError_t launch_dots_strip2_fp64(const double* V, long long ldv, int k, const
 // exact arithmetic c is the CGS2 coefficient vector h1 + V^T (w - V h1); the update w - V c follows.
 // One block; k <= 64.
 struct GramCorrK {
-  struct Args { const double* d; double* G; int ldg; int k; double* c; };
+  struct Args { const double* d; double* G; int ldg; int k; double* c; double* zero; };
   static constexpr int THREADS = 64, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int, int) {
     const int i = threadIdx.x, k = a.k;
@@ -489,12 +489,14 @@ struct GramCorrK {
       for (int l = 0; l < k; ++l) s = fma(a.G[(long long)i * a.ldg + l], a.d[l], s);
       const double h = a.d[i];
       a.c[i] = h + (h - s);
+      if (a.zero) a.zero[i] = 0.0;  // a second coefficient slot that callers add to c
     }
   }
 };
-cudaError_t launch_gram_correct(const double* d, double* G, int ldg, int k, double* c, cudaStream_t st) {
+cudaError_t launch_gram_correct(const double* d, double* G, int ldg, int k, double* c, double* zero,
+                                cudaStream_t st) {
   if (k < 1 || k > 64) return cudaErrorInvalidValue;
-  return submit<GramCorrK>({d, G, ldg, k, c}, 1, 0, st);
+  return submit<GramCorrK>({d, G, ldg, k, c, zero}, 1, 0, st);
 }
 
 template <typename B>

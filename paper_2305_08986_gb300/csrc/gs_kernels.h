@@ -203,7 +203,8 @@ cudaError_t launch_dots_strip2_df(const float2* V, long long ldv, int k, const d
                                   int G, cudaStream_t st);
 cudaError_t launch_dots_strip2_fp64(const double* V, long long ldv, int k, const double* w, long long n, double* part,
                                     int G, cudaStream_t st);
-cudaError_t launch_gram_correct(const double* d, double* G, int ldg, int k, double* c, cudaStream_t st);
+cudaError_t launch_gram_correct(const double* d, double* G, int ldg, int k, double* c, double* zero,
+                                cudaStream_t st);
 // k dot products V[i] . w plus w . w in row k of part (rows 0..k)
 cudaError_t launch_dots_norm_partial(const double* V, long long ldv, int k, const double* w, long long n,
                                      double* part, int G, cudaStream_t st);

@@ -6,7 +6,7 @@ import pytest
 def test_krylov_bytes_closed_form():
     import bench
     n, K = 1000, 7
-    dots, axpy, fd, fa = bench.krylov_bytes(n, K, restart=50)
+    dots, axpy, fd, fa = bench.krylov_bytes(n, K, restart=50, form="explicit")
     # iteration k orthogonalises against k + 1 rows: the first pass reads them and w once
     assert dots == sum((k + 2) * n * 8 for k in range(K)) == n * 8 * (K * (K + 1) // 2 + K)
     # two update passes (rows + w read + w written) and the new basis vector (w read, v written)
@@ -14,6 +14,20 @@ def test_krylov_bytes_closed_form():
     # FMAs: one per row entry for the dots, two for the fused update + dots, one (+ the norm) last
     assert fd == sum((k + 1) * n for k in range(K))
     assert fa == sum((3 * (k + 1) + 1) * n for k in range(K))
+
+
+def test_krylov_bytes_gram_form():
+    import bench
+    n, K = 1000, 7
+    dots, axpy, fd, fa = bench.krylov_bytes(n, K, restart=50)
+    # one dot pass (rows + w) with two dots per row entry, one update pass (rows + w read + w written)
+    assert dots == sum((k + 2) * n * 8 for k in range(K))
+    assert axpy == sum((k + 3) * n * 8 + 2 * n * 8 for k in range(K))
+    assert fd == sum(2 * (k + 1) * n for k in range(K))
+    assert fa == sum((k + 2) * n for k in range(K))
+    # 3 instead of 4 FMAs per basis entry (plus the norm)
+    e = bench.krylov_bytes(n, K, restart=50, form="explicit")
+    assert fd + fa - K * n == pytest.approx(0.75 * (e[2] + e[3] - K * n))
 
 
 def test_krylov_bytes_restart_resets_the_row_count():

@@ -157,6 +157,25 @@ def test_engine_options_in_one_batch():
         _same(refs[i], x, res[i]["iterations"], res[i]["rel_residual"], res[i]["status"])
 
 
+@pytest.mark.parametrize("orth", [3, 2])
+def test_engine_gram_schmidt_forms(orth):
+    """The explicit CGS2 (orth = 3) and the Gram-matrix form (orth = 2, the default) in the engine:
+    a 2D and a 3D solve, alone and together, give the same bits, and agree with gs_solve to the
+    solver tolerance."""
+    from paper_2305_08986_gb300 import gs
+    probs = [_problems()[1], _problems()[2]]
+    refs = [_engine_alone(p, orth=orth) for p in probs]
+    setups = [_setup(p, orth=orth) for p in probs]
+    eng = gs.Engine(2)
+    for i, (s, b, x) in enumerate(setups):
+        assert eng.add(s, b, x, TOL, tag=i)
+    res = {r["tag"]: r for r in eng.run()}
+    for i, (s, b, x) in enumerate(setups):
+        _same(refs[i], x, res[i]["iterations"], res[i]["rel_residual"], res[i]["status"])
+        xa, ita, rra, sta = _alone(probs[i], orth=orth)
+        _close((xa, ita, rra, sta), x, res[i]["iterations"], res[i]["rel_residual"], res[i]["status"])
+
+
 def test_engine_rejects_selective_reorthogonalisation():
     from paper_2305_08986_gb300 import gs
     s, b, x = _setup(_problems()[0], orth=1)
