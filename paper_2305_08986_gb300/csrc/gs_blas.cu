@@ -514,10 +514,7 @@ cudaError_t launch_dots_strip_fp64(const double* V, long long ldv, int k, const 
   return launch_dots_strip<double>(V, ldv, k, w, n, part, G, st);
 }
 
-// w <- w + sign * sum_i coef[i] V[i] (sum carried in the basis arithmetic), partial sums of |w|^2.
-// The sum over the rows runs in four interleaved accumulators (row i into accumulator i mod 4,
-// combined as (a0 + a1) + (a2 + a3)): four independent FMA chains per element keep the FP64 pipe
-// busy where one chain would wait on each FMA's latency.
+// w <- w + sign * sum_i coef[i] V[i] (sum carried in the basis arithmetic), partial sums of |w|^2
 template <typename B>
 struct MultiAxpyNormBK {
   using O = BasisOps<B>;
@@ -536,19 +533,17 @@ struct MultiAxpyNormBK {
     double s = 0.0;
     GS_FOR(e, a.n) {
       const double we = w[e];
-      B acc[4] = {O::zero(), O::zero(), O::zero(), O::zero()};
+      B acc = O::zero();
       int i = 0;
       for (; i + 8 <= k; i += 8) {  // eight basis loads in flight per thread
         B v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = V[(i + u) * ldv + e];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) O::fma(acc[u & 3], cs2[i + u], v[u]);
+        for (int u = 0; u < 8; ++u) O::fma(acc, cs2[i + u], v[u]);
       }
-#pragma unroll
-      for (int u = 0; u < 7; ++u)  // the last k mod 8 rows (i is a multiple of 8, so row i + u -> u mod 4)
-        if (i + u < k) O::fma(acc[u & 3], cs2[i + u], V[(i + u) * ldv + e]);
-      const double r = we + ((O::join(acc[0]) + O::join(acc[1])) + (O::join(acc[2]) + O::join(acc[3])));
+      for (; i < k; ++i) O::fma(acc, cs2[i], V[i * ldv + e]);
+      const double r = we + O::join(acc);
       w[e] = r;
       s += r * r;
     }
