@@ -470,8 +470,8 @@ gs_status plan(const gs_mesh* m, int L, const double* eta, gs_ctx* c, const doub
   c->mono = c->opt.precond_kind == 1;
   c->hmfree.clear();
   if (c->mono && c->opt.deflate == 1) return fail(GS_EINVAL, "deflation applies to the block-triangular preconditioner");
-  if (c->opt.corrector && (dim != 2 || c->opt.deflate == 1))
-    return fail(GS_EINVAL, "the corrector stage is built for 2D meshes without deflation");
+  if (c->opt.corrector && c->opt.deflate == 1)
+    return fail(GS_EINVAL, "the corrector stage is built without deflation");
   if (c->mono && c->opt.coarse_mode != 1) {
     c->hmfree = c->hfree;
     for (long long q = 0; q < C0.Np; ++q)
@@ -827,7 +827,8 @@ TileArgs<T> tile_args(const Level& lv) {
     a.rho = (T)lv.rho;
     a.ihx = (T)(1.0 / lv.h[0]);
     a.ihy = (T)(1.0 / lv.h[1]);
-    a.wq = (T)(lv.h[0] * lv.h[1]);
+    a.ihz = (T)(1.0 / lv.h[2]);
+    a.wq = (T)(lv.g.dim == 3 ? lv.h[0] * lv.h[1] * lv.h[2] : lv.h[0] * lv.h[1]);
   }
   return a;
 }
@@ -978,39 +979,56 @@ gs_status plap_lanczos(gs_ctx* c, int l) {
 }
 
 // host assembly of the dense coarse matrix on its free unknowns (same closed-form 1D matrices)
-// Corrector stage: the cell's rho (C + S) block (component-diagonal, 9 x 9 per component) added to
-// the dense coarse matrix, by the 3 x 3 Gauss rule of the kernels (host copy of the 1D matrices).
-void add_conv_cell(const Level& lv, int i, int j, const std::vector<int>& map, int nf, std::vector<double>& A) {
+// Corrector stage: the cell's rho (C + S) block (component-diagonal, 3^d x 3^d per component) added
+// to the dense coarse matrix, by the 3-point Gauss rule per axis of the kernels (host copy of the
+// 1D matrices): entry (p, q) = rho sum_g W_g (phi_p(g) adv_q(g) + r_K adv_p(g) adv_q(g)),
+// adv_q = v° . grad phi_q.
+void add_conv_cell(const Level& lv, int dim, int i, int j, int k, const std::vector<int>& map, int nf,
+                   std::vector<double>& A) {
   const double s = 0.38729833462074168852;
   const double Phi[3][3] = {{0.3 + s, 0.4, 0.3 - s}, {0.0, 1.0, 0.0}, {0.3 - s, 0.4, 0.3 + s}};
   const double Dq[3][3] = {{-1.0 - 4.0 * s, 8.0 * s, 1.0 - 4.0 * s}, {-1.0, 0.0, 1.0}, {-1.0 + 4.0 * s, -8.0 * s, 1.0 + 4.0 * s}};
   const double w[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
-  const double hx = lv.h[0], hy = lv.h[1];
-  const long long nv0 = 2 * lv.n[0] + 1;
-  const long long cc = i + (long long)lv.n[0] * j;
-  long long gn[9];
-  for (int q = 0; q < 9; ++q) gn[q] = (2 * i + q % 3) + nv0 * (2 * j + q / 3);
-  double vx[9] = {0}, vy[9] = {0};
-  for (int q = 0; q < 9; ++q)
-    for (int jn = 0; jn < 9; ++jn) {
-      const double ph = Phi[q % 3][jn % 3] * Phi[q / 3][jn / 3];
-      vx[q] += ph * lv.hvc[gn[jn]];
-      vy[q] += ph * lv.hvc[lv.Nv + gn[jn]];
+  const int nb = dim == 2 ? 9 : 27;  // nodes of the cell = Gauss points of the cell
+  const long long nv0 = 2 * lv.n[0] + 1, nv1 = 2 * lv.n[1] + 1;
+  const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+  double jac = 1.0;
+  for (int ax = 0; ax < dim; ++ax) jac *= lv.h[ax];
+  auto idx = [](int q, int ax) { return ax == 0 ? q % 3 : (ax == 1 ? (q / 3) % 3 : q / 9); };
+  long long gn[27];
+  for (int q = 0; q < nb; ++q)
+    gn[q] = (2 * i + idx(q, 0)) + nv0 * ((2 * j + idx(q, 1)) + nv1 * (dim == 3 ? 2 * k + idx(q, 2) : 0));
+  double vq[3][27] = {};
+  for (int g = 0; g < nb; ++g)
+    for (int jn = 0; jn < nb; ++jn) {
+      double ph = 1.0;
+      for (int ax = 0; ax < dim; ++ax) ph *= Phi[idx(g, ax)][idx(jn, ax)];
+      for (int b = 0; b < dim; ++b) vq[b][g] += ph * lv.hvc[b * lv.Nv + gn[jn]];
     }
-  const double r = lv.hrk[cc];
-  for (int p = 0; p < 9; ++p)
-    for (int qn = 0; qn < 9; ++qn) {
-      double v = 0.0;
-      for (int q = 0; q < 9; ++q) {
-        const int qa = q % 3, qb = q / 3;
-        const double W = w[qa] * w[qb] * hx * hy;
-        const double phi_p = Phi[qa][p % 3] * Phi[qb][p / 3];
-        const double adv_p = vx[q] * Dq[qa][p % 3] * Phi[qb][p / 3] / hx + vy[q] * Phi[qa][p % 3] * Dq[qb][p / 3] / hy;
-        const double adv_q = vx[q] * Dq[qa][qn % 3] * Phi[qb][qn / 3] / hx + vy[q] * Phi[qa][qn % 3] * Dq[qb][qn / 3] / hy;
-        v += W * (phi_p * adv_q + r * adv_p * adv_q);
+  double phi[27][27], adv[27][27], W[27];
+  for (int g = 0; g < nb; ++g) {
+    W[g] = jac;
+    for (int ax = 0; ax < dim; ++ax) W[g] *= w[idx(g, ax)];
+    for (int p = 0; p < nb; ++p) {
+      double ph = 1.0, ad = 0.0;
+      for (int ax = 0; ax < dim; ++ax) ph *= Phi[idx(g, ax)][idx(p, ax)];
+      for (int ax = 0; ax < dim; ++ax) {
+        double t = vq[ax][g] * Dq[idx(g, ax)][idx(p, ax)] / lv.h[ax];
+        for (int o = 0; o < dim; ++o)
+          if (o != ax) t *= Phi[idx(g, o)][idx(p, o)];
+        ad += t;
       }
+      phi[p][g] = ph;
+      adv[p][g] = ad;
+    }
+  }
+  const double r = lv.hrk[cc];
+  for (int p = 0; p < nb; ++p)
+    for (int qn = 0; qn < nb; ++qn) {
+      double v = 0.0;
+      for (int g = 0; g < nb; ++g) v += W[g] * (phi[p][g] * adv[qn][g] + r * adv[p][g] * adv[qn][g]);
       v *= lv.rho;
-      for (int a = 0; a < 2; ++a) {
+      for (int a = 0; a < dim; ++a) {
         const int row = map[a * lv.Nv + gn[p]], col = map[a * lv.Nv + gn[qn]];
         if (row >= 0 && col >= 0) A[(size_t)row * nf + col] += v;
       }
@@ -1080,7 +1098,7 @@ void assemble_coarse(gs_ctx* c, std::vector<double>& A) {
                 A[(size_t)row * nf + col] += v;
               }
             }
-        if (lv.conv) add_conv_cell(lv, i, j, map, nf, A);
+        if (lv.conv) add_conv_cell(lv, dim, i, j, k, map, nf, A);
       }
 }
 
@@ -2870,20 +2888,25 @@ namespace {
 // Brooks-Hughes streamline parameter r_K per cell: |v°| at the cell's centre node, h_K the cell
 // diameter, Pe = rho |v°| h_K / (2 eta_K p1), r_K = h_K / (2 |v°| p1) (coth Pe - 1 / Pe), p1 = 2,
 // and r_K = 0 where Pe < 1.
-void streamline_parameters(Level& lv, double rho) {
-  const long long nv0 = 2 * lv.n[0] + 1;
-  const double hK = std::sqrt(lv.h[0] * lv.h[0] + lv.h[1] * lv.h[1]);
+void streamline_parameters(Level& lv, int dim, double rho) {
+  const long long nv0 = 2 * lv.n[0] + 1, nv1 = 2 * lv.n[1] + 1;
+  double h2 = 0.0;
+  for (int ax = 0; ax < dim; ++ax) h2 += lv.h[ax] * lv.h[ax];
+  const double hK = std::sqrt(h2);  // the cell diameter
   lv.hrk.assign(lv.Nc, 0.0);
-  for (int j = 0; j < lv.n[1]; ++j)
-    for (int i = 0; i < lv.n[0]; ++i) {
-      const long long cc = i + (long long)lv.n[0] * j;
-      const long long ctr = (2 * i + 1) + nv0 * (2 * j + 1);
-      const double vn = std::sqrt(lv.hvc[ctr] * lv.hvc[ctr] + lv.hvc[lv.Nv + ctr] * lv.hvc[lv.Nv + ctr]);
-      const double eta = lv.heta[cc];
-      if (!(vn > 0.0) || !(eta > 0.0)) continue;
-      const double pe = rho * vn * hK / (2.0 * eta * 2.0);
-      if (pe >= 1.0) lv.hrk[cc] = hK / (2.0 * vn * 2.0) * (1.0 / std::tanh(pe) - 1.0 / pe);
-    }
+  for (int k = 0; k < lv.n[2]; ++k)
+    for (int j = 0; j < lv.n[1]; ++j)
+      for (int i = 0; i < lv.n[0]; ++i) {
+        const long long cc = i + (long long)lv.n[0] * (j + (long long)lv.n[1] * k);
+        const long long ctr = (2 * i + 1) + nv0 * ((2 * j + 1) + nv1 * (dim == 3 ? 2 * k + 1 : 0));
+        double v2 = 0.0;
+        for (int b = 0; b < dim; ++b) v2 += lv.hvc[b * lv.Nv + ctr] * lv.hvc[b * lv.Nv + ctr];
+        const double vn = std::sqrt(v2);
+        const double eta = lv.heta[cc];
+        if (!(vn > 0.0) || !(eta > 0.0)) continue;
+        const double pe = rho * vn * hK / (2.0 * eta * 2.0);
+        if (pe >= 1.0) lv.hrk[cc] = hK / (2.0 * vn * 2.0) * (1.0 / std::tanh(pe) - 1.0 / pe);
+      }
 }
 
 template <typename T>
@@ -2913,7 +2936,6 @@ extern "C" {
 gs_status gs_set_corrector(gs_ctx* c, const double* vcirc, double rho) {
   if (!c) return fail(GS_EINVAL, "NULL argument");
   if (!c->opt.corrector) return fail(GS_EINVAL, "the context was created without gs_options.corrector = 1");
-  if (c->dim != 2) return fail(GS_EINVAL, "the corrector stage is built for 2D meshes");
   if (vcirc && !(rho >= 0.0 && std::isfinite(rho))) return fail(GS_EINVAL, "rho must be finite and >= 0");
   const int L = c->L;
   if (vcirc) {
@@ -2921,19 +2943,22 @@ gs_status gs_set_corrector(gs_ctx* c, const double* vcirc, double rho) {
     for (long long i = 0; i < F.nu; ++i)
       if (!std::isfinite(vcirc[i])) return fail(GS_EINVAL, "v° is not finite");
     F.hvc.assign(vcirc, vcirc + F.nu);
-    for (int l = L - 2; l >= 0; --l) {  // injection: coarse node (I, J) takes fine node (2 I, 2 J)
+    const int dim = c->dim;
+    for (int l = L - 2; l >= 0; --l) {  // injection: coarse node (I, J, K) takes fine node (2 I, 2 J, 2 K)
       Level& cl = c->lv[l];
       const Level& fl = c->lv[l + 1];
-      const long long cnv0 = 2 * cl.n[0] + 1, fnv0 = 2 * fl.n[0] + 1;
+      const long long cnv0 = 2 * cl.n[0] + 1, cnv1 = 2 * cl.n[1] + 1, cnv2 = dim == 3 ? 2 * cl.n[2] + 1 : 1;
+      const long long fnv0 = 2 * fl.n[0] + 1, fnv1 = 2 * fl.n[1] + 1;
       cl.hvc.assign(cl.nu, 0.0);
-      for (int a = 0; a < 2; ++a)
-        for (long long J = 0; J < 2 * cl.n[1] + 1; ++J)
-          for (long long I = 0; I < cnv0; ++I)
-            cl.hvc[a * cl.Nv + I + cnv0 * J] = fl.hvc[a * fl.Nv + 2 * I + fnv0 * (2 * J)];
+      for (int a = 0; a < dim; ++a)
+        for (long long K = 0; K < cnv2; ++K)
+          for (long long J = 0; J < cnv1; ++J)
+            for (long long I = 0; I < cnv0; ++I)
+              cl.hvc[a * cl.Nv + I + cnv0 * (J + cnv1 * K)] = fl.hvc[a * fl.Nv + 2 * I + fnv0 * (2 * J + fnv1 * 2 * K)];
     }
     for (int l = 0; l < L; ++l) {
       Level& lv = c->lv[l];
-      streamline_parameters(lv, rho);
+      streamline_parameters(lv, dim, rho);
       lv.conv = 1;
       lv.rho = rho;
       CK(cudaMemcpyAsync(lv.vc64, lv.hvc.data(), sizeof(double) * lv.nu, cudaMemcpyHostToDevice, c->st));

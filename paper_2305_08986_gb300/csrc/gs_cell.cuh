@@ -324,6 +324,101 @@ __device__ __forceinline__ void cell_conv2(const T (&u)[2][9], const T (&vc)[2][
   }
 }
 
+// ---- corrector stage in 3D: the same terms at the 3 x 3 x 3 Gauss points ---------------------------
+// out = (M along axis AX) in on a 3 x 3 x 3 array (x fastest); M = Phi or Dq (TR: transposed).
+template <int AX, bool TR, bool DER, typename T>
+__device__ __forceinline__ void gsweep3(const T* __restrict__ in, T* __restrict__ out) {
+#pragma unroll
+  for (int o2 = 0; o2 < 3; ++o2)
+#pragma unroll
+    for (int o1 = 0; o1 < 3; ++o1)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const double m = TR ? (DER ? GaussQ2::dq(q, p) : GaussQ2::phi(q, p)) : (DER ? GaussQ2::dq(p, q) : GaussQ2::phi(p, q));
+          if (m == 0.0) continue;
+          const int a = AX == 0 ? q : o1, b = AX == 0 ? o1 : (AX == 1 ? q : o2), c = AX == 2 ? q : o2;
+          acc += T(m) * in[a + 3 * b + 9 * c];
+        }
+        const int a = AX == 0 ? p : o1, b = AX == 0 ? o1 : (AX == 1 ? p : o2), c = AX == 2 ? p : o2;
+        out[a + 3 * b + 9 * c] = acc;
+      }
+}
+
+// (Phi or Dq along each axis) of a nodal 3 x 3 x 3 array: DX, DY, DZ select Dq on that axis
+template <bool DX, bool DY, bool DZ, bool TR, typename T>
+__device__ __forceinline__ void gsweep3_all(const T* __restrict__ in, T* __restrict__ out, T* __restrict__ tmp) {
+  gsweep3<0, TR, DX>(in, out);
+  gsweep3<1, TR, DY>(out, tmp);
+  gsweep3<2, TR, DZ>(tmp, out);
+}
+
+// y += rho (C + S) u (CONV = 1) or rho (S + (C + C^T) / 2) u (CONV = 2) for one velocity component in
+// the rotated frame of the caller: u, and v° component q (the component along logical axis q), are
+// read from shared-memory windows at x[o0[i] + o1[j] + o2[k]]; ih[q] = 1 / h along logical axis q;
+// jac = h_x h_y h_z.  Sum factorisation at the 3 x 3 x 3 Gauss points as in cell_conv2; the v°
+// interpolation is redone for the back sweeps instead of keeping three Gauss-point arrays alive.
+template <int CONV, typename T>
+__device__ __forceinline__ void cell_conv3(const T* u_, const T* const (&v_)[3], const int* o0, const int* o1,
+                                           const int* o2, T rho, T rK, const T (&ih)[3], T jac, T (&y)[27]) {
+  T uu[27], f[27], g[27], t[27], adv[27];
+  auto load = [&](const T* base, T (&dst)[27]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dst[i + 3 * j + 9 * k] = base[o0[i] + o1[j] + o2[k]];
+  };
+  load(u_, uu);
+#pragma unroll
+  for (int q = 0; q < 27; ++q) adv[q] = T(0);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    T vv[27];
+    load(v_[ax], vv);
+    gsweep3_all<false, false, false, false>(vv, f, t);  // v°_ax at the Gauss points
+    if (ax == 0) gsweep3_all<true, false, false, false>(uu, g, t);
+    else if (ax == 1) gsweep3_all<false, true, false, false>(uu, g, t);
+    else gsweep3_all<false, false, true, false>(uu, g, t);  // d u / d x_ax (reference)
+#pragma unroll
+    for (int q = 0; q < 27; ++q) adv[q] += f[q] * g[q] * ih[ax];
+  }
+  const T kc = CONV == 1 ? rho : T(0.5) * rho;
+  if (CONV == 2) gsweep3_all<false, false, false, false>(uu, g, t);  // u at the Gauss points
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int q = a + 3 * b + 9 * c;
+        const T W = T(GaussQ2::w(a) * GaussQ2::w(b) * GaussQ2::w(c)) * jac;
+        f[q] = kc * W * adv[q];                                  // C u at the Gauss points
+        T sq = rho * rK * W * adv[q];                             // streamline source
+        if (CONV == 2) sq += T(0.5) * rho * W * g[q];             // C^T u
+        adv[q] = sq;
+      }
+  gsweep3_all<false, false, false, true>(f, g, t);              // (Phi^T x Phi^T x Phi^T)
+#pragma unroll
+  for (int q = 0; q < 27; ++q) y[q] += g[q];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {  // (v° . grad phi_i) terms, axis by axis
+    T vv[27];
+    load(v_[ax], vv);
+    gsweep3_all<false, false, false, false>(vv, f, t);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) f[q] = f[q] * adv[q] * ih[ax];
+    if (ax == 0) gsweep3_all<true, false, false, true>(f, g, t);
+    else if (ax == 1) gsweep3_all<false, true, false, true>(f, g, t);
+    else gsweep3_all<false, false, true, true>(f, g, t);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) y[q] += g[q];
+  }
+}
+
 // ---- 3D cell operators reading their input nodes from a shared-memory window ----------------------
 // x_a points to the cell's local node (0, 0, 0) of component a in the window; local node (i, j, k)
 // sits at x_a[i + ro[j] + po[k]] (row and plane offsets of the cell, which absorb any skew of the

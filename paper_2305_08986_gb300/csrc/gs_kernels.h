@@ -34,11 +34,12 @@ struct TileArgs {
   int use_d;
   int raw;        // 1: no constraint elimination (operator of the unconstrained forms)
   int* err;       // device word set nonzero when a bounded wait of the kernel gave up (may be NULL)
-  // corrector stage (2D): conv = 1 adds rho (C + S) to A, conv = 2 the symmetric part of that term
+  // corrector stage: conv = 1 adds rho (C + S) to A, conv = 2 the symmetric part of that term
   int conv;
   const T* vc;    // the convective field v° on this level (d N_v entries, component-blocked)
   const T* rk;    // streamline parameter r_K per cell
-  T rho, ihx, ihy, wq;  // density, 1 / h_x, 1 / h_y, h_x h_y
+  T rho, ihx, ihy, wq;  // density, 1 / h_x, 1 / h_y, h_x h_y (3D: h_x h_y h_z)
+  T ihz;                // 1 / h_z (3D)
   int tiles[3];
   T* part;        // 3D FP32: per-tile partial sums of the nodes on shared tile faces (gs_tile.cu,
                   // tile3nh_body; NULL: the halo tiles are used)

@@ -611,9 +611,84 @@ __global__ void k_diag_conv(Geom g, const double* __restrict__ vc, const double*
   diag[node] += rho * acc;
   diag[g.Nv + node] += rho * acc;
 }
+// 3D: the same sum over the (up to 8) active cells around the node, v° interpolated to the 27 Gauss
+// points of each cell by sum factorisation (one axis at a time).
+__global__ void k_diag_conv3(Geom g, const double* __restrict__ vc, const double* __restrict__ rk, double rho,
+                             double* __restrict__ diag) {
+  const long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (node >= g.Nv) return;
+  const int I = (int)(node % g.nv[0]);
+  const int J = (int)((node / g.nv[0]) % g.nv[1]);
+  const int K = (int)(node / ((long long)g.nv[0] * g.nv[1]));
+  if (g.vmask ? g.vmask[node] != 0 : face_constrained(g, I, J, K)) return;
+  const int X[3] = {I, J, K};
+  const double jac = g.h[0] * g.h[1] * g.h[2];
+  double acc = 0.0;
+  for (int cs = 0; cs < 8; ++cs) {
+    int cl[3], ll[3];
+    bool ok = true;
+    for (int ax = 0; ax < 3; ++ax) {
+      const int side = (cs >> ax) & 1;  // 0: the cell at or above the node, 1: the cell below an even node
+      const int c = (X[ax] % 2 == 0) ? (side == 0 ? X[ax] / 2 : X[ax] / 2 - 1) : (side == 0 ? X[ax] / 2 : -1);
+      if (c < 0 || c >= g.n[ax]) ok = false;
+      cl[ax] = c;
+      ll[ax] = X[ax] - 2 * c;
+    }
+    if (!ok) continue;
+    const long long cell = cl[0] + (long long)g.n[0] * (cl[1] + (long long)g.n[1] * cl[2]);
+    if (cell_void(g, cell)) continue;
+    double v[3][27];
+    for (int b = 0; b < 3; ++b) {
+      double a0[27], a1[27];
+      for (int jc = 0; jc < 3; ++jc)  // nodal values of component b
+        for (int jb = 0; jb < 3; ++jb)
+          for (int ja = 0; ja < 3; ++ja)
+            a0[ja + 3 * jb + 9 * jc] =
+                vc[b * g.Nv + (2 * cl[0] + ja) + (long long)g.nv[0] * ((2 * cl[1] + jb) + (long long)g.nv[1] * (2 * cl[2] + jc))];
+      for (int jc = 0; jc < 3; ++jc)  // along x
+        for (int jb = 0; jb < 3; ++jb)
+          for (int qa = 0; qa < 3; ++qa) {
+            double t = 0.0;
+            for (int ja = 0; ja < 3; ++ja) t += GaussQ2::phi(qa, ja) * a0[ja + 3 * jb + 9 * jc];
+            a1[qa + 3 * jb + 9 * jc] = t;
+          }
+      for (int jc = 0; jc < 3; ++jc)  // along y
+        for (int qb = 0; qb < 3; ++qb)
+          for (int qa = 0; qa < 3; ++qa) {
+            double t = 0.0;
+            for (int jb = 0; jb < 3; ++jb) t += GaussQ2::phi(qb, jb) * a1[qa + 3 * jb + 9 * jc];
+            a0[qa + 3 * qb + 9 * jc] = t;
+          }
+      for (int qc = 0; qc < 3; ++qc)  // along z
+        for (int qb = 0; qb < 3; ++qb)
+          for (int qa = 0; qa < 3; ++qa) {
+            double t = 0.0;
+            for (int jc = 0; jc < 3; ++jc) t += GaussQ2::phi(qc, jc) * a0[qa + 3 * qb + 9 * jc];
+            v[b][qa + 3 * qb + 9 * qc] = t;
+          }
+    }
+    const double r = rk[cell];
+    for (int qc = 0; qc < 3; ++qc)
+      for (int qb = 0; qb < 3; ++qb)
+        for (int qa = 0; qa < 3; ++qa) {
+          const int q = qa + 3 * qb + 9 * qc;
+          const double W = GaussQ2::w(qa) * GaussQ2::w(qb) * GaussQ2::w(qc) * jac;
+          const double pa = GaussQ2::phi(qa, ll[0]), pb = GaussQ2::phi(qb, ll[1]), pc = GaussQ2::phi(qc, ll[2]);
+          const double phi = pa * pb * pc;
+          const double adv = v[0][q] * GaussQ2::dq(qa, ll[0]) * pb * pc / g.h[0] +
+                             v[1][q] * pa * GaussQ2::dq(qb, ll[1]) * pc / g.h[1] +
+                             v[2][q] * pa * pb * GaussQ2::dq(qc, ll[2]) / g.h[2];
+          acc += W * (phi * adv + r * adv * adv);
+        }
+  }
+  for (int a = 0; a < 3; ++a) diag[a * g.Nv + node] += rho * acc;
+}
 cudaError_t launch_diag_conv(const Geom& g, const double* vc, const double* rk, double rho, double* diag,
                              cudaStream_t st) {
-  if (g.dim != 2) return cudaErrorInvalidValue;
+  if (g.dim == 3) {
+    k_diag_conv3<<<nblk(g.Nv), TPB, 0, st>>>(g, vc, rk, rho, diag);
+    return launched(cudaGetLastError(), 1);
+  }
   k_diag_conv<<<nblk(g.Nv), TPB, 0, st>>>(g, vc, rk, rho, diag);
   return launched(cudaGetLastError(), 1);
 }

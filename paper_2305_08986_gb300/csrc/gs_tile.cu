@@ -71,7 +71,7 @@ struct Skew3 {
   static constexpr int OA = 1, OB = F ? 0 : 3, OP = F ? 236 : 229;  // output tile (VE = 15)
 };
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB, class S>
+template <typename T, int MODE, bool WA, bool WBT, bool WB, class S, int CONV = 0>
 struct Smem3 {
   using K = Skew3<T>;
   static constexpr bool NEED_U = WA || WB, WU = WA || WBT;
@@ -87,17 +87,18 @@ struct Smem3 {
   static constexpr int SP = WB ? S::PSZ : 0;                // pressure outputs
   static constexpr int SX = NEED_U ? 3 * WVA : 0;
   static constexpr int SPW = WBT ? PWV : 0;
-  static constexpr int TOTAL = SU + SP + SX + SPW;           // elements of T
+  static constexpr int SV = CONV ? 3 * WVA : 0;              // v° window (corrector stage)
+  static constexpr int TOTAL = SU + SP + SX + SPW + SV;      // elements of T
   static constexpr int FLAGS = NEED_U ? WV : 0;              // bytes
   static_assert(S::TC0 == 8 && S::TC1 == 8, "the skewed layouts assume 8 x 8 cells in x and y");
   static_assert(K::WP >= W * W1 + K::WA * ((W1 - 1) >> 2) && K::OP >= S::VE0 * S::VE1 + K::OA * ((S::VE1 - 1) >> 2),
                 "planes of the skewed layouts must not overlap");
 };
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB, class S>
+template <typename T, int MODE, bool WA, bool WBT, bool WB, class S, int CONV = 0>
 __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   using D = S;
-  using SM = Smem3<T, MODE, WA, WBT, WB, S>;
+  using SM = Smem3<T, MODE, WA, WBT, WB, S, CONV>;
   using K = Skew3<T>;
   constexpr bool NEED_U = SM::NEED_U, WU = SM::WU;
   constexpr int W = SM::W, WW = W * SM::W1, WV = SM::WV, WVA = SM::WVA, VSZA = SM::VSZA;
@@ -111,7 +112,8 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
   T* sp = su + SM::SU;
   T* sx = sp + SM::SP;
   T* spw = sx + SM::SX;
-  uint8_t* sflag = reinterpret_cast<uint8_t*>(spw + SM::SPW);
+  T* svc = spw + SM::SPW;  // v° window (CONV)
+  uint8_t* sflag = reinterpret_cast<uint8_t*>(svc + SM::SV);
   const Geom& g = A.g;
   const OpCoef<T>& c = A.c;
   const bool raw = A.raw != 0;
@@ -144,6 +146,10 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
       const int wi = widx(a, b, k);
 #pragma unroll
       for (int cc = 0; cc < 3; ++cc) cp_async_3d(sx + cc * WVA + wi, A.xu + cc * Nv + node, inr && !fcon);
+      if (CONV) {  // v° as given (constrained nodes included)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) cp_async_3d(svc + cc * WVA + wi, A.vc + cc * Nv + node, inr);
+      }
       sflag[i] = (vmasked && inr) ? g.vmask[node] : 0;
     }
   }
@@ -217,6 +223,13 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
         T yl[27];
         if (WA)
           cell_A3p(sx + pa[0] * WVA, sx + pa[1] * WVA, sx + pa[2] * WVA, o[0], o[1], o[2], yl, eta, mmK, km_l, ex_l);
+        if (CONV && WA) {  // corrector stage: rho (C + S) on the thread's own component
+          const T* const vl[3] = {svc + pa[0] * WVA, svc + pa[1] * WVA, svc + pa[2] * WVA};
+          const T ihl[3] = {pa[0] == 0 ? A.ihx : (pa[0] == 1 ? A.ihy : A.ihz),
+                            pa[1] == 0 ? A.ihx : (pa[1] == 1 ? A.ihy : A.ihz),
+                            pa[2] == 0 ? A.ihx : (pa[2] == 1 ? A.ihy : A.ihz)};
+          cell_conv3<CONV>(sx + pa[0] * WVA, vl, o[0], o[1], o[2], A.rho, A.rk[cell], ihl, A.wq, yl);
+        }
         if (WBT) {
           T pl[8];  // the cell's pressure nodes in the logical frame
 #pragma unroll
@@ -620,26 +633,26 @@ static cudaError_t launch_nh3(TileArgs<T> a, cudaStream_t st) {
   return submit<Fix3NHK<T, MODE>>(a, (nfix + 255) / 256, 0, st);
 }
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB, int C2>
+template <typename T, int MODE, bool WA, bool WBT, bool WB, int C2, int CONV = 0>
 struct TileK {
   using Args = TileArgs<T>;
   using S = TileShape3<C2>;
   static constexpr int THREADS = S::THREADS, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int blk, int) {
-    tile3d_body<T, MODE, WA, WBT, WB, S>(a, blk);
+    tile3d_body<T, MODE, WA, WBT, WB, S, CONV>(a, blk);
   }
 };
 
-template <typename T, int MODE, bool WA, bool WBT, bool WB, int C2>
+template <typename T, int MODE, bool WA, bool WBT, bool WB, int C2, int CONV = 0>
 static cudaError_t launch_shape(TileArgs<T> a, cudaStream_t st) {
   using S = TileShape3<C2>;
-  using SM = Smem3<T, MODE, WA, WBT, WB, S>;
+  using SM = Smem3<T, MODE, WA, WBT, WB, S, CONV>;
   a.tiles[0] = (a.g.n[0] + S::TC0 - 2) / (S::TC0 - 1);
   a.tiles[1] = (a.g.n[1] + S::TC1 - 2) / (S::TC1 - 1);
   a.tiles[2] = (a.g.n[2] + S::TC2 - 2) / (S::TC2 - 1);
   const size_t smem = sizeof(T) * SM::TOTAL + SM::FLAGS;
   const long long nblocks = (long long)a.tiles[0] * a.tiles[1] * a.tiles[2];
-  return submit<TileK<T, MODE, WA, WBT, WB, C2>>(a, nblocks, smem, st);
+  return submit<TileK<T, MODE, WA, WBT, WB, C2, CONV>>(a, nblocks, smem, st);
 }
 
 template <typename T, int DIM, int MODE, bool WA, bool WBT, bool WB>
@@ -664,6 +677,20 @@ template <typename T>
 cudaError_t launch_tile(int dim, int mode, int ops, TileArgs<T> a, cudaStream_t st) {
   if (mode == TILE_CHEB && ops != OPS_A) return cudaErrorInvalidValue;
   if (dim == 2) return launch_tile2d<T>(mode, ops, a, st);  // gs_tile2d.cu
+  if (a.conv && (ops & OPS_A)) {  // corrector stage: 8 x 8 x 4 halo tiles with the convection term
+    if (a.conv == 2) return mode == TILE_APPLY && ops == OPS_A ? launch_shape<T, TILE_APPLY, true, false, false, 4, 2>(a, st)
+                                                               : cudaErrorInvalidValue;
+    if (ops == OPS_A) {
+      if (mode == TILE_APPLY) return launch_shape<T, TILE_APPLY, true, false, false, 4, 1>(a, st);
+      if (mode == TILE_RESID) return launch_shape<T, TILE_RESID, true, false, false, 4, 1>(a, st);
+      return launch_shape<T, TILE_CHEB, true, false, false, 4, 1>(a, st);
+    }
+    if (ops == (OPS_A | OPS_BT | OPS_B)) {
+      if (mode == TILE_APPLY) return launch_shape<T, TILE_APPLY, true, true, true, 4, 1>(a, st);
+      if (mode == TILE_RESID) return launch_shape<T, TILE_RESID, true, true, true, 4, 1>(a, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   if constexpr (sizeof(T) == 4) {
     if (ops == OPS_A && a.part != nullptr) {  // FP32 velocity block: tiles without halo cells
       if (mode == TILE_APPLY) return launch_nh3<T, TILE_APPLY>(a, st);
