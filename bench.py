@@ -941,14 +941,21 @@ def run_corrector(args):
     gsbuild.build(verbose=False)
     from paper_2305_08986_gb300 import gs, inputs
     dev = torch.device("cuda", 0)
-    p = inputs.config_channel(**WORKLOAD)
+    if args.dim3:  # 3D: box inclusion (contrast 1e3, aligned with the coarsest mesh), do-nothing face z+
+        n3 = args.dim3
+        p = inputs.config_box_inclusion(3, (n3,) * 3, inputs.levels_for(n3, 3), 1e3, 100.0, seed=0,
+                                        faces=inputs.all_faces(3) & ~inputs.FACE_ZP, align_coarse=True)
+    else:
+        p = inputs.config_channel(**WORKLOAD)
     f = torch.tensor(p.f, device=dev)
     g = torch.tensor(p.g, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
-    out = {"workload": f"corrector stage, channel {WORKLOAD['nx']}x{WORKLOAD['ny']} Q2-Q1, v° = the predictor "
-                       "solution, rho 1, alpha 1e3, convection + streamline diffusion (Eq. a_stab), "
-                       f"{WORKLOAD['levels']} MG levels, FGMRES({args.restart}) FP64, rel-res 1e-8",
+    where = (f"box inclusion {args.dim3}^3 Q2-Q1 (contrast 1e3, alpha 100)" if args.dim3 else
+             f"channel {WORKLOAD['nx']}x{WORKLOAD['ny']} Q2-Q1")
+    out = {"workload": f"corrector stage, {where}, v° = the predictor solution, rho 1, convection + "
+                       f"streamline diffusion (Eq. a_stab), {p.levels} MG levels, FGMRES({args.restart}) FP64, "
+                       "rel-res 1e-8", "unknowns": len(p.f),
            "l2": "flushed (256 MiB write) before every timed solve"}
     # k_A = 4 (the predictor's degree) and k_A = 6, the corrector column of Table
     # "NS-solver-parameters-1"

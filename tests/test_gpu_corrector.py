@@ -192,6 +192,33 @@ def test_corrector_rejects_unsupported_contexts():
         s2.set_corrector(bad, rho)
 
 
+def test_saddle_point_multigrid_in_the_corrector_stage_3d():
+    """The block smoother K_j with ChebBiCGStab(1, 1) and one V-cycle of the saddle-point multigrid on
+    a 3D corrector block (FP64) against MonolithicHierarchy(corrector=(v°, rho))."""
+    import torch
+    from oracle.monolithic import MonolithicHierarchy
+    from paper_2305_08986_gb300 import gs
+    p = inputs.config_box_inclusion(3, (8, 8, 8), 2, 1e3, 20.0, seed=2, faces=inputs.all_faces(3) & ~inputs.FACE_XP,
+                                    align_coarse=True)
+    m = mesh_from_problem(p)
+    rng = np.random.default_rng(8)
+    vcirc = 2.0 * rng.standard_normal(m.n_u)
+    rho = 20.0
+    h = MonolithicHierarchy(m, p.eta, p.alpha, p.levels, corrector=(vcirc, rho))
+    s = gs.Solver.from_problem(p, precond_kind=1, mg_precision=64, corrector=1)
+    s.set_corrector(vcirc, rho)
+    L = p.levels - 1
+    fl = h.levels[L]
+    r = rng.standard_normal(fl.mesh.N)
+    r[fl.sys.constrained] = 0.0
+    rt = torch.tensor(r, device="cuda")
+    y = torch.empty_like(rt)
+    s.apply_level(L, gs.OP_SADDLE_SMOOTH, rt, y)
+    assert rel(y.cpu().numpy(), h.smoother(L, r)) <= 1e-9
+    s.apply_level(L, gs.OP_SADDLE_VCYCLE, rt, y)
+    assert rel(y.cpu().numpy(), h.vcycle(r)) <= 1e-9
+
+
 def test_saddle_point_multigrid_in_the_corrector_stage():
     """Sec. 4's own preconditioner with the corrector block: the block smoother K_j with
     Shat^{-1} = ChebBiCGStab(1, 1) and one V-cycle (FP64 multigrid) against
