@@ -160,7 +160,7 @@ typedef struct {            /* zero-initialised = defaults */
                                   schur_*, plap_degree and deflate do not apply. */
   int mono_smooth;          /* m of precond_kind 1; 0 -> 2 (Table NS-solver-parameters-1) */
   int mono_cycles;          /* n of precond_kind 1; 0 -> 1 */
-  int corrector;            /* 1: reserve the per-level fields of the corrector stage (2D; see
+  int corrector;            /* 1: reserve the per-level fields of the corrector stage (see
                                gs_set_corrector); 0 -> none */
 } gs_options;
 
@@ -249,7 +249,7 @@ gs_status gs_lift_rhs(gs_ctx* ctx, const double* f, const double* g, double* rhs
  *   sum_K r_K ((v° . grad) phi_i, (v° . grad) phi_j)_K with the Brooks-Hughes parameter
  *   r_K = h_K / (2 |v°|_K p1) (coth Pe_K - 1 / Pe_K), Pe_K = rho |v°|_K h_K / (2 eta_K p1), p1 = 2,
  *   |v°|_K at the cell centre, h_K the cell diameter, r_K = 0 where Pe_K < 1;
- * both integrated with the 3 x 3 Gauss rule.  Every later gs_vmult / gs_vmult_A / gs_solve /
+ * both integrated with the 3-point Gauss rule per axis.  Every later gs_vmult / gs_vmult_A / gs_solve /
  * gs_vcycle / gs_lift_rhs uses A_c (non-symmetric; B and B^T unchanged): the V-cycle smooths with
  * A_c, its Chebyshev bounds come from 12 Lanczos steps on the symmetric part (A_c + A_c^T) / 2, the
  * coarse levels take v° by injection (coarse node I = fine node 2 I) and the dense coarse solve
@@ -258,8 +258,8 @@ gs_status gs_lift_rhs(gs_ctx* ctx, const double* f, const double* g, double* rhs
  * With the saddle-point multigrid (precond_kind = 1) every level's velocity block is A_c and the
  * Schur solve of the block smoother is ChebBiCGStab(1, 1) (one BiCGStab step preconditioned by
  * diag(B diag(A_c)^-1 B^T)^-1, shadow residual = the right-hand side) in place of ChebMINRES.
- * NULL switches back to the predictor stage (rho ignored).  rho >= 0.  2D meshes, contexts created
- * with gs_options.corrector = 1, no deflation; synchronises the context stream (setup work:
+ * NULL switches back to the predictor stage (rho ignored).  rho >= 0.  2D and 3D meshes, contexts
+ * created with gs_options.corrector = 1, no deflation; synchronises the context stream (setup work:
  * diagonals, Lanczos, coarse factorisations).  Not while the context is in a batching engine. */
 gs_status gs_set_corrector(gs_ctx* ctx, const double* vcirc, double rho);
 

@@ -81,7 +81,7 @@ struct Level {
   void *xA = nullptr, *xB = nullptr, *b = nullptr, *d = nullptr, *dinv = nullptr;
   double lam_hi = 0.0;
   int* errw = nullptr;  // the context's device error word (bounded waits that gave up)
-  // corrector stage (option corrector, 2D): v° on this level (injected), r_K per cell
+  // corrector stage (option corrector): v° on this level (injected), r_K per cell
   std::vector<double> hvc, hrk;
   double* vc64 = nullptr;
   float* vc32 = nullptr;
