@@ -157,7 +157,8 @@ __device__ __forceinline__ void named_sync(int id) { asm volatile("bar.sync %0, 
 // Copy one window row: the 16-byte chunks covering the row that starts at element e_lo of vector v
 // land in the shared row srow (16-byte aligned), element e_lo at srow[phase].  One bulk copy
 // completing on `bar` when the chunks lie inside the vector (valid elements [0, vlen)); at the two
-// ends of the vector element-wise cp.async with zero fill instead (waited for with cp.async.wait).
+// ends of the vector element-wise cp.async with zero fill instead, committed as one group (waited
+// for with cp.async.wait_group by the copying thread before the next barrier).
 // Arrives on `bar` once, with the bytes it expects.  Returns the phase.
 template <typename T, int CH>
 __device__ __forceinline__ int stage_row(T* srow, const T* v, long long vlen, long long e_lo, uint64_t* bar) {
@@ -173,6 +174,7 @@ __device__ __forceinline__ int stage_row(T* srow, const T* v, long long vlen, lo
       const bool ok = e + i >= 0 && e + i < vlen;
       cp_async_elem(srow + i, ok ? v + e + i : v, ok);
     }
+    cp_async_commit();  // cp.async.wait_group covers committed groups only
   }
   return phase;
 }
