@@ -109,8 +109,7 @@ typedef struct {            /* zero-initialised = defaults */
                                   one pass over V for h1 = V^T w and the newest column of G, the
                                   coefficients c = h1 + (h1 - G h1) (CGS2's coefficients
                                   h1 + V^T (w - V h1) in exact arithmetic), one update pass w -= V c;
-                                  3 instead of 4 FP64 FMAs per basis entry (up to 64 basis vectors,
-                                  the explicit form beyond);
+                                  3 instead of 4 FP64 FMAs per basis entry;
                                1: second pass only when the new vector's norm drops below
                                   1/sqrt(2) of its value before the projection (single solves
                                   only: the engine needs a fixed number of passes);

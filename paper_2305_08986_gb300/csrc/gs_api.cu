@@ -747,8 +747,8 @@ void layout(gs_ctx* c, Arena& ar) {
   if (GF > 4 * 152) GF = 4 * 152;
   if (GF < 1) GF = 1;
   c->GF = (int)GF;
-  // partial-sum rows: m + 2 dots, or both dot blocks of orth = 2 (2 k rows, k <= 64)
-  const int prow = std::max(m + 2, 2 * std::min(m + 1, 64) + 2);
+  // partial-sum rows: m + 2 dots, or both dot blocks of orth = 2 (2 k rows, k <= m + 1)
+  const int prow = std::max(m + 2, 2 * (m + 1) + 2);
   c->part = ar.take<double>((long long)std::max(c->G, c->GF) * prow);
   c->dsc = ar.take<double>(4 * (m + 4));
   c->gram = ar.take<double>((long long)(m + 1) * (m + 1));
@@ -1953,7 +1953,7 @@ gs_status fgmres(gs_ctx* c, const double* b, double* x, double tol, int* its, do
       // |w|^2 in the same pass); a second pass when |w| fell below 1/sqrt(2) of its value
       // (Daniel-Gragg-Kaufman-Stewart, orth = 1), or always (CGS2, explicit or through the Gram matrix)
       double hn;
-      if (c->opt.orth == 2 && j + 1 <= kFusedGsMax) {
+      if (c->opt.orth == 2) {
         if (dfk)
           CKS(cgs_gram(c, (const float2*)Vdf, j, h2, nrm));
         else
@@ -2491,7 +2491,7 @@ gs_status slot_record_post(gs_ctx* c, double* gather_dev) {
       double* nrm = sl_nrm(c);
       CKS(c->fp32 ? sl_cast_out<float>(c, v, Zj) : sl_cast_out<double>(c, v, Zj));
       CKS(saddle(c, TILE_APPLY, Zj, c->w, nullptr));
-      if (c->opt.orth == 2 && j + 1 <= kFusedGsMax) {  // coefficients in h1, zeros in h2
+      if (c->opt.orth == 2) {  // coefficients in h1, zeros in h2
         if (dfk)
           CKS(cgs_gram(c, (const float2*)Vdf, j, h1, nrm, h2));
         else

@@ -387,23 +387,24 @@ struct DotsStripK {
     }
   }
 };
-// Both dot blocks of classical Gram-Schmidt evaluated through the Gram matrix (option orth = 2):
-// part[i * nblk + blk] = partials of V[i] . w and part[(k + i) * nblk + blk] = partials of V[i] . u
-// for i < k, u = V[k - 1] (the newest basis vector: one new column of G = V^T V).  Like DotsStripK,
-// with a second staged strip; every basis row is read once for both dots.
+// Both dot blocks of classical Gram-Schmidt evaluated through the Gram matrix (option orth = 2) for
+// rows r0 .. r0 + k - 1 of the basis (a chunk of at most 64): part[(r0 + i) * nblk + blk] = partials
+// of V[r0 + i] . w and part[(kt + r0 + i) * nblk + blk] = partials of V[r0 + i] . u, with u the newest
+// basis vector (one new column of G = V^T V) and kt the basis size.  Like DotsStripK, with a second
+// staged strip; every basis row is read once for both dots.
 template <typename B>
 struct DotsStrip2K {
   using O = BasisOps<B>;
   static constexpr int KW = 8;
-  struct Args { const B* V; long long ldv; int k; const double* w; long long n; double* part; };
+  struct Args { const B* V; long long ldv; int r0; int k; int kt; const B* U; const double* w; long long n; double* part; };
   static constexpr int THREADS = TPB, MINB = 3;
   static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
     __shared__ B wt[TPB];
     __shared__ B ut[TPB];
-    const B* __restrict__ V = a.V;
+    const B* __restrict__ V = a.V + (long long)a.r0 * a.ldv;
     const long long ldv = a.ldv, n = a.n;
     const int k = a.k;
-    const B* __restrict__ U = V + (long long)(k - 1) * ldv;
+    const B* __restrict__ U = a.U;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     B accw[KW], accu[KW];
 #pragma unroll
@@ -447,18 +448,26 @@ struct DotsStrip2K {
           u += __shfl_down_sync(0xffffffffu, u, o);
         }
         if (lane == 0) {
-          a.part[(long long)i * nblk + blk] = v;
-          a.part[(long long)(k + i) * nblk + blk] = u;
+          a.part[(long long)(a.r0 + i) * nblk + blk] = v;
+          a.part[(long long)(a.kt + a.r0 + i) * nblk + blk] = u;
         }
       }
     }
   }
 };
+// all kt rows, in launches of at most 64 rows; u = V[kt - 1]
 template <typename B>
-cudaError_t launch_dots_strip2(const B* V, long long ldv, int k, const double* w, long long n, double* part, int G,
+cudaError_t launch_dots_strip2(const B* V, long long ldv, int kt, const double* w, long long n, double* part, int G,
                                cudaStream_t st) {
-  if (k < 1 || k > 8 * DotsStrip2K<B>::KW) return cudaErrorInvalidValue;
-  return submit<DotsStrip2K<B>>({V, ldv, k, w, n, part}, G, 0, st);
+  constexpr int KMAX = 8 * DotsStrip2K<B>::KW;
+  if (kt < 1) return cudaErrorInvalidValue;
+  const B* U = V + (long long)(kt - 1) * ldv;
+  for (int r0 = 0; r0 < kt; r0 += KMAX) {
+    const int k = kt - r0 < KMAX ? kt - r0 : KMAX;
+    cudaError_t e = submit<DotsStrip2K<B>>({V, ldv, r0, k, kt, U, w, n, part}, G, 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 cudaError_t launch_dots_strip2_df(const float2* V, long long ldv, int k, const double* w, long long n, double* part,
                                   int G, cudaStream_t st) {
@@ -472,19 +481,19 @@ cudaError_t launch_dots_strip2_fp64(const double* V, long long ldv, int k, const
 // Gram-matrix form of the second Gram-Schmidt pass: with d = [V^T w ; V^T v_{k-1}] (2k values),
 // store column k - 1 of G = V^T V (and its mirror row), then c = h1 + (h1 - G h1), h1 = V^T w.  In
 // exact arithmetic c is the CGS2 coefficient vector h1 + V^T (w - V h1); the update w - V c follows.
-// One block; k <= 64.
+// One block of 256 threads; any k <= ldg.
 struct GramCorrK {
   struct Args { const double* d; double* G; int ldg; int k; double* c; double* zero; };
-  static constexpr int THREADS = 64, MINB = 1;
+  static constexpr int THREADS = 256, MINB = 1;
   static __device__ __forceinline__ void body(const Args& a, int, int) {
-    const int i = threadIdx.x, k = a.k;
-    if (i < k) {
+    const int k = a.k;
+    for (int i = threadIdx.x; i < k; i += THREADS) {
       const double g = a.d[k + i];
       a.G[(long long)i * a.ldg + (k - 1)] = g;
       a.G[(long long)(k - 1) * a.ldg + i] = g;
     }
     __syncthreads();
-    if (i < k) {
+    for (int i = threadIdx.x; i < k; i += THREADS) {
       double s = 0.0;
       for (int l = 0; l < k; ++l) s = fma(a.G[(long long)i * a.ldg + l], a.d[l], s);
       const double h = a.d[i];
@@ -495,7 +504,7 @@ struct GramCorrK {
 };
 cudaError_t launch_gram_correct(const double* d, double* G, int ldg, int k, double* c, double* zero,
                                 cudaStream_t st) {
-  if (k < 1 || k > 64) return cudaErrorInvalidValue;
+  if (k < 1 || k > ldg) return cudaErrorInvalidValue;
   return submit<GramCorrK>({d, G, ldg, k, c, zero}, 1, 0, st);
 }
 

@@ -148,6 +148,30 @@ def test_solve_parity_gram_matrix_cgs(name):
         assert rel(normalize_pressure(m, o.sys, x.cpu().numpy()), normalize_pressure(m, o.sys, xo)) <= 1e-8
 
 
+def test_gram_matrix_cgs_beyond_64_basis_vectors():
+    """The Gram-matrix form with a long cycle (restart 100; the mass-only Schur approximation makes the
+    channel need more than 64 iterations, so the dot pass runs in several 64-row launches) against the
+    explicit CGS2 (orth = 3): the same iteration count within max(2, 5 %), both to rel-res 1e-9."""
+    import torch
+    from paper_2305_08986_gb300 import gs
+    p = PROBLEMS["channel_small"]()
+    out = {}
+    for orth in (2, 3):
+        s = gs.Solver.from_problem(p, mg_precision=64, orth=orth, schur_kind=1, restart=100, max_iter=2000)
+        f = torch.tensor(p.f, device="cuda")
+        g = torch.tensor(p.g, device="cuda")
+        b = torch.empty_like(f)
+        s.lift_rhs(f, g, b)
+        x = torch.zeros_like(b)
+        it, rr, st = s.solve(b, x, tol=1e-9)
+        assert st == 0 and rr <= 1e-9, (orth, it, rr)
+        out[orth] = (it, x.cpu().numpy())
+    assert out[2][0] > 64, out[2][0]
+    assert abs(out[2][0] - out[3][0]) <= max(2, 0.05 * out[3][0]), (out[2][0], out[3][0])
+    n_u = len(p.f) - int(np.prod([k + 1 for k in p.n]))
+    assert rel(out[2][1][:n_u], out[3][1][:n_u]) <= 1e-6
+
+
 def test_cahouet_chabard_iterations():
     """alpha = 1e3 channel: FP32 multigrid with the Cahouet-Chabard term stays in the tens of
     iterations (the mass-only Schur approximation needs several hundred)."""
