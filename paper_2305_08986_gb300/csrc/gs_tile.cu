@@ -351,7 +351,8 @@ __device__ __forceinline__ void tile3d_body(const TileArgs<T>& A, int bid) {
 // fixed order (tiles lexicographic, x fastest) and applies the epilogue.  Inside a tile the cells are
 // processed in 8 phases by their global parity class, as in the tiles above.  The sums are
 // deterministic; they differ in rounding from the halo tiles' (a different association at the
-// shared faces), so all FP32 applications of the 3D velocity block use this kernel.
+// shared faces), so all FP32 applications of the 3D velocity block use this kernel, except in the
+// corrector stage (the convection term runs in the 8 x 8 x 4 halo tiles).
 struct NH3 {
   static constexpr int TC0 = kNH3Cells0, TC1 = kNH3Cells1, TC2 = kNH3Cells2;  // cells per tile
   static constexpr int G0 = TC0 / 2, G1 = TC1 / 2, G2 = TC2 / 2, NG = G0 * G1 * G2;  // 32 groups
