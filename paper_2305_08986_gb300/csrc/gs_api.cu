@@ -1789,8 +1789,7 @@ gs_status capture_precond(gs_ctx* c) {
 template <typename T>
 gs_status precond_T(gs_ctx* c, const double* v, double* z) {
   Level& F = c->lv[c->L - 1];
-  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)body_in_p(c), F.Np, (T)1, c->st));
-  KL(K_VEC, launch_cast<double, T>(v, (T*)body_in_u(c), F.nu, (T)1, c->st));
+  KL(K_VEC, launch_precond_in<T>(v, (T*)body_in_u(c), (T*)body_in_p(c), F.nu, F.Np, c->st));
   const void* zu;
   const void* zp;
   const bool use_graph = c->opt.graphs == 0 && !c->prof && c->cap_st != nullptr;
@@ -1808,9 +1807,7 @@ gs_status precond_T(gs_ctx* c, const double* v, double* z) {
     zp = body_out_p(c);
   }
   c->pcalls++;
-  KL(K_VEC, launch_cast<T, double>((const T*)zu, z, F.nu, 1.0, c->st));
-  KL(K_VEC, launch_cast<T, double>((const T*)zp, z + c->nu, F.Np, 1.0, c->st));
-  KL(K_VEC, launch_copy_constrained(v, z, F.g, c->st));
+  KL(K_VEC, launch_precond_out<T>((const T*)zu, (const T*)zp, v, z, F.g, c->st));
   CKS(project_pressure(c, z));
   return GS_OK;
 }
@@ -2357,16 +2354,13 @@ gs_status sl_norm2(gs_ctx* c, const double* v, double* dst) {
 template <typename T>
 gs_status sl_cast_in(gs_ctx* c, const double* v) {
   Level& F = c->lv[c->L - 1];
-  KL(K_VEC, launch_cast<double, T>(v + c->nu, (T*)body_in_p(c), F.Np, (T)1, c->st));
-  KL(K_VEC, launch_cast<double, T>(v, (T*)body_in_u(c), F.nu, (T)1, c->st));
+  KL(K_VEC, launch_precond_in<T>(v, (T*)body_in_u(c), (T*)body_in_p(c), F.nu, F.Np, c->st));
   return GS_OK;
 }
 template <typename T>
 gs_status sl_cast_out(gs_ctx* c, const double* v, double* z) {
   Level& F = c->lv[c->L - 1];
-  KL(K_VEC, launch_cast<T, double>((const T*)c->ks.zu, z, F.nu, 1.0, c->st));
-  KL(K_VEC, launch_cast<T, double>((const T*)c->ks.zp, z + c->nu, F.Np, 1.0, c->st));
-  KL(K_VEC, launch_copy_constrained(v, z, F.g, c->st));
+  KL(K_VEC, launch_precond_out<T>((const T*)c->ks.zu, (const T*)c->ks.zp, v, z, F.g, c->st));
   CKS(project_pressure(c, z));
   return GS_OK;
 }

@@ -919,6 +919,68 @@ cudaError_t launch_copy_constrained(const double* v, double* z, const Geom& geo,
   return submit<CopyConstrainedK>({v, z, geo}, nblk(N), 0, st);
 }
 
+// The preconditioner's result back in FGMRES precision, z = [(double) zu | (double) zp], with the
+// constrained entries copied from v instead (the saddle matrix is the identity there): the two
+// casts and the constrained copy above in one pass.  One thread per velocity node, all of its
+// components (its mesh position, and so its constraint, is found once), then one per pressure
+// node.  Each entry of z depends only on the same entry of v, zu or zp, so z may alias v.
+template <typename T>
+struct PrecondOutK {
+  struct Args { const T* zu; const T* zp; const double* v; double* z; Geom geo; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    const Geom& g = a.geo;
+    const long long Nv = g.Nv, n_u = g.dim * Nv;
+    const bool idx32 = Nv < (1LL << 31);
+    GS_FOR(i, Nv + g.Np) {
+      if (i < Nv) {
+        bool con;
+        if (g.vmask) {
+          con = g.vmask[i] != 0;
+        } else if (idx32) {
+          const unsigned node = (unsigned)i, n0 = (unsigned)g.nv[0], n1 = (unsigned)g.nv[1];
+          const unsigned q = node / n0;
+          con = face_constrained(g, (int)(node - q * n0), (int)(q % n1), g.dim == 3 ? (int)(q / n1) : 0);
+        } else {
+          const long long q = i / g.nv[0];
+          con = face_constrained(g, (int)(i - q * g.nv[0]), (int)(q % g.nv[1]), g.dim == 3 ? (int)(q / g.nv[1]) : 0);
+        }
+        for (int c = 0; c < g.dim; ++c) {
+          const long long e = c * Nv + i;
+          a.z[e] = con ? a.v[e] : (double)a.zu[e];
+        }
+      } else {
+        const long long p = i - Nv;
+        const bool con = g.pmask != nullptr && g.pmask[p] != 0;
+        a.z[n_u + p] = con ? a.v[n_u + p] : (double)a.zp[p];
+      }
+    }
+  }
+};
+template <typename T>
+cudaError_t launch_precond_out(const T* zu, const T* zp, const double* v, double* z, const Geom& geo,
+                               cudaStream_t st) {
+  return submit<PrecondOutK<T>>({zu, zp, v, z, geo}, nblk(geo.Nv + geo.Np), 0, st);
+}
+
+// the preconditioner's input in its own precision: u = (T) v[0, n_u), p = (T) v[n_u, n_u + n_p)
+template <typename T>
+struct PrecondInK {
+  struct Args { const double* v; T* u; T* p; long long n_u, n_p; };
+  static constexpr int THREADS = TPB, MINB = 1;
+  static __device__ __forceinline__ void body(const Args& a, int blk, int nblk) {
+    GS_FOR(i, a.n_u + a.n_p) {
+      const T x = (T)a.v[i];
+      if (i < a.n_u) a.u[i] = x;
+      else a.p[i - a.n_u] = x;
+    }
+  }
+};
+template <typename T>
+cudaError_t launch_precond_in(const double* v, T* u, T* p, long long n_u, long long n_p, cudaStream_t st) {
+  return submit<PrecondInK<T>>({v, u, p, n_u, n_p}, nblk(n_u + n_p), 0, st);
+}
+
 // rhs = Mf - Kg on free entries, g on constrained entries (velocity then pressure)
 __global__ void k_combine_lift(const double* __restrict__ Mf, const double* __restrict__ Kg,
                                const double* __restrict__ g, const Geom geo, double* __restrict__ rhs) {
@@ -941,7 +1003,9 @@ cudaError_t launch_combine_lift(const double* Mf, const double* Kg, const double
   template cudaError_t launch_lanczos_post<T>(const T*, const T*, const T*, T, T*, long long, cudaStream_t); \
   template cudaError_t launch_dots_partial<T>(const T*, long long, int, const T*, long long, double*, int, cudaStream_t); \
   template cudaError_t launch_axpby<T>(const T*, T*, T, T, long long, cudaStream_t);                 \
-  template cudaError_t launch_coarse_solve<T>(const double*, const int*, int, const T*, T*, long long, double*, cudaStream_t);
+  template cudaError_t launch_coarse_solve<T>(const double*, const int*, int, const T*, T*, long long, double*, cudaStream_t); \
+  template cudaError_t launch_precond_out<T>(const T*, const T*, const double*, double*, const Geom&, cudaStream_t); \
+  template cudaError_t launch_precond_in<T>(const double*, T*, T*, long long, long long, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -262,6 +262,13 @@ template <typename T>
 cudaError_t launch_axpby(const T* x, T* y, T a, T b, long long n, cudaStream_t st);  // y = a x + b y
 // z[i] = v[i] on every constrained entry of a full vector [u | p] (finest level)
 cudaError_t launch_copy_constrained(const double* v, double* z, const Geom& geo, cudaStream_t st);
+// z = [(double) zu | (double) zp] with z[i] = v[i] on every constrained entry (finest level)
+template <typename T>
+cudaError_t launch_precond_out(const T* zu, const T* zp, const double* v, double* z, const Geom& geo,
+                               cudaStream_t st);
+// u = (T) v[0, n_u), p = (T) v[n_u, n_u + n_p)
+template <typename T>
+cudaError_t launch_precond_in(const double* v, T* u, T* p, long long n_u, long long n_p, cudaStream_t st);
 cudaError_t launch_combine_lift(const double* Mf, const double* Kg, const double* g,
                                 const uint8_t* vmask, const uint8_t* pmask, const Geom& geo,
                                 double* rhs, cudaStream_t st);
