@@ -530,29 +530,36 @@ __device__ __forceinline__ void fix3nh_body(const TileArgs<T>& A, int blk) {
   long long idx = (long long)blk * 256 + threadIdx.x;
   // an interior tile face along an axis: node coordinate P k with 0 < k < tiles
   auto face = [](int X, int P, int tiles) { return X % P == 0 && X > 0 && X / P < tiles; };
+  // q = a / b and a - q b; every index and plane size here is below Nv, so 32-bit division serves
+  // whenever Nv < 2^31 (a 64-bit division takes several times the instructions)
+  const bool i32 = g.Nv < (1LL << 31);
+  auto divmod = [i32](long long a, long long b, int& q) -> long long {
+    if (i32) {
+      const unsigned ua = (unsigned)a, ub = (unsigned)b, uq = ua / ub;
+      q = (int)uq;
+      return (long long)(ua - uq * ub);
+    }
+    const long long lq = a / b;
+    q = (int)lq;
+    return a - lq * b;
+  };
   int I, J, Kz;
   if (idx < nX) {
-    const long long pl = (long long)nv1 * nv2;
-    const int p = (int)(idx / pl);
-    const long long r = idx - p * pl;
+    int p;
+    const long long r = divmod(idx, (long long)nv1 * nv2, p);
     I = S::P0 * (p + 1);
-    J = (int)(r % nv1);
-    Kz = (int)(r / nv1);
+    J = (int)divmod(r, nv1, Kz);
   } else if ((idx -= nX) < nY) {
-    const long long pl = (long long)nv0 * nv2;
-    const int p = (int)(idx / pl);
-    const long long r = idx - p * pl;
+    int p;
+    const long long r = divmod(idx, (long long)nv0 * nv2, p);
     J = S::P1 * (p + 1);
-    I = (int)(r % nv0);
-    Kz = (int)(r / nv0);
+    I = (int)divmod(r, nv0, Kz);
     if (face(I, S::P0, A.tiles[0])) return;
   } else if ((idx -= nY) < nZ) {
-    const long long pl = (long long)nv0 * nv1;
-    const int p = (int)(idx / pl);
-    const long long r = idx - p * pl;
+    int p;
+    const long long r = divmod(idx, (long long)nv0 * nv1, p);
     Kz = S::P2 * (p + 1);
-    I = (int)(r % nv0);
-    J = (int)(r / nv0);
+    I = (int)divmod(r, nv0, J);
     if (face(I, S::P0, A.tiles[0]) || face(J, S::P1, A.tiles[1])) return;
   } else {
     return;
@@ -582,9 +589,15 @@ __device__ __forceinline__ void fix3nh_body(const TileArgs<T>& A, int blk) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     T acc = T(0);
-    for (int b2 = 0; b2 < nt[2]; ++b2)
-      for (int b1 = 0; b1 < nt[1]; ++b1)
-        for (int b0 = 0; b0 < nt[0]; ++b0) {
+    // unrolled to the maximum of two tiles per axis and predicated, so tl and ll stay in registers;
+    // the sharing tiles are added in the same order (z, then y, then x outermost to innermost)
+#pragma unroll
+    for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+      for (int b1 = 0; b1 < 2; ++b1)
+#pragma unroll
+        for (int b0 = 0; b0 < 2; ++b0) {
+          if (b2 >= nt[2] || b1 >= nt[1] || b0 >= nt[0]) continue;
           const long long t = tl[0][b0] + (long long)A.tiles[0] * (tl[1][b1] + (long long)A.tiles[1] * tl[2][b2]);
           const int li = ll[0][b0] + S::W0 * (ll[1][b1] + S::W1 * ll[2][b2]);
           acc += A.part[(t * 3 + a) * S::NW + li];
@@ -615,7 +628,7 @@ struct Tile3NHK {
 template <typename T, int MODE>
 struct Fix3NHK {
   using Args = TileArgs<T>;
-  static constexpr int THREADS = 256, MINB = 1;
+  static constexpr int THREADS = 256, MINB = 4;
   static __device__ __forceinline__ void body(const Args& a, int blk, int) { fix3nh_body<T, MODE>(a, blk); }
 };
 
