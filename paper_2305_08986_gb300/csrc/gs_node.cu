@@ -9,6 +9,14 @@ namespace {
 constexpr int TPB = 256;
 
 __device__ __forceinline__ void unflat(long long idx, const int* ext, int dim, int& I, int& J, int& K) {
+  if (idx < (1LL << 31)) {  // 32-bit division (a 64-bit one takes several times the instructions)
+    const unsigned u = (unsigned)idx, e0 = (unsigned)ext[0], e1 = (unsigned)ext[1];
+    const unsigned q = u / e0;
+    I = (int)(u - q * e0);
+    J = (int)(q % e1);
+    K = dim == 3 ? (int)(q / e1) : 0;
+    return;
+  }
   I = (int)(idx % ext[0]);
   idx /= ext[0];
   J = (int)(idx % ext[1]);
@@ -80,23 +88,23 @@ cudaError_t launch_diagA(const Geom& g, const OpCoef<T>& c, const T* eta, const 
 // coarse (2c, 2c+1, 2c+2); fine 4c+3 <- (-1/8, 3/4, 3/8).  Constrained fine rows and
 // constrained coarse columns are removed. -----------------------------------------------------
 
-// weights of coarse node C seen from fine nodes: offsets f - 2C and weights.  The weights and
-// their pairwise products are dyadic and exact in FP32, so they are kept in float (FP64
-// arithmetic runs at 1/74 of the FP32 rate on this GPU); the results are the same bits.
-__device__ __forceinline__ int restrict_stencil(int C, int nvf, int* fi, float* w) {
-  int m = 0;
-  if (C & 1) {
-    const int f[3] = {2 * C - 1, 2 * C, 2 * C + 1};
-    const float ww[3] = {0.75f, 1.0f, 0.75f};
-    for (int t = 0; t < 3; ++t)
-      if (f[t] >= 0 && f[t] < nvf) { fi[m] = f[t]; w[m] = ww[t]; m++; }
-  } else {
-    const int f[5] = {2 * C - 3, 2 * C - 1, 2 * C, 2 * C + 1, 2 * C + 3};
-    const float ww[5] = {-0.125f, 0.375f, 1.0f, 0.375f, -0.125f};
-    for (int t = 0; t < 5; ++t)
-      if (f[t] >= 0 && f[t] < nvf) { fi[m] = f[t]; w[m] = ww[t]; m++; }
+// weights of coarse node C seen from fine nodes, in five slots at offsets f - 2C = -3, -1, 0, 1, 3:
+// even C: (-1/8, 3/8, 1, 3/8, -1/8); odd C: (-, 3/4, 1, 3/4, -); ok marks the slots that exist
+// (inside the fine mesh, and the inner three for odd C).  Fixed slots, so the arrays stay in
+// registers when the loops over them are unrolled.  The weights and their pairwise products are
+// dyadic and exact in FP32, so they are kept in float (FP64 arithmetic is far slower on this GPU);
+// the results are the same bits.
+__device__ __forceinline__ void restrict_stencil(int C, int nvf, int (&fi)[5], float (&w)[5], bool (&ok)[5]) {
+  const bool odd = C & 1;
+  const int off[5] = {-3, -1, 0, 1, 3};
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    fi[t] = 2 * C + off[t];
+    ok[t] = fi[t] >= 0 && fi[t] < nvf && (!odd || (t >= 1 && t <= 3));
   }
-  return m;
+  w[0] = w[4] = -0.125f;
+  w[1] = w[3] = odd ? 0.75f : 0.375f;
+  w[2] = 1.0f;
 }
 
 // Optional start of the coarse level's Chebyshev smoother from zero, fused into the restriction
@@ -132,15 +140,25 @@ __device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, co
   if (!con) {
     int fx[5], fy[5], fz[5];
     float wx[5], wy[5], wz[5];
-    const int mx = restrict_stencil(I, gf.nv[0], fx, wx);
-    const int my = restrict_stencil(J, gf.nv[1], fy, wy);
-    int mz = 1;
-    fz[0] = 0; wz[0] = 1.0f;
-    if (DIM == 3) mz = restrict_stencil(K, gf.nv[2], fz, wz);
-    for (int k = 0; k < mz; ++k)
-      for (int j = 0; j < my; ++j) {
+    bool okx[5], oky[5], okz[5];
+    restrict_stencil(I, gf.nv[0], fx, wx, okx);
+    restrict_stencil(J, gf.nv[1], fy, wy, oky);
+    if (DIM == 3) {
+      restrict_stencil(K, gf.nv[2], fz, wz, okz);
+    } else {
+      fz[0] = 0; wz[0] = 1.0f; okz[0] = true;
+    }
+    // the existing fine nodes in slot order (z, then y, then x innermost)
+#pragma unroll
+    for (int k = 0; k < (DIM == 3 ? 5 : 1); ++k) {
+      if (!okz[k]) continue;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        if (!oky[j]) continue;
         const T wjk = T(wy[j] * wz[k]);  // exact in float
-        for (int i = 0; i < mx; ++i) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          if (!okx[i]) continue;
           const long long fn = fx[i] + (long long)gf.nv[0] * (fy[j] + (long long)gf.nv[1] * fz[k]);
           if (vnode_constrained(gf, fn, fx[i], fy[j], fz[k])) continue;
           const T w = T(wx[i]) * wjk;
@@ -148,6 +166,7 @@ __device__ __forceinline__ void restrict_body(const Geom& gf, const Geom& gc, co
           for (int a = 0; a < DIM; ++a) acc[a] += w * rf[a * gf.Nv + fn];
         }
       }
+    }
   }
 #pragma unroll
   for (int a = 0; a < DIM; ++a) rc[a * gc.Nv + node] = acc[a];
@@ -416,25 +435,42 @@ __device__ __forceinline__ void p_restrict_body(const Geom& gf, const Geom& gc, 
   int I, J, K;
   unflat(q, gc.npn, DIM, I, J, K);
   const int idx[3] = {I, J, K};
-  int f[3][3], m[3];
+  // fine nodes 2C - 1, 2C, 2C + 1 per axis with weights 1/2, 1, 1/2; ok marks those inside the
+  // fine mesh (fixed slots: the arrays stay in registers)
+  int f[3][3];
   T w[3][3];
+  bool ok[3][3];
+#pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    m[ax] = 0;
-    if (ax >= DIM) { f[ax][0] = 0; w[ax][0] = T(1); m[ax] = 1; continue; }
+    if (ax >= DIM) {
+      f[ax][0] = 0; w[ax][0] = T(1); ok[ax][0] = true; ok[ax][1] = ok[ax][2] = false;
+      continue;
+    }
     const int C = idx[ax];
-    const int cand[3] = {2 * C - 1, 2 * C, 2 * C + 1};
-    const T ww[3] = {T(0.5), T(1), T(0.5)};
-    for (int t = 0; t < 3; ++t)
-      if (cand[t] >= 0 && cand[t] < gf.npn[ax]) { f[ax][m[ax]] = cand[t]; w[ax][m[ax]] = ww[t]; m[ax]++; }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      f[ax][t] = 2 * C - 1 + t;
+      ok[ax][t] = f[ax][t] >= 0 && f[ax][t] < gf.npn[ax];
+    }
+    w[ax][0] = w[ax][2] = T(0.5);
+    w[ax][1] = T(1);
   }
   T acc = T(0);
-  for (int k = 0; k < m[2]; ++k)
-    for (int j = 0; j < m[1]; ++j)
-      for (int i = 0; i < m[0]; ++i) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (!ok[2][k]) continue;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (!ok[1][j]) continue;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (!ok[0][i]) continue;
         const long long fq = f[0][i] + (long long)gf.npn[0] * (f[1][j] + (long long)gf.npn[1] * f[2][k]);
         if (mf[fq]) continue;
         acc += w[0][i] * w[1][j] * w[2][k] * rf[fq];
       }
+    }
+  }
   rc[q] = acc;
   if (cs.d) {  // start of the coarse level's Chebyshev smoother (ChebStart)
     const T v = cs.dinv[q] * acc * cs.inv_theta;
@@ -453,22 +489,42 @@ __device__ __forceinline__ void p_prolong_add_body(const Geom& gf, const Geom& g
   int I, J, K;
   unflat(q, gf.npn, DIM, I, J, K);
   const int idx[3] = {I, J, K};
-  int cidx[3][2], m[3];
+  // even fine coordinate v: coarse v / 2 with weight 1; odd: coarse (v - 1) / 2 and (v + 1) / 2 with
+  // weights 1/2 (fixed slots: the arrays stay in registers)
+  int cidx[3][2];
   T w[3][2];
+  bool ok[3][2];
+#pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    if (ax >= DIM) { cidx[ax][0] = 0; w[ax][0] = T(1); m[ax] = 1; continue; }
+    if (ax >= DIM) {
+      cidx[ax][0] = 0; w[ax][0] = T(1); ok[ax][0] = true; ok[ax][1] = false;
+      continue;
+    }
     const int v = idx[ax];
-    if (!(v & 1)) { cidx[ax][0] = v >> 1; w[ax][0] = T(1); m[ax] = 1; }
-    else { cidx[ax][0] = v >> 1; cidx[ax][1] = (v >> 1) + 1; w[ax][0] = w[ax][1] = T(0.5); m[ax] = 2; }
+    const bool odd = v & 1;
+    cidx[ax][0] = v >> 1;
+    cidx[ax][1] = (v >> 1) + 1;
+    w[ax][0] = odd ? T(0.5) : T(1);
+    w[ax][1] = T(0.5);
+    ok[ax][0] = true;
+    ok[ax][1] = odd;
   }
   T acc = T(0);
-  for (int k = 0; k < m[2]; ++k)
-    for (int j = 0; j < m[1]; ++j)
-      for (int i = 0; i < m[0]; ++i) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (!ok[2][k]) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (!ok[1][j]) continue;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (!ok[0][i]) continue;
         const long long cq = cidx[0][i] + (long long)gc.npn[0] * (cidx[1][j] + (long long)gc.npn[1] * cidx[2][k]);
         if (mc[cq]) continue;
         acc += w[0][i] * w[1][j] * w[2][k] * xc[cq];
       }
+    }
+  }
   xf[q] += acc;
 }
 
